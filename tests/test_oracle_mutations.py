@@ -1,0 +1,122 @@
+"""Planted mistakes in the oracle (CPU only): each plausible error must fail at least one pin.
+
+Each case monkeypatches one oracle function with a subtly wrong variant and runs the pin tests
+that should catch it, expecting an assertion failure. This shows the pins are not vacuous.
+"""
+
+import numpy as np
+import pytest
+
+import oracle.convert
+import oracle.mpo
+import oracle.rng
+import oracle.rounding
+from tests import test_oracle_basics as tb
+from tests import test_oracle_convert as tc
+from tests import test_oracle_rng as tr
+from tests import test_oracle_rounding as tro
+from tests import test_oracle_tnrsvd as tt
+
+
+def _fails(fn, *args):
+    with pytest.raises((AssertionError, ValueError, IndexError)):
+        fn(*args)
+
+
+def test_transposed_operand_in_contract(monkeypatch):
+    orig = oracle.mpo.contract
+
+    def bad(A, X, trans=False):
+        return orig(A, X, trans=not trans) if A[0].shape[1] == A[0].shape[2] else orig(oracle.mpo.transpose(A), X, trans)
+
+    monkeypatch.setattr(oracle.mpo, "contract", bad)
+    _fails(tb.test_contract_equals_dense_product, False)
+
+
+def test_bond_order_swapped_in_contract(monkeypatch):
+    def bad(A, X, trans=False):
+        out = []
+        for a, x in zip(A, X):
+            R, Ia, Ja, R2 = a.shape
+            S, Ix, Kx, S2 = x.shape
+            y = np.einsum("rijt,sjku->rsikut", a, x).reshape(S * R, Ia, Kx, S2 * R2)  # (r,s) -> s + S r
+            out.append(y)
+        return out
+
+    monkeypatch.setattr(oracle.mpo, "contract", bad)
+    _fails(tb.test_contract_equals_dense_product, False)
+
+
+def test_dropped_r_absorption(monkeypatch):
+    def bad(cores):
+        cores = [c.copy() for c in cores]
+        for k in range(len(cores) - 1):
+            t, I, Kx, t2 = cores[k].shape
+            Q, _ = np.linalg.qr(cores[k].reshape(t * I * Kx, t2, order="F"))
+            cores[k] = Q.reshape(t, I, Kx, Q.shape[1], order="F")  # R never absorbed
+        return cores
+
+    monkeypatch.setattr(oracle.rounding, "_lr_orthogonalize", bad)
+    _fails(tro.test_orthogonalize_no_truncation, 0)
+
+
+def test_wrong_sign_in_site1(monkeypatch):
+    orig = oracle.rounding._site1_core
+
+    def bad(M, I1, R2):
+        M = M.copy()
+        M[0] = -M[0]
+        return orig(M, I1, R2)
+
+    monkeypatch.setattr(oracle.rounding, "_site1_core", bad)
+    _fails(tro.test_orthogonalize_no_truncation, 0)
+
+
+def test_omega_kappa_fastest(monkeypatch):
+    def bad(seed, J, K):
+        g = oracle.rng.normals(seed, 0, J[0] * K + sum(J[1:]))
+        cores = [g[: J[0] * K].reshape(J[0], K)[None, :, :, None].copy()]  # kappa fastest
+        pos = J[0] * K
+        for j in J[1:]:
+            cores.append(g[pos:pos + j].reshape(1, j, 1, 1).copy())
+            pos += j
+        return cores
+
+    monkeypatch.setattr(oracle.rng, "omega", bad)
+    _fails(tr.test_omega_lemma_5_1_rank_and_layout)
+
+
+def test_digits_reversed(monkeypatch):
+    orig = oracle.convert.convert
+
+    def bad(*a, **k):
+        R, X, digits = orig(*a, **k)
+        return R, X, digits[:, ::-1].copy()
+
+    monkeypatch.setattr(oracle.convert, "convert", bad)
+    _fails(tc.test_random_sparse_exact_and_lemmas, 0)
+
+
+def test_keep_rank_off_by_one(monkeypatch):
+    orig = oracle.rounding.keep_rank
+    monkeypatch.setattr(oracle.rounding, "keep_rank", lambda s, d, m: min(len(s), orig(s, d, m) + 1))
+    _fails(tro.test_keep_rank_closed_form)
+
+
+def test_mpo_svd_w_transposed(monkeypatch):
+    orig = oracle.rounding.mpo_svd
+
+    def bad(Z, tol=0.0, max_rank=0):
+        W, S, V = orig(Z, tol, max_rank)
+        return W.T, S, V
+
+    monkeypatch.setattr(oracle.rounding, "mpo_svd", bad)
+    _fails(tro.test_mpo_svd_matches_lapack)
+
+
+def test_no_power_iteration_transpose(monkeypatch):
+    """Using A instead of A^T in the power iteration breaks the dense cross-check (rectangular
+    products would not even conform; here the square case gives the wrong subspace)."""
+    orig = oracle.mpo.contract
+    monkeypatch.setattr(oracle.mpo, "contract", lambda A, X, trans=False: orig(A, X, False))
+    _fails(tt.test_dense_rsvd_cross_check, 1)

@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module only draws and assembles inputs; it holds none of the method's arithmetic
+(no contraction, orthogonalisation, SVD sweep or conversion of the paper). All generators
+use numpy.random.default_rng(seed) (PCG64) and return float64 MPO cores as numpy arrays of
+logical shape (R_k, I_k, J_k, R_{k+1}), or COO triplets for sparse matrices.
+
+Workloads (sizes and distributions follow the paper's experiments, Section 6):
+  gaussian_mpo    i.i.d. N(0,1) cores scaled by a constant (plain FP64 case: d=6, 4x4 sites, ranks 3)
+  prescribed_mpo  A = U diag(sigma) V^T with orthogonal MPOs U, V (the construction of Section 6.3's
+                  second experiment, there with TT_RAND; here from QR'd Gaussian cores)
+  banded_coo      random banded sparse matrix standing in for the UF collection matrices of
+                  Sections 6.1-6.2, which are not available here.
+"""
+
+import numpy as np
+
+
+def gaussian_mpo(seed, I, J, R, scale=None):
+    """Cores k = 1..d drawn in turn, each in memory order (r fastest), as N(0,1) * scale.
+
+    ``scale`` is a float or a callable(k, core_shape) -> float; default 1.
+    """
+    rng = np.random.default_rng(seed)
+    d = len(I)
+    assert len(J) == d and len(R) == d + 1 and R[0] == 1 and R[-1] == 1
+    cores = []
+    for k in range(d):
+        shape = (int(R[k]), int(I[k]), int(J[k]), int(R[k + 1]))
+        g = rng.standard_normal(int(np.prod(shape))).reshape(shape, order="F")
+        s = 1.0 if scale is None else (scale(k, shape) if callable(scale) else float(scale))
+        cores.append(g * s)
+    return cores
+
+
+def _right_orthogonal_core(rng, r, n, r2):
+    """r x n x 1 x r2 core whose r x (n r2) unfolding has orthonormal rows (needs r <= n r2)."""
+    G = rng.standard_normal((n * r2, r))
+    Qt, _ = np.linalg.qr(G)  # (n r2) x r orthonormal columns
+    return Qt.T.reshape(r, n, 1, r2, order="F")
+
+
+def orthogonal_mpo(seed, I1, dims, K, rank):
+    """A rows x K matrix with orthonormal columns as an MPO with K on site 1.
+
+    Site 1 is 1 x I1 x K x rank whose K x (I1 rank) matrix has orthonormal rows; sites 2..d are
+    right-orthogonal rank x I_k x 1 x rank' cores, with the last bonds shrunk so that every
+    unfolding can be right-orthogonal (rank' <= product of the remaining dims).
+    """
+    rng = np.random.default_rng(seed)
+    d = 1 + len(dims)
+    ranks = [1]
+    for k in range(1, d):
+        tail = int(np.prod(dims[k - 1:]))
+        ranks.append(min(rank, tail))
+    ranks.append(1)
+    G = rng.standard_normal((I1 * ranks[1], K))
+    Qt, _ = np.linalg.qr(G)  # (I1 R2) x K
+    site1 = Qt.T.reshape(K, I1, ranks[1], order="F").transpose(1, 0, 2)[None]  # (1, I1, K, R2)
+    cores = [site1.copy()]
+    for k in range(1, d):
+        cores.append(_right_orthogonal_core(rng, ranks[k], int(dims[k - 1]), ranks[k + 1]))
+    return cores
+
+
+def prescribed_mpo(seed_u, seed_v, I1, dims, K, rank, sigma):
+    """A = U diag(sigma) V^T with U, V from ``orthogonal_mpo`` (square: the same site dims).
+
+    Site 1: A_1(0, i, j, (a, b)) = sum_c U_1(0, i, c, a) sigma_c V_1(0, j, c, b); sites k >= 2:
+    A_k((a,b), i, j, (a',b')) = U_k(a, i, 0, a') V_k(b, j, 0, b'); bonds (a, b) -> a + R_U b.
+    The exact singular values of A are ``sigma`` (length K).
+    """
+    U = orthogonal_mpo(seed_u, I1, dims, K, rank)
+    V = orthogonal_mpo(seed_v, I1, dims, K, rank)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    cores = []
+    u, v = U[0][0], V[0][0]  # (I1, K, a), (J1, K, b)
+    c1 = np.einsum("ica,c,jcb->ijba", u, sigma, v)  # (I1, J1, b, a)
+    ra, rb = u.shape[2], v.shape[2]
+    cores.append(c1.reshape(I1, I1, rb * ra)[None].copy())  # (b, a) -> b*ra + a = a + ra*b
+    for uk, vk in zip(U[1:], V[1:]):
+        a1, n, _, a2 = uk.shape
+        b1, _, _, b2 = vk.shape
+        ck = np.einsum("aiu,bjv->baijvu", uk[:, :, 0, :], vk[:, :, 0, :])
+        cores.append(ck.reshape(b1 * a1, n, n, b2 * a2).copy())
+    return cores, U, V
+
+
+def banded_coo(seed, n, per_row, half_band):
+    """Sparse n x n matrix: each row i holds ``per_row`` distinct columns drawn uniformly from
+    [i - half_band, i + half_band] intersected with [0, n), values N(0,1); COO sorted by (row, col).
+    """
+    rng = np.random.default_rng(seed)
+    rows = np.arange(n, dtype=np.int64)
+    lo = np.maximum(rows - half_band, 0)
+    hi = np.minimum(rows + half_band, n - 1)
+    width = hi - lo + 1
+    assert width.min() >= per_row
+    cols = np.empty((n, per_row), dtype=np.int64)
+    todo = np.arange(n)
+    while todo.size:
+        u = rng.random((todo.size, per_row))
+        c = lo[todo, None] + np.floor(u * width[todo, None]).astype(np.int64)
+        c.sort(axis=1)
+        bad = (np.diff(c, axis=1) == 0).any(axis=1)
+        cols[todo[~bad]] = c[~bad]
+        todo = todo[bad]
+    vals = rng.standard_normal(n * per_row)
+    vals[vals == 0.0] = 1.0  # no signed zeros in the inputs
+    return np.repeat(rows, per_row), cols.reshape(-1), vals
+
+
+# Named configurations of the paper-shaped workloads.
+
+def c1_plain_fp64(seed=0):
+    """4096 x 4096 Gaussian MPO: d=6, I=J=4, ranks 3, N(0,1)/sqrt(4*3); k=10, p=10, q=1."""
+    d = 6
+    A = gaussian_mpo(seed, [4] * d, [4] * d, [1] + [3] * (d - 1) + [1], scale=1.0 / np.sqrt(12.0))
+    return dict(A=A, k=10, p=10, q=1, seed=seed, tol=1e-14, max_rank=0)
+
+
+def c2_prescribed(seed_u=0, seed_v=1, seed_omega=2, tol=1e-12, max_rank=32):
+    """2^20 x 2^20 MPO with sigma_j = 0.7^j (j < 32), built in merged layout (64, 4 x 7): U, V
+    orthogonal rank-5 MPOs; A ranks 25 (16 at the last bond); k=16, p=16, q=2."""
+    K = 32
+    sigma = 0.7 ** np.arange(K)
+    A, U, V = prescribed_mpo(seed_u, seed_v, 64, [4] * 7, K, 5, sigma)
+    return dict(A=A, k=16, p=16, q=2, seed=seed_omega, tol=tol, max_rank=max_rank, sigma=sigma)

@@ -1,0 +1,279 @@
+"""Benchmark: TNrSVD solves/s on one GB300 (or N replicas), with roofline and CPU-oracle baseline.
+
+Workload (one step = one full TNrSVD solve: merge check, Omega, every MPO product, every
+QR/rounding sweep and the final MPO-SVD): the 2^20 x 2^20 MPO with prescribed singular values
+sigma_j = 0.7^j (j < 32), built as U diag(sigma) V^T from orthogonal rank-5 MPOs in the merged
+layout (site dims 64, 4 x 7), k = 16, p = 16, q = 2 (the shape of the paper's Section 6.3
+prescribed-sigma experiment). Synthetic, seeded inputs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp64]
+Under torchrun (WORLD_SIZE > 1) every rank runs an independent replica of the same workload
+(a single solve does not shard); value = solves of all ranks / max time over ranks.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "TNrSVD solves/s (2^20 x 2^20 MPO, sigma_j = 0.7^j, k=16 p=16 q=2)"
+UNIT = "solves/s"
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
+
+
+def workload_config():
+    c = W.c2_prescribed()
+    cfg = {
+        "workload": "prescribed-sigma MPO 2^20 x 2^20 (merged sites 64,4^7; A ranks 25), k=16 p=16 q=2, seed 2",
+        "global_batch": 1,
+        "seq_len": 0,
+        "tol": c["tol"],
+        "max_rank": c["max_rank"],
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "replicas",
+    }
+    return c, cfg
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def run_oracle_sample(c, budget_s):
+    """Time the CPU oracle (as it stands) on the same workload: whole solves until ~budget_s."""
+    from oracle import tnrsvd as ot
+
+    n, t0 = 0, time.perf_counter()
+    S = None
+    while True:
+        _, S, _ = ot.tnrsvd(c["A"], c["k"], c["p"], c["q"], c["seed"], tol=c["tol"], max_rank=c["max_rank"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 50:
+            break
+    return n / el, n, el, S
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    c, cfg = workload_config()
+    for _ in range(args.warmup):
+        run_oracle_sample(c, 0.0)
+    t0 = time.perf_counter()
+    steps = 0
+    for _ in range(args.steps):
+        run_oracle_sample(c, 0.0)
+        steps += 1
+    el = time.perf_counter() - t0
+    v = steps / el
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} whole solves of the same workload (numpy/LAPACK FP64 oracle)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    c, cfg = workload_config()
+    A = T.Mpo.from_numpy(c["A"], device=dev)
+    precision = T.TNR_FP64
+    plan = T.SolvePlan(A, c["k"], c["p"], tol=c["tol"], max_rank=c["max_rank"], precision=precision)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(3, args.warmup)):
+        plan.run(c["q"], c["seed"])
+    torch.cuda.synchronize()
+
+    # dominant kernel class for the roofline: the FP64 Householder QR
+    classes = T.stats_classes()
+    qr_cls = classes.index("qr")
+    T.stats_reset()
+    T.stats_enable(1 << qr_cls)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(c["q"], c["seed"])
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches, _ = T.stats(-1)
+    qr_launches, qr_ms = T.stats(qr_cls)
+    qr_flops = T.stats_work(qr_cls)
+    T.stats_enable(0)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+
+    # accuracy of this run against the exact singular values
+    S = plan.S.cpu().numpy()
+    sv_err = float(np.linalg.norm(S - c["sigma"][: c["k"]]) / np.linalg.norm(c["sigma"][: c["k"]]))
+
+    # end to end through the public API with host buffers: H2D of the cores, solve, D2H of U, S, V
+    host_cores = [torch.from_numpy(np.ascontiguousarray(np.asarray(x).reshape(-1, order="F"))).pin_memory()
+                  for x in c["A"]]
+    h2d = sum(x.numel() * 8 for x in host_cores)
+    e2e_ms = 0.0
+    d2h = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for dst, src in zip(A.cores, host_cores):
+            dst.copy_(src, non_blocking=True)
+        plan.run(c["q"], c["seed"])
+        U, Sd, V = plan.outputs()
+        outs = [Sd] + [U.cores[i][: U.R[i] * U.I[i] * U.J[i] * U.R[i + 1]] for i in range(U.d)] + \
+               [V.cores[i][: V.R[i] * V.I[i] * V.J[i] * V.R[i + 1]] for i in range(V.d)]
+        host = [o.to("cpu", non_blocking=True) for o in outs]
+        e1.record(stream)
+        e1.synchronize()
+        d2h = sum(o.numel() * 8 for o in outs)
+        e2e_ms += e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+    del host
+
+    value = world * args.steps / (max_ms / 1000.0)
+    qr_avg_ms = qr_ms / max(qr_launches, 1)
+    achieved_gflops = (qr_flops / max(qr_launches, 1)) / (qr_avg_ms * 1e-3) / 1e9 if qr_launches else 0.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "e2e": {"value": world * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_qr_coop (FP64 Householder QR, explicit Q)", "bound": "alu",
+                     "achieved": achieved_gflops, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+                     "frac": achieved_gflops / FP64_NOMINAL_GFLOPS, "traffic": None,
+                     "launches_per_step": qr_launches / args.steps, "avg_launch_us": 1000 * qr_avg_ms,
+                     "share_of_step": qr_ms / max(total_ms, 1e-9)},
+        "accuracy": {"sv_rel_err_vs_exact": sv_err},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        rate, n, el, So = run_oracle_sample(c, args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{n} whole solves of the same workload in {el:.1f} s (numpy/LAPACK FP64)"}
+        line["accuracy"]["sv_rel_err_vs_oracle"] = float(np.linalg.norm(S - So) / np.linalg.norm(So))
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * tnrsvd.h - C ABI of the GB300 TNrSVD library (libtnrsvd.so).
+ *
+ * Implements the data-parallel path of "Computing low-rank approximations of large-scale
+ * matrices with the Tensor Network randomized SVD" (Batselier, Yu, Daniel, Wong):
+ * sparse matrix -> MPO conversion (Alg. 4.1), the MPO x MPO product (Section 5.2), MPO-QR
+ * with integrated rounding (Alg. 5.2 and Section 5.4), MPO-SVD (Alg. 5.3) and the randomized
+ * MPO subspace iteration (Alg. 5.4) that drives the rSVD of Alg. 5.1.
+ *
+ * Conventions (Section 2, Eq. (2.1); Section 3):
+ *  - Row and column multi-indices are column-major: row = i_1 + I_1 (i_2 + I_2 (i_3 + ...)).
+ *  - Core k of an MPO is R_k x I_k x J_k x R_{k+1}, stored contiguously in column-major order:
+ *    element (r, i, j, r') at offset r + R_k (i + I_k (j + J_k r')). R_1 = R_{d+1} = 1.
+ *  - A tall I x K matrix (Y, Q, U, V of Section 5) is an MPO whose site-1 core is
+ *    1 x I_1 x K x R_2 and whose other cores have J_k = 1 (Lemma 5.1, Algs. 5.2-5.3).
+ *  - All floating-point data is IEEE float64 unless a precision mode says otherwise.
+ *
+ * Ownership: the caller allocates every device buffer (cores, outputs, workspace) and owns
+ * it; the library never allocates device memory. Host-side descriptors are read during the
+ * call only. Work is enqueued on the caller's stream; calls that return host values
+ * (ranks, counts) synchronise that stream.
+ *
+ * Errors: every entry point returns TNR_OK (0) or a negative status. Argument errors are
+ * detected before any work is enqueued. Device-side failures (non-finite data, an exhausted
+ * bounded wait, an unsorted or duplicate COO entry) are recorded in a device status word and
+ * reported by the next call that synchronises. tnr_strerror() names a status.
+ */
+#ifndef TNRSVD_H
+#define TNRSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TNR_MAX_SITES 64
+
+enum tnr_status {
+  TNR_OK = 0,
+  TNR_EINVAL = -1,      /* inconsistent dims/ranks, K too large, bad pointer or size */
+  TNR_EDUP = -2,        /* duplicate (row, col) entry in the COO input */
+  TNR_ENOTSORTED = -3,  /* COO input not sorted by (row, col) */
+  TNR_ENONFINITE = -4,  /* NaN or Inf met in device data */
+  TNR_ENOMEM = -5,      /* workspace or output capacity too small */
+  TNR_ECUDA = -6,       /* a CUDA runtime call failed */
+  TNR_ETIMEOUT = -7,    /* a bounded device wait ran out */
+  TNR_ERANGE = -8       /* an index or count exceeds the supported range */
+};
+
+enum tnr_precision {
+  TNR_FP64 = 0,  /* every step in float64 */
+  TNR_MIXED = 1  /* products A*Omega, A^T Q, A Q on tensor cores (bf16 in, fp32 accumulate);
+                    B = Q^T A, the QR sweeps and the SVDs in float64 */
+};
+
+/* MPO descriptor (host memory). For inputs only d, I, J, R and core are read. For outputs
+ * the caller sets d, I, J, core and cap (capacity of each core buffer in elements); the
+ * library writes the achieved ranks into R. */
+typedef struct tnr_mpo {
+  int32_t d;
+  int32_t reserved;
+  int64_t I[TNR_MAX_SITES];
+  int64_t J[TNR_MAX_SITES];
+  int64_t R[TNR_MAX_SITES + 1];
+  double *core[TNR_MAX_SITES];
+  int64_t cap[TNR_MAX_SITES];
+} tnr_mpo;
+
+/* Rounding options (Section 5.4 integrates SVD-based rounding with the MPO-QR sweep).
+ * At each bond the smallest rank r >= 1 is kept whose discarded singular values satisfy
+ * sum s_l^2 <= delta^2, delta = tol * ||Y||_F / sqrt(d - 1); then r <= max_rank if max_rank > 0. */
+typedef struct tnr_opts {
+  int32_t precision;  /* enum tnr_precision */
+  int32_t reserved;
+  double tol;
+  int64_t max_rank;   /* 0: only the structural bounds of Thm 3.2 apply */
+} tnr_opts;
+
+/* ---------------------------------------------------------------------------------------
+ * Sparse -> MPO conversion, Alg. 4.1 (Section 4). The result is the block form of the
+ * rank-R MPO of Lemma 4.2: R nonzero I_1 x J_1 blocks X_t (column-major, block t at
+ * X + t*I_1*J_1, which is core A^(1)(0, i_1, j_1, t)), and for each block the digits
+ * i_2, j_2, ..., i_d, j_d of its block-row p and block-column q (mixed radix, site 2
+ * fastest) as uint8, row t of a R x 2(d-1) array. Blocks are ordered by (p, q), p major.
+ *
+ * Inputs: row, col (int64, device), val (float64, device), nnz entries sorted by (row, col)
+ * with no duplicates; nrows = prod I, ncols = prod J; I_1 * J_1 <= 4096, I_k, J_k <= 256
+ * for k >= 2; nnz < 2^31. Two phases (Section 4.2: the sizes are known a priori, so the
+ * caller preallocates): tnr_sparse_count() writes R to *R_out (synchronises); the caller
+ * allocates X (R*I_1*J_1 doubles) and digits (R*2(d-1) bytes); tnr_sparse_fill() writes
+ * them. Both take the same workspace, of at least tnr_sparse_workspace() bytes, whose
+ * contents must survive from count to fill. Errors: TNR_EINVAL (dims), TNR_ENOTSORTED,
+ * TNR_EDUP, TNR_ERANGE (an index outside the matrix), TNR_ENOMEM (workspace too small).
+ * ------------------------------------------------------------------------------------- */
+int tnr_sparse_workspace(int64_t nrows, int64_t ncols, int64_t nnz, int32_t d, const int64_t *I,
+                         const int64_t *J, size_t *bytes);
+int tnr_sparse_count(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row, const int64_t *col,
+                     int32_t d, const int64_t *I, const int64_t *J, int64_t *R_out, void *ws,
+                     size_t ws_bytes, void *stream);
+int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row, const int64_t *col,
+                    const double *val, int32_t d, const int64_t *I, const int64_t *J, int64_t R,
+                    double *X, uint8_t *digits, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * MPO x MPO product, Section 5.2: Y = op(A) X with op(A) = A (trans = 0) or A^T (trans = 1).
+ * X is a tall matrix MPO (site 1: 1 x n_1 x K x S_2, others S_k x n_k x 1 x S_{k+1}) whose
+ * row dims n_k equal J_k (trans = 0) or I_k (trans = 1). Per site
+ *   Y_k((r,s), i, c, (r',s')) = sum_j A_k(r,i,j,r') X_k(s,j,c,s')     (trans = 0)
+ * with product bonds numbered r + R_k s; ranks multiply. Y's descriptor: the caller sets
+ * core and cap; the library sets d, I, J, R. Precision: TNR_FP64 only through this entry
+ * (the mixed-precision products run inside tnr_solve). Errors: TNR_EINVAL, TNR_ENOMEM.
+ * ------------------------------------------------------------------------------------- */
+int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * MPO-QR with integrated rounding, Alg. 5.2 + Section 5.4, in place: Y (a tall matrix MPO,
+ * K columns on site 1, I_1 >= K) becomes Q with Q^T Q = I_K, and R_KxK (device, K*K
+ * doubles, column-major, upper triangular) receives R with Y = Q R up to the rounding.
+ * Steps: left-to-right Householder QR sweep (R factors absorbed to the right), right-to-left
+ * truncating SVD sweep (the rule of tnr_opts), then the site-1 QR of Alg. 5.2. Y's ranks
+ * are updated in Y->R. ws: at least tnr_orthogonalize_workspace() bytes. Synchronises.
+ * ------------------------------------------------------------------------------------- */
+int tnr_orthogonalize_workspace(const tnr_mpo *Y, size_t *bytes);
+int tnr_orthogonalize(tnr_mpo *Y, double *R_KxK, const tnr_opts *opts, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * TNrSVD, Alg. 5.4 + Alg. 5.3 driving Alg. 5.1: rank-k approximation A ~= U diag(S) V^T of
+ * the MPO A with oversampling p (K = k + p) and q power iterations. Leading sites are merged
+ * until I_1 >= K and J_1 >= K (Section 6.3); the random MPO Omega of Lemma 5.1 is drawn on
+ * the device from `seed` (SplitMix64 counter stream, Box-Muller normals; Omega^(1) first in
+ * column-major order, then the site vectors). Outputs: U (rows I, k columns on site 1) and
+ * V (rows J, k columns on site 1) over the merged sites, S (k doubles, device, descending).
+ * tnr_solve_query() fills the merged d, I, J and the per-core capacities (upper bounds) of U
+ * and V, and the workspace size; the caller allocates and sets U->core, V->core. On return
+ * U->R and V->R hold the achieved ranks. Synchronises (ranks are read back per bond).
+ * Errors: TNR_EINVAL (K > prod I or prod J, k < 1, q < 0), TNR_ENOMEM, TNR_ENONFINITE.
+ * ------------------------------------------------------------------------------------- */
+int tnr_solve_query(const tnr_mpo *A, int32_t k, int32_t p, const tnr_opts *opts, tnr_mpo *U_shape,
+                    tnr_mpo *V_shape, size_t *ws_bytes);
+int tnr_solve(const tnr_mpo *A, int32_t k, int32_t p, int32_t q, uint64_t seed, const tnr_opts *opts,
+              tnr_mpo *U, double *S, tnr_mpo *V, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Instrumentation (not part of the method): kernel launch counting and per-kernel-class
+ * device time, measured with CUDA events recorded on the launching stream around each
+ * launch while enabled. tnr_stats() synchronises and returns, for class `cls`, the number
+ * of launches and the summed device milliseconds since the last reset; cls = -1 returns the
+ * totals over all classes. tnr_stats_class_name() names a class (NULL past the last).
+ * ------------------------------------------------------------------------------------- */
+void tnr_stats_enable(int32_t class_mask); /* bit c: event-time class c */
+void tnr_stats_reset(void);
+int tnr_stats(int32_t cls, int64_t *launches, double *ms);
+/* Algorithmic work recorded for class cls (or all, cls = -1) since the last reset: flops for
+ * the FP64/tensor kernels (QR: dgeqrf + dorgqr counts; GEMM and products: 2 m n k), bytes
+ * for the conversion kernels (24 B per nonzero read, the block values and digits written). */
+int tnr_stats_work(int32_t cls, double *work);
+const char *tnr_stats_class_name(int32_t cls);
+
+const char *tnr_strerror(int status);
+int tnr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNRSVD_H */

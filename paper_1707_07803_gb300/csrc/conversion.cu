@@ -1,0 +1,366 @@
+// Sparse matrix -> MPO conversion (Alg. 4.1) in block form, on the GPU.
+//
+// Alg. 4.1 adds one rank-1 MPO per nonzero I1 x J1 block X of A: X on site 1 and unit
+// matrices E_{i_k j_k} on sites 2..d (Section 4.1). The MPO rank is the number of nonzero
+// blocks (Lemma 4.2), known before any value is written, so the conversion runs in two
+// phases (Section 4.2: preallocation): count the blocks, then fill them.
+//
+// Input: COO (row, col, val) sorted by (row, col), no duplicates. Entries of block-row
+// p = row / I1 form one contiguous segment. An entry is the "first occurrence" of its block
+// (p, q), q = col / J1, when it is the first entry of its row with that q and no earlier row
+// of the segment holds q (rows are sorted by col, so both tests are a neighbour compare and
+// binary searches). Blocks are numbered in (p, q) order: block index t of a first occurrence
+// = (#first occurrences before its segment) + (#distinct q' < q within the segment), the
+// latter read off a prefix count F of first-occurrence flags with one binary search per row.
+//
+// Kernels:
+//   k_first_scan  per entry: validate order/range, first-occurrence flag, tile-local exclusive
+//                 scan of the flags (1024 entries per CTA) -> F_local, tile totals
+//   k_tile_scan   one CTA: exclusive scan of the tile totals -> tile offsets, R
+//   k_fill        per first-occurrence entry: block index t, zero block t of X, scatter the
+//                 block's entries (gathered from the I1 rows of the segment), write digits.
+#include <cstdio>
+
+#include "tnr_internal.cuh"
+
+namespace tnr {
+namespace {
+
+constexpr int kTile = 1024;
+
+struct ConvDims {
+  int64_t nrows, ncols, nnz;
+  int64_t I1, J1;
+  int32_t d;
+  int32_t I[TNR_MAX_SITES];
+  int32_t J[TNR_MAX_SITES];
+};
+
+// Lower bound over entries [lo, hi) for the composite key (r, c).
+__device__ __forceinline__ int64_t lower_bound_rc(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+                                                  int64_t lo, int64_t hi, int64_t r, int64_t c) {
+  while (lo < hi) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    int64_t rm = __ldg(row + mid);
+    bool less = rm < r || (rm == r && __ldg(col + mid) < c);
+    if (less)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// First index in [0, e] whose row is >= rlo (entries sorted by row): gallop back from e.
+__device__ __forceinline__ int64_t segment_start(const int64_t *__restrict__ row, int64_t e, int64_t rlo) {
+  int64_t hi = e, step = 1, lo = e;
+  while (true) {
+    int64_t cand = e - step;
+    if (cand < 0) {
+      lo = 0;
+      break;
+    }
+    if (__ldg(row + cand) < rlo) {
+      lo = cand + 1;
+      break;
+    }
+    hi = cand;
+    step <<= 1;
+  }
+  // answer in [lo, hi]
+  while (lo < hi) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(row + mid) < rlo)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// First index in [e, nnz] whose row is >= rhi: gallop forward from e.
+__device__ __forceinline__ int64_t segment_end(const int64_t *__restrict__ row, int64_t nnz, int64_t e, int64_t rhi) {
+  int64_t lo = e, step = 1, hi = e;
+  while (true) {
+    int64_t cand = e + step;
+    if (cand >= nnz) {
+      hi = nnz;
+      break;
+    }
+    if (__ldg(row + cand) >= rhi) {
+      hi = cand;
+      break;
+    }
+    lo = cand;
+    step <<= 1;
+  }
+  while (lo < hi) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(row + mid) < rhi)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+                                                      ConvDims D, int32_t *__restrict__ F_local,
+                                                      int32_t *__restrict__ tile_total, int *status) {
+  __shared__ int32_t warp_sums[kTile / 32];
+  const int64_t e = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  int flag = 0;
+  if (e < D.nnz) {
+    const int64_t r = __ldg(row + e), c = __ldg(col + e);
+    bool ok = true;
+    if (r < 0 || r >= D.nrows || c < 0 || c >= D.ncols) {
+      set_status(status, TNR_ERANGE);
+      ok = false;
+    }
+    if (e > 0) {
+      const int64_t rp = __ldg(row + e - 1), cp = __ldg(col + e - 1);
+      if (rp > r || (rp == r && cp > c)) {
+        set_status(status, TNR_ENOTSORTED);
+        ok = false;
+      } else if (rp == r && cp == c) {
+        set_status(status, TNR_EDUP);
+        ok = false;
+      }
+    }
+    if (ok) {
+      const int64_t p = r / D.I1, q = c / D.J1;
+      bool first = true;
+      if (e > 0 && __ldg(row + e - 1) == r && __ldg(col + e - 1) / D.J1 == q) first = false;
+      if (first && r > p * D.I1) {
+        const int64_t s0 = segment_start(row, e, p * D.I1);
+        for (int64_t rr = p * D.I1; rr < r && first; ++rr) {
+          const int64_t x = lower_bound_rc(row, col, s0, e, rr, q * D.J1);
+          if (x < e && __ldg(row + x) == rr && __ldg(col + x) < (q + 1) * D.J1) first = false;
+        }
+      }
+      flag = first ? 1 : 0;
+    }
+  }
+  // CTA-wide exclusive scan of flag.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = flag;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = warp_sums[lane];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    warp_sums[lane] = wi - w;  // exclusive prefix of warp totals
+    if (lane == 31) tile_total[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  if (e < D.nnz) F_local[e] = warp_sums[warp] + incl - flag;
+}
+
+// Exclusive scan of the tile totals in place; writes the grand total to tile_off[ntiles].
+__global__ void __launch_bounds__(1024) k_tile_scan(int32_t *__restrict__ tile_off, int64_t ntiles) {
+  __shared__ int32_t warp_sums[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < ntiles; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    int v = i < ntiles ? tile_off[i] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int w = warp_sums[lane], wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      warp_sums[lane] = wi - w;
+    }
+    __syncthreads();
+    const int c0 = carry;
+    if (i < ntiles) tile_off[i] = c0 + warp_sums[warp] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = c0 + warp_sums[warp] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_off[ntiles] = carry;
+}
+
+__device__ __forceinline__ int64_t F_at(const int32_t *__restrict__ F_local, const int32_t *__restrict__ tile_off,
+                                        int64_t x, int64_t nnz) {
+  if (x >= nnz) return tile_off[cdiv(nnz, kTile)];
+  return (int64_t)__ldg(tile_off + x / kTile) + __ldg(F_local + x);
+}
+
+__global__ void __launch_bounds__(256) k_fill(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+                                              const double *__restrict__ val, ConvDims D,
+                                              const int32_t *__restrict__ F_local, const int32_t *__restrict__ tile_off,
+                                              double *__restrict__ X, uint8_t *__restrict__ digits, int64_t R,
+                                              int *status) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.nnz) return;
+  const int64_t Fe = F_at(F_local, tile_off, e, D.nnz);
+  if (F_at(F_local, tile_off, e + 1, D.nnz) == Fe) return;  // not a first occurrence
+  const int64_t r = __ldg(row + e), c = __ldg(col + e);
+  const int64_t p = r / D.I1, q = c / D.J1;
+  const int64_t r0 = p * D.I1;
+  const int64_t s0 = segment_start(row, e, r0);
+  const int64_t s1 = segment_end(row, D.nnz, e, r0 + D.I1);
+  // Rank of q among the distinct block-columns of this block-row.
+  int64_t rank = 0;
+  for (int64_t rr = r0; rr < r0 + D.I1; ++rr) {
+    const int64_t x0 = lower_bound_rc(row, col, s0, s1, rr, 0);
+    const int64_t xq = lower_bound_rc(row, col, x0, s1, rr, q * D.J1);
+    rank += F_at(F_local, tile_off, xq, D.nnz) - F_at(F_local, tile_off, x0, D.nnz);
+  }
+  const int64_t t = F_at(F_local, tile_off, s0, D.nnz) + rank;
+  if (t < 0 || t >= R) {  // caller's R disagrees with the count phase: write nothing
+    set_status(status, TNR_ERANGE);
+    return;
+  }
+  const int64_t bs = D.I1 * D.J1;
+  double *blk = X + t * bs;
+  if ((bs & 1) == 0) {
+    double2 z = make_double2(0.0, 0.0);
+    for (int64_t i = 0; i < bs; i += 2) *reinterpret_cast<double2 *>(blk + i) = z;
+  } else {
+    for (int64_t i = 0; i < bs; ++i) blk[i] = 0.0;
+  }
+  for (int64_t rr = r0; rr < r0 + D.I1; ++rr) {
+    int64_t x = lower_bound_rc(row, col, s0, s1, rr, q * D.J1);
+    while (x < s1 && __ldg(row + x) == rr) {
+      const int64_t cx = __ldg(col + x);
+      if (cx >= (q + 1) * D.J1) break;
+      blk[(rr - r0) + D.I1 * (cx - q * D.J1)] = __ldg(val + x);
+      ++x;
+    }
+  }
+  if (D.d > 1) {
+    uint8_t *dg = digits + t * 2 * (int64_t)(D.d - 1);
+    int64_t pp = p, qq = q;
+    for (int k = 1; k < D.d; ++k) {
+      dg[2 * (k - 1)] = (uint8_t)(pp % D.I[k]);
+      dg[2 * (k - 1) + 1] = (uint8_t)(qq % D.J[k]);
+      pp /= D.I[k];
+      qq /= D.J[k];
+    }
+  }
+}
+
+int make_dims(int64_t nrows, int64_t ncols, int64_t nnz, int32_t d, const int64_t *I, const int64_t *J, ConvDims *D) {
+  if (d < 1 || d > TNR_MAX_SITES || !I || !J || nrows < 1 || ncols < 1 || nnz < 0) return TNR_EINVAL;
+  if (nnz >= (int64_t(1) << 31)) return TNR_ERANGE;
+  __int128 pi = 1, pj = 1;
+  for (int k = 0; k < d; ++k) {
+    if (I[k] < 1 || J[k] < 1) return TNR_EINVAL;
+    if (k > 0 && (I[k] > 256 || J[k] > 256)) return TNR_EINVAL;
+    pi *= I[k];
+    pj *= J[k];
+    if (pi > ((__int128)1 << 62) || pj > ((__int128)1 << 62)) return TNR_EINVAL;
+    D->I[k] = (int32_t)(k > 0 ? I[k] : 0);
+    D->J[k] = (int32_t)(k > 0 ? J[k] : 0);
+  }
+  if (pi != nrows || pj != ncols) return TNR_EINVAL;
+  if (I[0] * J[0] > 4096) return TNR_EINVAL;
+  D->nrows = nrows;
+  D->ncols = ncols;
+  D->nnz = nnz;
+  D->I1 = I[0];
+  D->J1 = J[0];
+  D->d = d;
+  return TNR_OK;
+}
+
+size_t ws_bytes_for(int64_t nnz) {
+  const int64_t ntiles = cdiv(nnz, kTile);
+  return ((size_t(nnz) * 4 + 255) & ~size_t(255)) + ((size_t(ntiles + 1) * 4 + 255) & ~size_t(255));
+}
+
+}  // namespace
+}  // namespace tnr
+
+using namespace tnr;
+
+extern "C" int tnr_sparse_workspace(int64_t nrows, int64_t ncols, int64_t nnz, int32_t d, const int64_t *I,
+                                    const int64_t *J, size_t *bytes) {
+  ConvDims D;
+  TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
+  if (!bytes) return TNR_EINVAL;
+  *bytes = ws_bytes_for(nnz);
+  return TNR_OK;
+}
+
+extern "C" int tnr_sparse_count(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row, const int64_t *col,
+                                int32_t d, const int64_t *I, const int64_t *J, int64_t *R_out, void *ws,
+                                size_t ws_bytes, void *stream) {
+  ConvDims D;
+  TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
+  if (!R_out) return TNR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nnz == 0) {
+    *R_out = 0;
+    return TNR_OK;
+  }
+  if (!row || !col || !ws) return TNR_EINVAL;
+  if (ws_bytes < ws_bytes_for(nnz)) return TNR_ENOMEM;
+  const int64_t ntiles = cdiv(nnz, kTile);
+  int32_t *F_local = reinterpret_cast<int32_t *>(ws);
+  int32_t *tile_off = reinterpret_cast<int32_t *>((char *)ws + ((size_t(nnz) * 4 + 255) & ~size_t(255)));
+  TNR_TRY(reset_status(s));
+  {
+    LaunchScope ls(K_CONV_FLAGS, s);
+    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, status_ptr());
+  }
+  TNR_CK(cudaGetLastError());
+  {
+    LaunchScope ls(K_CONV_SCAN, s);
+    k_tile_scan<<<1, 1024, 0, s>>>(tile_off, ntiles);
+  }
+  TNR_CK(cudaGetLastError());
+  int32_t total = 0;
+  TNR_CK(cudaMemcpyAsync(&total, tile_off + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int st = read_status(s);  // synchronises
+  if (st != TNR_OK) return st;
+  *R_out = total;
+  return TNR_OK;
+}
+
+extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row, const int64_t *col,
+                               const double *val, int32_t d, const int64_t *I, const int64_t *J, int64_t R,
+                               double *X, uint8_t *digits, void *ws, size_t ws_bytes, void *stream) {
+  ConvDims D;
+  TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
+  if (nnz == 0 || R == 0) return TNR_OK;
+  if (!row || !col || !val || !X || !ws || (d > 1 && !digits) || R < 0) return TNR_EINVAL;
+  if (ws_bytes < ws_bytes_for(nnz)) return TNR_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t *F_local = reinterpret_cast<const int32_t *>(ws);
+  const int32_t *tile_off =
+      reinterpret_cast<const int32_t *>((const char *)ws + ((size_t(nnz) * 4 + 255) & ~size_t(255)));
+  // algorithmic bytes of the conversion: 24 B per nonzero read, values and digits written
+  stats_work(K_CONV_FILL, 24.0 * (double)nnz + (double)R * (8.0 * (double)(I[0] * J[0]) + 2.0 * (d - 1)));
+  {
+    LaunchScope ls(K_CONV_FILL, s);
+    k_fill<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R,
+                                                     status_ptr());
+  }
+  TNR_CK(cudaGetLastError());
+  return TNR_OK;
+}

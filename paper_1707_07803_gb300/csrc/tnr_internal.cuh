@@ -1,0 +1,118 @@
+// Internal helpers shared by the translation units of libtnrsvd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/tnrsvd.h"
+
+namespace tnr {
+
+// Device status word (one per device, in runtime.cu): the first device-side failure wins.
+// Kernels receive its address; status_ptr() returns it for the current device.
+int *status_ptr();
+
+__device__ __forceinline__ void set_status(int *st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// Iteration cap for every spin-wait on a flag written by another CTA. At ~1e3 cycles per
+// poll this bounds a wait to roughly a second at 2 GHz.
+constexpr long long kSpinCap = 2000000;
+
+// Kernel classes for launch counting and event timing.
+enum KClass : int {
+  K_CONV_ROWPTR = 0,
+  K_CONV_FLAGS,
+  K_CONV_SCAN,
+  K_CONV_FILL,
+  K_OMEGA,
+  K_MERGE,
+  K_CONTRACT,
+  K_CONTRACT_TC,
+  K_GEMM,
+  K_QR,
+  K_SVD,
+  K_MISC,
+  K_NUM_CLASSES
+};
+
+// Launch bookkeeping: call before/after each kernel launch on `s`.
+void stats_begin(int cls, cudaStream_t s);
+// Add algorithmic work (flops or bytes, per class) for the launch being recorded.
+void stats_work(int cls, double work);
+void stats_end(int cls, cudaStream_t s);
+
+struct LaunchScope {
+  int cls;
+  cudaStream_t s;
+  LaunchScope(int c, cudaStream_t st) : cls(c), s(st) { stats_begin(cls, s); }
+  ~LaunchScope() { stats_end(cls, s); }
+};
+
+// Bump allocator over the caller's workspace; with base == nullptr it only measures.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0;
+  size_t off = 0;
+  bool ok = true;
+  template <typename T>
+  T *take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    size_t at = off;
+    off += bytes;
+    if (base == nullptr) return nullptr;
+    if (off > size) {
+      ok = false;
+      return nullptr;
+    }
+    return reinterpret_cast<T *>(base + at);
+  }
+};
+
+int check_cuda(cudaError_t e);
+int read_status(cudaStream_t s);  // synchronises s, returns and clears the device status word
+int reset_status(cudaStream_t s);
+
+#define TNR_CK(expr)                                  \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return tnr::check_cuda(_e); \
+  } while (0)
+
+#define TNR_TRY(expr)           \
+  do {                          \
+    int _rc = (expr);           \
+    if (_rc != TNR_OK) return _rc; \
+  } while (0)
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- FP64 dense building blocks (column-major, explicit leading dimensions) ----
+
+// C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b], b = 0..batch-1 with element strides sa, sb, sc.
+int gemm_f64(cudaStream_t s, bool transA, bool transB, int64_t m, int64_t n, int64_t k, double alpha,
+             const double *A, int64_t lda, int64_t sa, const double *B, int64_t ldb, int64_t sb, double beta,
+             double *C, int64_t ldc, int64_t sc, int64_t batch = 1);
+
+// Thin Householder QR of the m x n matrix A (lda): A <- Q (m x min(m,n), explicit), Rout <- R
+// (min(m,n) x n, upper trapezoidal, ldr). Scratch from the arena: V (m x n), tau, flags.
+size_t qr_f64_scratch(int64_t m, int64_t n);
+// Scratch enough for any QR of an m x n matrix with m * n <= max_elems and n <= max_n.
+size_t qr_scratch_bound(int64_t max_elems, int64_t max_n);
+int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double *Rout, int64_t ldr,
+           void *scratch);
+
+// SVD of the n x n matrix G (ldg) by one-sided Jacobi: G <- U (columns), S (descending),
+// V (n x n, ldv) with G_in = U diag(S) V^T. `sweeps_out` (device int, may be null).
+size_t jacobi_scratch(int64_t n);
+int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S, double *V, int64_t ldv,
+                   void *scratch);
+
+// Small element-wise kernels.
+int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
+                    bool transpose);
+int scale_columns_f64(cudaStream_t s, double *A, int64_t lda, int64_t m, int64_t n, const double *scale);
+
+}  // namespace tnr

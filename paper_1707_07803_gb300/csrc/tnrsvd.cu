@@ -1,0 +1,703 @@
+// TNrSVD on the GPU: MPO products (Section 5.2), MPO-QR with integrated rounding (Alg. 5.2,
+// Section 5.4), MPO-SVD (Alg. 5.3) and the randomized MPO subspace iteration (Alg. 5.4).
+//
+// Host code orders the per-site steps (the sweeps are sequential over sites); every step
+// runs in this library's kernels. Bond ranks chosen by the truncation are read back to the
+// host after each bond so the next launch is sized exactly.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tnr_internal.cuh"
+
+namespace tnr {
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------------------
+
+// Per-site product, Section 5.2. Output core (R*S, Xo, Kx, R2*S2) with bonds r + R s.
+//   trans = 0: Y((r,s), i, c, (r',s')) = sum_j A(r,i,j,r') X(s,j,c,s')
+//   trans = 1: Y((r,s), j, c, (r',s')) = sum_i A(r,i,j,r') X(s,i,c,s')
+struct ContractDims {
+  int64_t R, I, J, R2;  // A core
+  int64_t S, Kx, S2;    // X core (row dim = J or I)
+  int trans;
+};
+
+__global__ void k_contract(const double *__restrict__ A, const double *__restrict__ X, double *__restrict__ Y,
+                           ContractDims D) {
+  const int64_t Xo = D.trans ? D.J : D.I;
+  const int64_t Ny = D.trans ? D.I : D.J;
+  const int64_t RS = D.R * D.S, RS2 = D.R2 * D.S2;
+  const int64_t total = RS * Xo * D.Kx * RS2;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx;
+    const int64_t rs = t % RS;
+    t /= RS;
+    const int64_t xo = t % Xo;
+    t /= Xo;
+    const int64_t c = t % D.Kx;
+    const int64_t rs2 = t / D.Kx;
+    const int64_t r = rs % D.R, s = rs / D.R;
+    const int64_t r2 = rs2 % D.R2, s2 = rs2 / D.R2;
+    // A(r, i, j, r2) at r + R(i + I(j + J r2)); X(s, y, c, s2) at s + S(y + Ny(c + Kx s2))
+    const double *xp = X + s + D.S * (Ny * (c + D.Kx * s2));
+    double acc = 0.0;
+    if (!D.trans) {
+      const double *ap = A + r + D.R * (xo + D.I * (D.J * r2));
+      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[D.R * D.I * y], xp[D.S * y], acc);
+    } else {
+      const double *ap = A + r + D.R * (D.I * (xo + D.J * r2));
+      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[D.R * y], xp[D.S * y], acc);
+    }
+    Y[idx] = acc;
+  }
+}
+
+// One step of the leading-site merge (Section 6.3): T (nr x nc x R) with core (R, I, J, R2)
+// gives T' ((nr I) x (nc J) x R2), rows (a, i) -> a + nr i, columns (b, j) -> b + nc j.
+__global__ void k_merge(const double *__restrict__ T, int64_t nr, int64_t nc, int64_t R, const double *__restrict__ C,
+                        int64_t I, int64_t J, int64_t R2, double *__restrict__ out) {
+  const int64_t NR = nr * I, NC = nc * J, total = NR * NC * R2;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx % NR, col = (idx / NR) % NC, s = idx / (NR * NC);
+    const int64_t a = row % nr, i = row / nr, b = col % nc, j = col / nc;
+    double acc = 0.0;
+    for (int64_t r = 0; r < R; ++r) acc = fma(T[a + nr * (b + nc * r)], C[r + R * (i + I * (j + J * s))], acc);
+    out[idx] = acc;
+  }
+}
+
+// Lemma 5.1 random MPO: SplitMix64 counter stream, uniforms ((z >> 11) + 1) 2^-53 in (0, 1],
+// Box-Muller cosine branch, normal m from uniforms 2m and 2m+1.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_omega(uint64_t seed, int64_t count, double *out) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < count; m += (int64_t)gridDim.x * blockDim.x) {
+    const double u1 = (double)((splitmix64_at(seed, 2 * m) >> 11) + 1) * 0x1.0p-53;
+    const double u2 = (double)((splitmix64_at(seed, 2 * m + 1) >> 11) + 1) * 0x1.0p-53;
+    out[m] = sqrt(-2.0 * log(u1)) * cos((2.0 * M_PI) * u2);
+  }
+}
+
+// Site-1 permutation of Algs. 5.2/5.3: core (1, I1, K, t) <-> matrix A1^T of size (I1 t) x K,
+// element (i + I1 r, c) <-> core (i, c, r). dir = 0: core -> matrix. dir = 1: matrix -> core,
+// keeping only columns c < kout (core (1, I1, kout, t)).
+__global__ void k_site1_perm(const double *__restrict__ src, double *__restrict__ dst, int64_t I1, int64_t K,
+                             int64_t t, int64_t kout, int dir) {
+  const int64_t total = dir == 0 ? I1 * K * t : I1 * kout * t;
+  const int64_t kk = dir == 0 ? K : kout;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % I1, c = (idx / I1) % kk, r = idx / (I1 * kk);
+    const int64_t mi = (i + I1 * r) + (I1 * t) * c;
+    if (dir == 0)
+      dst[mi] = src[idx];
+    else
+      dst[idx] = src[mi];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_norm2(const double *__restrict__ x, int64_t n, double *out, int *status) {
+  __shared__ double red[32];
+  double s = 0.0;
+  bool bad = false;
+  for (int64_t i = threadIdx.x; i < n; i += 1024) {
+    const double v = x[i];
+    if (!isfinite(v)) bad = true;
+    s = fma(v, v, s);
+  }
+  if (bad) set_status(status, TNR_ENONFINITE);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 32; ++w) t += red[w];
+    *out = t;
+  }
+}
+
+// Truncation rule: delta^2 = tol^2 ||Y||^2 / (d - 1); keep the smallest r >= 1 with
+// sum_{l >= r} s_l^2 <= delta^2, then r <= max_rank.
+__global__ void k_trunc(const double *__restrict__ S, int64_t n, const double *norm2, double tol, int64_t dm1,
+                        int64_t max_rank, int64_t *r_out, int *status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double delta2 = dm1 > 0 ? tol * tol * (*norm2) / (double)dm1 : 0.0;
+  double tail = 0.0;
+  int64_t r = n;
+  // tail(r) = sum_{l >= r} s_l^2, computed from the back (same order as the definition)
+  for (int64_t cand = n - 1; cand >= 1; --cand) {
+    tail += S[cand] * S[cand];
+    if (tail <= delta2)
+      r = cand;
+    else
+      break;
+  }
+  for (int64_t l = 0; l < n; ++l)
+    if (!isfinite(S[l])) set_status(status, TNR_ENONFINITE);
+  if (max_rank > 0 && r > max_rank) r = max_rank;
+  if (r < 1) r = 1;
+  *r_out = r;
+}
+
+int grid_for(int64_t work, int threads = 256) {
+  int64_t g = cdiv(work, threads);
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side MPO helpers
+// ---------------------------------------------------------------------------------------
+int64_t core_elems(const tnr_mpo &M, int k) { return M.R[k] * M.I[k] * M.J[k] * M.R[k + 1]; }
+
+int validate_input(const tnr_mpo *A) {
+  if (!A || A->d < 1 || A->d > TNR_MAX_SITES) return TNR_EINVAL;
+  if (A->R[0] != 1 || A->R[A->d] != 1) return TNR_EINVAL;
+  for (int k = 0; k < A->d; ++k) {
+    if (A->I[k] < 1 || A->J[k] < 1 || A->R[k + 1] < 1 || !A->core[k]) return TNR_EINVAL;
+  }
+  return TNR_OK;
+}
+
+struct Bufs {
+  double *tmp = nullptr;    // GEMM / copy staging, max core
+  double *Rbuf = nullptr;   // R factors
+  double *Mq = nullptr;     // matrix copies for QR-of-SVD
+  double *Rm = nullptr;     // small square factors
+  double *G = nullptr;      // Jacobi input/U
+  double *Vr = nullptr;     // Jacobi V
+  double *Sv = nullptr;     // singular values
+  double *US = nullptr;     // U * S
+  void *qr = nullptr;       // QR scratch
+  void *jac = nullptr;      // Jacobi scratch
+  double *norm2 = nullptr;  // device scalar
+  int64_t *rdev = nullptr;  // device rank
+};
+
+struct Limits {
+  int64_t maxcore = 1;  // elements of the largest core
+  int64_t maxbond = 1;  // largest bond
+  int64_t maxrows = 1;  // largest row count of an L->R QR
+  int64_t maxsq = 1;    // largest square factor side
+};
+
+void carve(Arena &ar, const Limits &L, Bufs &b) {
+  b.tmp = ar.take<double>(L.maxcore);
+  b.Rbuf = ar.take<double>(L.maxbond * L.maxbond);
+  b.Mq = ar.take<double>(L.maxcore);
+  b.Rm = ar.take<double>(L.maxsq * L.maxsq);
+  b.G = ar.take<double>(L.maxsq * L.maxsq);
+  b.Vr = ar.take<double>(L.maxsq * L.maxsq);
+  b.Sv = ar.take<double>(L.maxsq);
+  b.US = ar.take<double>(L.maxcore);
+  // every QR factors a core-sized matrix (m * n <= maxcore) with n <= max(maxbond, maxsq)
+  b.qr = ar.take<char>(qr_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq)));
+  b.jac = ar.take<char>(std::max<size_t>(jacobi_scratch(L.maxsq), 256));
+  b.norm2 = ar.take<double>(1);
+  b.rdev = ar.take<int64_t>(1);
+}
+
+int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
+  TNR_CK(cudaMemcpyAsync(r, rdev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int st = read_status(s);
+  return st;
+}
+
+// Left-to-right Householder QR sweep (rounding part 1, Section 5.4): core k reshaped
+// (R_k I_k J_k) x R_{k+1} = Q R; Q replaces the core, R is absorbed into core k+1.
+int sweep_lr(cudaStream_t s, tnr_mpo &Y, Bufs &b) {
+  for (int k = 0; k + 1 < Y.d; ++k) {
+    const int64_t rows = Y.R[k] * Y.I[k] * Y.J[k], cols = Y.R[k + 1];
+    const int64_t n = std::min(rows, cols);
+    TNR_TRY(qr_f64(s, Y.core[k], rows, cols, rows, b.Rbuf, n, b.qr));
+    const int64_t w = Y.I[k + 1] * Y.J[k + 1] * Y.R[k + 2];
+    TNR_TRY(gemm_f64(s, false, false, n, w, cols, 1.0, b.Rbuf, n, 0, Y.core[k + 1], cols, 0, 0.0, b.tmp, n, 0));
+    TNR_CK(cudaMemcpyAsync(Y.core[k + 1], b.tmp, sizeof(double) * n * w, cudaMemcpyDeviceToDevice, s));
+    Y.R[k + 1] = n;
+  }
+  return TNR_OK;
+}
+
+// Truncated SVD of M (t x w, ld t) for the right-to-left sweep: writes V^T[:r] (r x w) into
+// `core_out`, U[:, :r] diag(S[:r]) (t x r, ld t) into b.US, returns r.
+int svd_trunc(cudaStream_t s, const double *M, int64_t t, int64_t w, double tol, int64_t dm1, int64_t max_rank,
+              double *core_out, Bufs &b, int64_t *r_out) {
+  int64_t r = 0;
+  if (t >= w) {
+    TNR_TRY(copy_matrix_f64(s, M, t, b.Mq, t, t, w, false));
+    TNR_TRY(qr_f64(s, b.Mq, t, w, t, b.Rm, w, b.qr));  // Mq <- Q_m (t x w), Rm (w x w)
+    TNR_TRY(jacobi_svd_f64(s, b.Rm, w, w, b.Sv, b.Vr, w, b.jac));  // Rm <- U_r
+    {
+      LaunchScope ls(K_MISC, s);
+      k_trunc<<<1, 32, 0, s>>>(b.Sv, w, b.norm2, tol, dm1, max_rank, b.rdev, status_ptr());
+    }
+    TNR_TRY(d2h_rank(s, b.rdev, &r));
+    TNR_TRY(copy_matrix_f64(s, b.Vr, w, core_out, r, r, w, true));  // V_r[:, :r]^T
+    TNR_TRY(scale_columns_f64(s, b.Rm, w, w, r, b.Sv));
+    TNR_TRY(gemm_f64(s, false, false, t, r, w, 1.0, b.Mq, t, 0, b.Rm, w, 0, 0.0, b.US, t, 0));
+  } else {
+    TNR_TRY(copy_matrix_f64(s, M, t, b.Mq, w, w, t, true));  // M^T (w x t)
+    TNR_TRY(qr_f64(s, b.Mq, w, t, w, b.Rm, t, b.qr));  // Mq <- Q_m (w x t), Rm (t x t)
+    TNR_TRY(copy_matrix_f64(s, b.Rm, t, b.G, t, t, t, true));  // G = Rm^T
+    TNR_TRY(jacobi_svd_f64(s, b.G, t, t, b.Sv, b.Vr, t, b.jac));  // G <- U
+    {
+      LaunchScope ls(K_MISC, s);
+      k_trunc<<<1, 32, 0, s>>>(b.Sv, t, b.norm2, tol, dm1, max_rank, b.rdev, status_ptr());
+    }
+    TNR_TRY(d2h_rank(s, b.rdev, &r));
+    // V^T[:r] = V_r[:, :r]^T Q_m^T  (r x w)
+    TNR_TRY(gemm_f64(s, true, true, r, w, t, 1.0, b.Vr, t, 0, b.Mq, w, 0, 0.0, core_out, r, 0));
+    TNR_TRY(scale_columns_f64(s, b.G, t, t, r, b.Sv));
+    TNR_TRY(copy_matrix_f64(s, b.G, t, b.US, t, t, r, false));
+  }
+  *r_out = r;
+  return TNR_OK;
+}
+
+// Right-to-left truncating sweep (rounding part 2 fused with the loop of Alg. 5.2).
+int sweep_rl(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, Bufs &b) {
+  if (Y.d < 2) return TNR_OK;
+  {
+    LaunchScope ls(K_MISC, s);
+    k_norm2<<<1, 1024, 0, s>>>(Y.core[Y.d - 1], core_elems(Y, Y.d - 1), b.norm2, status_ptr());
+  }
+  TNR_CK(cudaGetLastError());
+  for (int k = Y.d - 1; k >= 1; --k) {
+    const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
+    int64_t r = 0;
+    TNR_TRY(svd_trunc(s, Y.core[k], t, w, tol, Y.d - 1, max_rank, b.tmp, b, &r));
+    TNR_CK(cudaMemcpyAsync(Y.core[k], b.tmp, sizeof(double) * r * w, cudaMemcpyDeviceToDevice, s));
+    const int64_t rows = Y.R[k - 1] * Y.I[k - 1] * Y.J[k - 1];
+    TNR_TRY(gemm_f64(s, false, false, rows, r, t, 1.0, Y.core[k - 1], rows, 0, b.US, t, 0, 0.0, b.tmp, rows, 0));
+    TNR_CK(cudaMemcpyAsync(Y.core[k - 1], b.tmp, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));
+    Y.R[k] = r;
+  }
+  return TNR_OK;
+}
+
+int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64_t K, int64_t t, int64_t kout,
+               int dir) {
+  LaunchScope ls(K_MISC, s);
+  k_site1_perm<<<grid_for(I1 * K * t), 256, 0, s>>>(src, dst, I1, K, t, kout, dir);
+  return check_cuda(cudaGetLastError());
+}
+
+// MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
+// columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
+int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b) {
+  TNR_TRY(sweep_lr(s, Y, b));
+  TNR_TRY(sweep_rl(s, Y, tol, max_rank, b));
+  const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
+  const int64_t m = I1 * t;
+  if (m < K) return TNR_EINVAL;
+  TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
+  TNR_TRY(qr_f64(s, b.Mq, m, K, m, b.Rm, K, b.qr));  // A1^T = Q~ R~
+  if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
+  TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
+  return TNR_OK;
+}
+
+// MPO-SVD (Alg. 5.3 + Section 5.4) of B = Z^T, Z a tall matrix MPO (rows J, K columns on
+// site 1). Writes W (K x K) into Wout, S (K) into Sout, and V^(1) restricted to the first
+// kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
+int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
+                 double *V1, int64_t kout, int64_t v1cap) {
+  TNR_TRY(sweep_lr(s, Z, b));
+  TNR_TRY(sweep_rl(s, Z, tol, max_rank, b));
+  const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
+  const int64_t m = J1 * t;
+  if (m < K) return TNR_EINVAL;
+  if (J1 * kout * t > v1cap) return TNR_ENOMEM;
+  TNR_TRY(site1_perm(s, Z.core[0], b.Mq, J1, K, t, K, 0));  // M^T ((J1 t) x K)
+  TNR_TRY(qr_f64(s, b.Mq, m, K, m, b.Rm, K, b.qr));         // M^T = Q~ R~
+  TNR_TRY(copy_matrix_f64(s, b.Rm, K, Wout, K, K, K, true));  // R~^T
+  TNR_TRY(jacobi_svd_f64(s, Wout, K, K, Sout, b.Vr, K, b.jac));  // R~^T = W S Zr^T
+  // V = Q~ Zr ((J1 t) x K), then V^(1) columns < kout
+  TNR_TRY(gemm_f64(s, false, false, m, K, K, 1.0, b.Mq, m, 0, b.Vr, K, 0, 0.0, b.US, m, 0));
+  TNR_TRY(site1_perm(s, b.US, V1, J1, K, t, kout, 1));
+  return TNR_OK;
+}
+
+int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X, tnr_mpo &Y) {
+  Y.d = A.d;
+  Y.R[0] = 1;
+  for (int k = 0; k < A.d; ++k) {
+    ContractDims D;
+    D.R = A.R[k];
+    D.I = A.I[k];
+    D.J = A.J[k];
+    D.R2 = A.R[k + 1];
+    D.S = X.R[k];
+    D.Kx = X.J[k];
+    D.S2 = X.R[k + 1];
+    D.trans = trans;
+    const int64_t Xo = trans ? A.J[k] : A.I[k];
+    const int64_t Ny = trans ? A.I[k] : A.J[k];
+    if (X.I[k] != Ny) return TNR_EINVAL;
+    const int64_t total = D.R * D.S * Xo * D.Kx * D.R2 * D.S2;
+    if (total > Y.cap[k]) return TNR_ENOMEM;
+    Y.I[k] = Xo;
+    Y.J[k] = D.Kx;
+    Y.R[k + 1] = D.R2 * D.S2;
+    stats_work(K_CONTRACT, 2.0 * (double)total * (double)Ny);
+    LaunchScope ls(K_CONTRACT, s);
+    k_contract<<<grid_for(total), 256, 0, s>>>(A.core[k], X.core[k], Y.core[k], D);
+    TNR_CK(cudaGetLastError());
+  }
+  return TNR_OK;
+}
+
+// Structural bound of bond b (1..d-1) of a (prod dims) x K matrix MPO with K on site 1.
+int64_t tall_bound(const int64_t *dims, int d, int64_t K, int b) {
+  double left = (double)K, right = 1.0;
+  for (int i = 0; i < b; ++i) left *= (double)dims[i];
+  for (int i = b; i < d; ++i) right *= (double)dims[i];
+  double v = std::min(left, right);
+  return v > 4e18 ? (int64_t)4e18 : (int64_t)v;
+}
+
+// The merged operator A' (Section 6.3) and the plan of every buffer of a solve.
+struct Plan {
+  int m = 1;  // sites merged into site 1
+  int d = 0;  // sites after the merge
+  int64_t I[TNR_MAX_SITES], J[TNR_MAX_SITES], RA[TNR_MAX_SITES + 1];
+  int64_t sq[TNR_MAX_SITES + 1];  // cap of Q bonds (max of the I- and J-side bounds)
+  int64_t pcap[TNR_MAX_SITES];    // product core capacity
+  int64_t omega_len = 0;
+  int64_t merged_elems = 0;
+  Limits L;
+};
+
+int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
+  TNR_TRY(validate_input(A));
+  if (K < 1) return TNR_EINVAL;
+  double pi = 1, pj = 1;
+  int m = 0;
+  for (int k = 0; k < A->d; ++k) {
+    pi *= (double)A->I[k];
+    pj *= (double)A->J[k];
+    if (pi >= (double)K && pj >= (double)K) {
+      m = k + 1;
+      break;
+    }
+  }
+  if (m == 0) return TNR_EINVAL;
+  P.m = m;
+  P.d = A->d - m + 1;
+  P.I[0] = 1;
+  P.J[0] = 1;
+  for (int k = 0; k < m; ++k) {
+    P.I[0] *= A->I[k];
+    P.J[0] *= A->J[k];
+  }
+  P.RA[0] = 1;
+  P.RA[1] = A->R[m];
+  for (int k = 1; k < P.d; ++k) {
+    P.I[k] = A->I[m - 1 + k];
+    P.J[k] = A->J[m - 1 + k];
+    P.RA[k + 1] = A->R[m + k];
+  }
+  const int64_t maxr = o ? o->max_rank : 0;
+  P.sq[0] = 1;
+  P.sq[P.d] = 1;
+  for (int b = 1; b < P.d; ++b) {
+    int64_t v = std::max(tall_bound(P.I, P.d, K, b), tall_bound(P.J, P.d, K, b));
+    if (maxr > 0) v = std::min(v, maxr);
+    P.sq[b] = v;
+  }
+  P.L = Limits();
+  for (int k = 0; k < P.d; ++k) {
+    const int64_t X = std::max(P.I[k], P.J[k]);
+    const int64_t Kx = k == 0 ? K : 1;
+    const int64_t b0 = P.RA[k] * P.sq[k], b1 = P.RA[k + 1] * P.sq[k + 1];
+    const double cap = (double)b0 * (double)X * (double)Kx * (double)b1;
+    if (cap > 2e9) return TNR_ENOMEM;  // product core over 16 GB: outside the supported sizes
+    P.pcap[k] = (int64_t)cap;
+    P.L.maxcore = std::max(P.L.maxcore, P.pcap[k]);
+    P.L.maxbond = std::max(P.L.maxbond, std::max(b0, b1));
+    P.L.maxrows = std::max(P.L.maxrows, b0 * X * Kx);
+  }
+  // square factors: min(t, w) of the R->L SVDs and K of the site-1 step
+  P.L.maxsq = std::max<int64_t>(K, 1);
+  for (int k = 1; k < P.d; ++k) {
+    const int64_t X = std::max(P.I[k], P.J[k]);
+    const int64_t t = P.RA[k] * P.sq[k], w = X * P.RA[k + 1] * P.sq[k + 1];
+    P.L.maxsq = std::max(P.L.maxsq, std::min(t, w));
+  }
+  P.L.maxcore = std::max(P.L.maxcore, std::max(P.I[0], P.J[0]) * K * P.L.maxbond);
+  if (P.L.maxsq > 1024) return TNR_ENOMEM;  // Jacobi kernel limit
+  P.omega_len = P.J[0] * K;
+  for (int k = 1; k < P.d; ++k) P.omega_len += P.J[k];
+  P.merged_elems = 0;
+  if (m > 1) {
+    int64_t nr = A->I[0], nc = A->J[0];
+    for (int k = 1; k < m; ++k) {
+      nr *= A->I[k];
+      nc *= A->J[k];
+      P.merged_elems = std::max(P.merged_elems, nr * nc * A->R[k + 1]);
+    }
+  }
+  return TNR_OK;
+}
+
+struct SolveBufs {
+  double *merged = nullptr, *merge_tmp = nullptr;
+  double *omega = nullptr;
+  double *P0[TNR_MAX_SITES], *P1[TNR_MAX_SITES];
+  double *W = nullptr, *S = nullptr;
+  Bufs b;
+};
+
+void carve_solve(Arena &ar, const Plan &P, int64_t K, SolveBufs &sb) {
+  if (P.m > 1) {
+    sb.merged = ar.take<double>(P.merged_elems);
+    sb.merge_tmp = ar.take<double>(P.merged_elems);
+  }
+  sb.omega = ar.take<double>(P.omega_len);
+  for (int k = 0; k < P.d; ++k) sb.P0[k] = ar.take<double>(P.pcap[k]);
+  for (int k = 0; k < P.d; ++k) sb.P1[k] = ar.take<double>(P.pcap[k]);
+  sb.W = ar.take<double>(K * K);
+  sb.S = ar.take<double>(K);
+  carve(ar, P.L, sb.b);
+}
+
+int merge_leading(cudaStream_t s, const tnr_mpo *A, const Plan &P, SolveBufs &sb, double **out) {
+  if (P.m == 1) {
+    *out = A->core[0];
+    return TNR_OK;
+  }
+  // T starts as core 1 (I1 x J1 x R2); ping-pong so the last step lands in sb.merged.
+  const double *T = A->core[0];
+  int64_t nr = A->I[0], nc = A->J[0], R = A->R[1];
+  for (int k = 1; k < P.m; ++k) {
+    double *dst = ((P.m - 1 - k) % 2 == 0) ? sb.merged : sb.merge_tmp;
+    const int64_t total = nr * A->I[k] * nc * A->J[k] * A->R[k + 1];
+    {
+      LaunchScope ls(K_MERGE, s);
+      k_merge<<<grid_for(total), 256, 0, s>>>(T, nr, nc, R, A->core[k], A->I[k], A->J[k], A->R[k + 1], dst);
+    }
+    TNR_CK(cudaGetLastError());
+    T = dst;
+    nr *= A->I[k];
+    nc *= A->J[k];
+    R = A->R[k + 1];
+  }
+  *out = sb.merged;
+  return TNR_OK;
+}
+
+int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q, uint64_t seed, const tnr_opts *o,
+               tnr_mpo *U, double *S, tnr_mpo *V, void *ws, size_t ws_bytes) {
+  if (k < 1 || p < 0 || q < 0 || !U || !V || !S || !o) return TNR_EINVAL;
+  if (o->precision != TNR_FP64 && o->precision != TNR_MIXED) return TNR_EINVAL;
+  const int64_t K = (int64_t)k + p;
+  Plan P;
+  TNR_TRY(make_plan(A, K, o, P));
+  Arena ar;
+  ar.base = static_cast<char *>(ws);
+  ar.size = ws_bytes;
+  SolveBufs sb;
+  carve_solve(ar, P, K, sb);
+  if (!ar.ok || !ws) return TNR_ENOMEM;
+  // output capacities
+  if (U->d != P.d || V->d != P.d) return TNR_EINVAL;
+  TNR_TRY(reset_status(s));
+
+  // A' : merged operator
+  tnr_mpo Am;
+  memset(&Am, 0, sizeof(Am));
+  Am.d = P.d;
+  for (int i = 0; i < P.d; ++i) {
+    Am.I[i] = P.I[i];
+    Am.J[i] = P.J[i];
+    Am.R[i] = P.RA[i];
+    Am.core[i] = i == 0 ? nullptr : A->core[P.m - 1 + i];
+  }
+  Am.R[P.d] = 1;
+  TNR_TRY(merge_leading(s, A, P, sb, &Am.core[0]));
+
+  // Omega, Lemma 5.1
+  {
+    LaunchScope ls(K_OMEGA, s);
+    k_omega<<<grid_for(P.omega_len), 256, 0, s>>>(seed, P.omega_len, sb.omega);
+  }
+  TNR_CK(cudaGetLastError());
+  tnr_mpo Om;
+  memset(&Om, 0, sizeof(Om));
+  Om.d = P.d;
+  {
+    int64_t pos = 0;
+    for (int i = 0; i < P.d; ++i) {
+      Om.I[i] = P.J[i];
+      Om.J[i] = i == 0 ? K : 1;
+      Om.R[i] = 1;
+      Om.core[i] = sb.omega + pos;
+      pos += i == 0 ? P.J[0] * K : P.J[i];
+    }
+    Om.R[P.d] = 1;
+  }
+  tnr_mpo Y0, Y1;
+  memset(&Y0, 0, sizeof(Y0));
+  memset(&Y1, 0, sizeof(Y1));
+  for (int i = 0; i < P.d; ++i) {
+    Y0.core[i] = sb.P0[i];
+    Y0.cap[i] = P.pcap[i];
+    Y1.core[i] = sb.P1[i];
+    Y1.cap[i] = P.pcap[i];
+  }
+  // Alg. 5.4
+  TNR_TRY(contract_impl(s, Am, 0, Om, Y0));
+  TNR_TRY(orthogonalize_impl(s, Y0, nullptr, o->tol, o->max_rank, sb.b));
+  for (int it = 0; it < q; ++it) {
+    TNR_TRY(contract_impl(s, Am, 1, Y0, Y1));
+    TNR_TRY(orthogonalize_impl(s, Y1, nullptr, o->tol, o->max_rank, sb.b));
+    TNR_TRY(contract_impl(s, Am, 0, Y1, Y0));
+    TNR_TRY(orthogonalize_impl(s, Y0, nullptr, o->tol, o->max_rank, sb.b));
+  }
+  // B = Q^T A as Z = A^T Q, then Alg. 5.3
+  TNR_TRY(contract_impl(s, Am, 1, Y0, Y1));
+  {
+    // V^(1) goes straight into the caller's V core 1.
+    TNR_TRY(mpo_svd_impl(s, Y1, o->tol, o->max_rank, sb.b, sb.W, sb.S, V->core[0], k, V->cap[0]));
+  }
+  // Outputs. U = Q x_3 W^T on site 1 (Section 5.4), first k columns.
+  {
+    const int64_t I1 = Y0.I[0], t = Y0.R[1];
+    if (I1 * k * t > U->cap[0]) return TNR_ENOMEM;
+    TNR_TRY(gemm_f64(s, false, false, I1, k, K, 1.0, Y0.core[0], I1, I1 * K, sb.W, K, 0, 0.0, U->core[0], I1, I1 * k,
+                     t));
+  }
+  U->R[0] = 1;
+  V->R[0] = 1;
+  U->R[1] = Y0.R[1];
+  V->R[1] = Y1.R[1];
+  U->I[0] = Y0.I[0];
+  U->J[0] = k;
+  V->I[0] = Y1.I[0];
+  V->J[0] = k;
+  for (int i = 1; i < P.d; ++i) {
+    const int64_t ue = Y0.R[i] * Y0.I[i] * Y0.R[i + 1];
+    const int64_t ve = Y1.R[i] * Y1.I[i] * Y1.R[i + 1];
+    if (ue > U->cap[i] || ve > V->cap[i]) return TNR_ENOMEM;
+    TNR_CK(cudaMemcpyAsync(U->core[i], Y0.core[i], sizeof(double) * ue, cudaMemcpyDeviceToDevice, s));
+    TNR_CK(cudaMemcpyAsync(V->core[i], Y1.core[i], sizeof(double) * ve, cudaMemcpyDeviceToDevice, s));
+    U->R[i + 1] = Y0.R[i + 1];
+    V->R[i + 1] = Y1.R[i + 1];
+    U->I[i] = Y0.I[i];
+    V->I[i] = Y1.I[i];
+    U->J[i] = 1;
+    V->J[i] = 1;
+  }
+  TNR_CK(cudaMemcpyAsync(S, sb.S, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+  return read_status(s);
+}
+
+}  // namespace
+}  // namespace tnr
+
+using namespace tnr;
+
+extern "C" int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, void *stream) {
+  TNR_TRY(validate_input(A));
+  TNR_TRY(validate_input(X));
+  if (!Y || X->d != A->d || (trans != 0 && trans != 1)) return TNR_EINVAL;
+  for (int k = 0; k < A->d; ++k)
+    if (!Y->core[k]) return TNR_EINVAL;
+  return contract_impl((cudaStream_t)stream, *A, trans, *X, *Y);
+}
+
+namespace {
+int orth_limits(const tnr_mpo *Y, Limits &L) {
+  TNR_TRY(validate_input(Y));
+  L = Limits();
+  for (int k = 0; k < Y->d; ++k) {
+    const int64_t rows = Y->R[k] * Y->I[k] * Y->J[k];
+    L.maxcore = std::max(L.maxcore, core_elems(*Y, k));
+    L.maxbond = std::max(L.maxbond, std::max(Y->R[k], Y->R[k + 1]));
+    L.maxrows = std::max(L.maxrows, rows);
+    if (k > 0) L.maxsq = std::max(L.maxsq, std::min(Y->R[k], Y->I[k] * Y->J[k] * Y->R[k + 1]));
+  }
+  L.maxsq = std::max(L.maxsq, Y->J[0]);
+  L.maxcore = std::max(L.maxcore, Y->I[0] * Y->J[0] * L.maxbond);
+  if (L.maxsq > 1024) return TNR_ENOMEM;
+  return TNR_OK;
+}
+}  // namespace
+
+extern "C" int tnr_orthogonalize_workspace(const tnr_mpo *Y, size_t *bytes) {
+  Limits L;
+  TNR_TRY(orth_limits(Y, L));
+  if (!bytes) return TNR_EINVAL;
+  Arena ar;
+  Bufs b;
+  carve(ar, L, b);
+  *bytes = ar.off;
+  return TNR_OK;
+}
+
+extern "C" int tnr_orthogonalize(tnr_mpo *Y, double *R_KxK, const tnr_opts *opts, void *ws, size_t ws_bytes,
+                                 void *stream) {
+  Limits L;
+  TNR_TRY(orth_limits(Y, L));
+  for (int k = 1; k < Y->d; ++k)
+    if (Y->J[k] != 1) return TNR_EINVAL;
+  if (Y->I[0] < Y->J[0]) return TNR_EINVAL;  // Alg. 5.2 needs I_1 >= K
+  Arena ar;
+  ar.base = static_cast<char *>(ws);
+  ar.size = ws_bytes;
+  Bufs b;
+  carve(ar, L, b);
+  if (!ar.ok || !ws) return TNR_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  TNR_TRY(reset_status(s));
+  const double tol = opts ? opts->tol : 0.0;
+  const int64_t mr = opts ? opts->max_rank : 0;
+  TNR_TRY(orthogonalize_impl(s, *Y, R_KxK, tol, mr, b));
+  return read_status(s);
+}
+
+extern "C" int tnr_solve_query(const tnr_mpo *A, int32_t k, int32_t p, const tnr_opts *opts, tnr_mpo *U_shape,
+                               tnr_mpo *V_shape, size_t *ws_bytes) {
+  if (k < 1 || p < 0 || !opts) return TNR_EINVAL;
+  const int64_t K = (int64_t)k + p;
+  Plan P;
+  TNR_TRY(make_plan(A, K, opts, P));
+  Arena ar;
+  SolveBufs sb;
+  carve_solve(ar, P, K, sb);
+  if (ws_bytes) *ws_bytes = ar.off;
+  for (tnr_mpo *M : {U_shape, V_shape}) {
+    if (!M) continue;
+    const bool isU = M == U_shape;
+    M->d = P.d;
+    for (int i = 0; i < P.d; ++i) {
+      M->I[i] = isU ? P.I[i] : P.J[i];
+      M->J[i] = i == 0 ? k : 1;
+      M->R[i] = P.sq[i];
+      M->cap[i] = P.sq[i] * M->I[i] * (i == 0 ? k : 1) * P.sq[i + 1];
+      M->core[i] = nullptr;
+    }
+    M->R[P.d] = 1;
+  }
+  return TNR_OK;
+}
+
+extern "C" int tnr_solve(const tnr_mpo *A, int32_t k, int32_t p, int32_t q, uint64_t seed, const tnr_opts *opts,
+                         tnr_mpo *U, double *S, tnr_mpo *V, void *ws, size_t ws_bytes, void *stream) {
+  return solve_impl((cudaStream_t)stream, A, k, p, q, seed, opts, U, S, V, ws, ws_bytes);
+}

@@ -1,0 +1,345 @@
+"""Thin Python binding of libtnrsvd.so (argument marshalling only).
+
+The names mirror include/tnrsvd.h. PyTorch supplies device memory and the current stream;
+every step of the method runs in the library's CUDA kernels. There is no CPU fallback: if
+the library is missing or cannot be loaded, every call raises.
+
+Device data layout: an MPO core is a flat float64 CUDA tensor holding the core in memory
+order (r fastest, then i, j, r'); ``Mpo`` carries those tensors with their dims and ranks.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnrsvd.so")
+MAX_SITES = 64
+
+TNR_FP64 = 0
+TNR_MIXED = 1
+
+_STATUS = {
+    0: "ok", -1: "EINVAL", -2: "EDUP", -3: "ENOTSORTED", -4: "ENONFINITE", -5: "ENOMEM", -6: "ECUDA",
+    -7: "ETIMEOUT", -8: "ERANGE",
+}
+
+
+class TnrError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {_STATUS.get(status, status)} ({status})")
+
+
+class tnr_mpo(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("I", ctypes.c_int64 * MAX_SITES),
+        ("J", ctypes.c_int64 * MAX_SITES),
+        ("R", ctypes.c_int64 * (MAX_SITES + 1)),
+        ("core", ctypes.c_void_p * MAX_SITES),
+        ("cap", ctypes.c_int64 * MAX_SITES),
+    ]
+
+
+class tnr_opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tol", ctypes.c_double),
+        ("max_rank", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_SZP = ctypes.POINTER(ctypes.c_size_t)
+_MPOP = ctypes.POINTER(tnr_mpo)
+_OPTP = ctypes.POINTER(tnr_opts)
+
+_SIGS = {
+    "tnr_sparse_workspace": (ctypes.c_int, [_I64, _I64, _I64, _I32, _I64P, _I64P, _SZP]),
+    "tnr_sparse_count": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _I32, _I64P, _I64P, _I64P, _P, ctypes.c_size_t, _P]),
+    "tnr_sparse_fill": (ctypes.c_int,
+                        [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _I64, _P, _P, _P, ctypes.c_size_t, _P]),
+    "tnr_mpo_contract": (ctypes.c_int, [_MPOP, _I32, _MPOP, _MPOP, _P]),
+    "tnr_orthogonalize_workspace": (ctypes.c_int, [_MPOP, _SZP]),
+    "tnr_orthogonalize": (ctypes.c_int, [_MPOP, _P, _OPTP, _P, ctypes.c_size_t, _P]),
+    "tnr_solve_query": (ctypes.c_int, [_MPOP, _I32, _I32, _OPTP, _MPOP, _MPOP, _SZP]),
+    "tnr_solve": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _OPTP, _MPOP, _P, _MPOP, _P,
+                                 ctypes.c_size_t, _P]),
+    "tnr_stats_enable": (None, [_I32]),
+    "tnr_stats_reset": (None, []),
+    "tnr_stats": (ctypes.c_int, [_I32, _I64P, ctypes.POINTER(ctypes.c_double)]),
+    "tnr_stats_work": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.c_double)]),
+    "tnr_stats_class_name": (ctypes.c_char_p, [_I32]),
+    "tnr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "tnr_version": (ctypes.c_int, []),
+}
+
+
+def load():
+    """Load libtnrsvd.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtnrsvd.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise TnrError(rc, what)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _i64arr(vals):
+    return (ctypes.c_int64 * max(1, len(vals)))(*[int(v) for v in vals])
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise ValueError("device tensors (CUDA) are required")
+
+
+# ----------------------------------------------------------------------------------------
+# MPO container
+# ----------------------------------------------------------------------------------------
+class Mpo:
+    """Dims, ranks and flat float64 CUDA core buffers of an MPO (layout of include/tnrsvd.h)."""
+
+    def __init__(self, I, J, R, cores):
+        self.I = [int(x) for x in I]
+        self.J = [int(x) for x in J]
+        self.R = [int(x) for x in R]
+        self.cores = list(cores)
+
+    @property
+    def d(self):
+        return len(self.I)
+
+    def core_shape(self, k):
+        return (self.R[k], self.I[k], self.J[k], self.R[k + 1])
+
+    def to_struct(self, caps=None):
+        m = tnr_mpo()
+        m.d = self.d
+        for k in range(self.d):
+            m.I[k], m.J[k] = self.I[k], self.J[k]
+            m.core[k] = self.cores[k].data_ptr() if self.cores[k] is not None else 0
+            m.cap[k] = caps[k] if caps is not None else (self.cores[k].numel() if self.cores[k] is not None else 0)
+        for k in range(self.d + 1):
+            m.R[k] = self.R[k]
+        return m
+
+    @staticmethod
+    def from_numpy(cores, device="cuda"):
+        """Logical numpy cores (R, I, J, R') -> flat device buffers in memory order."""
+        import numpy as np
+
+        flat = [torch.from_numpy(np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, order="F")))
+                .to(device) for c in cores]
+        I = [c.shape[1] for c in cores]
+        J = [c.shape[2] for c in cores]
+        R = [cores[0].shape[0]] + [c.shape[3] for c in cores]
+        return Mpo(I, J, R, flat)
+
+    def to_numpy(self):
+        """Flat device buffers -> logical numpy cores (copies to host)."""
+        out = []
+        for k in range(self.d):
+            shape = self.core_shape(k)
+            n = shape[0] * shape[1] * shape[2] * shape[3]
+            out.append(self.cores[k][:n].cpu().numpy().reshape(shape, order="F"))
+        return out
+
+
+# ----------------------------------------------------------------------------------------
+# Entry points (names of include/tnrsvd.h)
+# ----------------------------------------------------------------------------------------
+def tnr_sparse_workspace(nrows, ncols, nnz, I, J):
+    lib = load()
+    b = ctypes.c_size_t(0)
+    _check(lib.tnr_sparse_workspace(nrows, ncols, nnz, len(I), _i64arr(I), _i64arr(J), ctypes.byref(b)),
+           "tnr_sparse_workspace")
+    return b.value
+
+
+def tnr_sparse_count(nrows, ncols, row, col, I, J, ws, stream=None):
+    lib = load()
+    _need_cuda(row, col, ws)
+    R = ctypes.c_int64(0)
+    _check(lib.tnr_sparse_count(nrows, ncols, row.numel(), _ptr(row), _ptr(col), len(I), _i64arr(I), _i64arr(J),
+                                ctypes.byref(R), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "tnr_sparse_count")
+    return R.value
+
+
+def tnr_sparse_fill(nrows, ncols, row, col, val, I, J, R, X, digits, ws, stream=None):
+    lib = load()
+    _need_cuda(row, col, val, ws)
+    _check(lib.tnr_sparse_fill(nrows, ncols, row.numel(), _ptr(row), _ptr(col), _ptr(val), len(I), _i64arr(I),
+                               _i64arr(J), R, _ptr(X), _ptr(digits), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream)), "tnr_sparse_fill")
+
+
+def sparse_to_mpo(nrows, ncols, row, col, val, I, J, stream=None):
+    """Alg. 4.1 on the device: returns (R, X, digits) as CUDA tensors (block form)."""
+    nbytes = tnr_sparse_workspace(nrows, ncols, row.numel(), I, J)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=row.device)
+    R = tnr_sparse_count(nrows, ncols, row, col, I, J, ws, stream)
+    X = torch.empty(max(R * int(I[0]) * int(J[0]), 1), dtype=torch.float64, device=row.device)
+    digits = torch.empty(max(R * 2 * (len(I) - 1), 1), dtype=torch.uint8, device=row.device)
+    tnr_sparse_fill(nrows, ncols, row, col, val, I, J, R, X, digits, ws, stream)
+    return R, X[: R * int(I[0]) * int(J[0])], digits[: R * 2 * (len(I) - 1)].view(R, 2 * (len(I) - 1))
+
+
+def tnr_mpo_contract(A, trans, X, Y_caps=None, stream=None):
+    """Y = op(A) X (Section 5.2). Allocates Y with exact sizes unless Y_caps is given."""
+    lib = load()
+    d = A.d
+    cores = []
+    for k in range(d):
+        xo = A.J[k] if trans else A.I[k]
+        n = A.R[k] * X.R[k] * xo * X.J[k] * A.R[k + 1] * X.R[k + 1]
+        cores.append(torch.empty(max(n, 1), dtype=torch.float64, device=A.cores[0].device))
+    Y = Mpo([0] * d, [0] * d, [1] * (d + 1), cores)
+    sa, sx, sy = A.to_struct(), X.to_struct(), Y.to_struct()
+    _check(lib.tnr_mpo_contract(ctypes.byref(sa), int(trans), ctypes.byref(sx), ctypes.byref(sy), _stream(stream)),
+           "tnr_mpo_contract")
+    Y.I = [sy.I[k] for k in range(d)]
+    Y.J = [sy.J[k] for k in range(d)]
+    Y.R = [sy.R[k] for k in range(d + 1)]
+    return Y
+
+
+def _opts(tol, max_rank, precision):
+    o = tnr_opts()
+    o.precision = int(precision)
+    o.tol = float(tol)
+    o.max_rank = int(max_rank)
+    return o
+
+
+def tnr_orthogonalize(Y, tol=0.0, max_rank=0, stream=None):
+    """In-place MPO-QR with rounding (Alg. 5.2 + Section 5.4); returns (Y as Q, R)."""
+    lib = load()
+    sy = Y.to_struct()
+    b = ctypes.c_size_t(0)
+    _check(lib.tnr_orthogonalize_workspace(ctypes.byref(sy), ctypes.byref(b)), "tnr_orthogonalize_workspace")
+    dev = Y.cores[0].device
+    ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+    K = Y.J[0]
+    Rk = torch.empty(K * K, dtype=torch.float64, device=dev)
+    o = _opts(tol, max_rank, TNR_FP64)
+    _check(lib.tnr_orthogonalize(ctypes.byref(sy), _ptr(Rk), ctypes.byref(o), _ptr(ws), b.value, _stream(stream)),
+           "tnr_orthogonalize")
+    Y.R = [sy.R[k] for k in range(Y.d + 1)]
+    return Y, Rk.view(K, K).t()  # column-major K x K -> row-major view
+
+
+class SolvePlan:
+    """Buffers for repeated solves of one operator shape (workspace and U, S, V outputs)."""
+
+    def __init__(self, A, k, p, tol=0.0, max_rank=0, precision=TNR_FP64):
+        lib = load()
+        self.k, self.p = int(k), int(p)
+        self.opts = _opts(tol, max_rank, precision)
+        self.A = A
+        self.sa = A.to_struct()
+        self.us, self.vs = tnr_mpo(), tnr_mpo()
+        b = ctypes.c_size_t(0)
+        _check(lib.tnr_solve_query(ctypes.byref(self.sa), self.k, self.p, ctypes.byref(self.opts),
+                                   ctypes.byref(self.us), ctypes.byref(self.vs), ctypes.byref(b)), "tnr_solve_query")
+        dev = A.cores[0].device
+        self.ws_bytes = b.value
+        self.ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+        self.U_cores = [torch.empty(max(self.us.cap[i], 1), dtype=torch.float64, device=dev) for i in range(self.us.d)]
+        self.V_cores = [torch.empty(max(self.vs.cap[i], 1), dtype=torch.float64, device=dev) for i in range(self.vs.d)]
+        for i in range(self.us.d):
+            self.us.core[i] = self.U_cores[i].data_ptr()
+            self.vs.core[i] = self.V_cores[i].data_ptr()
+        self.S = torch.empty(self.k, dtype=torch.float64, device=dev)
+
+    def run(self, q, seed, stream=None):
+        lib = load()
+        _check(lib.tnr_solve(ctypes.byref(self.sa), self.k, self.p, int(q), ctypes.c_uint64(int(seed)),
+                             ctypes.byref(self.opts), ctypes.byref(self.us), _ptr(self.S), ctypes.byref(self.vs),
+                             _ptr(self.ws), self.ws_bytes, _stream(stream)), "tnr_solve")
+        return self
+
+    def outputs(self):
+        d = self.us.d
+        U = Mpo([self.us.I[i] for i in range(d)], [self.us.J[i] for i in range(d)],
+                [self.us.R[i] for i in range(d + 1)], self.U_cores)
+        V = Mpo([self.vs.I[i] for i in range(d)], [self.vs.J[i] for i in range(d)],
+                [self.vs.R[i] for i in range(d + 1)], self.V_cores)
+        return U, self.S, V
+
+
+def tnr_solve(A, k, p, q, seed, tol=0.0, max_rank=0, precision=TNR_FP64, stream=None):
+    """TNrSVD (Alg. 5.4 + 5.3): returns (U, S, V) with U, V as Mpo over the merged sites."""
+    plan = SolvePlan(A, k, p, tol, max_rank, precision)
+    plan.run(q, seed, stream)
+    return plan.outputs()
+
+
+# ----------------------------------------------------------------------------------------
+# Instrumentation
+# ----------------------------------------------------------------------------------------
+def stats_classes():
+    lib = load()
+    out = []
+    i = 0
+    while True:
+        n = lib.tnr_stats_class_name(i)
+        if n is None:
+            return out
+        out.append(n.decode())
+        i += 1
+
+
+def stats_enable(mask):
+    load().tnr_stats_enable(int(mask))
+
+
+def stats_reset():
+    load().tnr_stats_reset()
+
+
+def stats_work(cls=-1):
+    w = ctypes.c_double(0.0)
+    _check(load().tnr_stats_work(int(cls), ctypes.byref(w)), "tnr_stats_work")
+    return w.value
+
+
+def stats(cls=-1):
+    L = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    _check(load().tnr_stats(int(cls), ctypes.byref(L), ctypes.byref(ms)), "tnr_stats")
+    return L.value, ms.value

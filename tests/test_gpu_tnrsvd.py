@@ -1,0 +1,120 @@
+"""GPU parity for the MPO product, MPO-QR/rounding and TNrSVD (FP64), through the C ABI."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import mpo as om
+from oracle import rounding as orr
+from oracle import tnrsvd as ot
+from paper_1707_07803_gb300 import tnrsvd as T
+from tests.gpu_util import dev_mpo, host_cores, sv_rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_SV_TOL = 1e-10  # relative singular-value error gate for the FP64 path
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+def test_contract_elementwise(trans):
+    I, J = [5, 2, 3, 4], [3, 4, 2, 2]
+    A = W.gaussian_mpo(1, I, J, [1, 3, 4, 2, 1])
+    rows = J if trans == 0 else I
+    X = W.gaussian_mpo(2, rows, [6, 1, 1, 1], [1, 2, 3, 2, 1])
+    want = om.contract(A, X, trans=bool(trans))
+    Y = T.tnr_mpo_contract(dev_mpo(A), trans, dev_mpo(X))
+    got = host_cores(Y)
+    for g, w in zip(got, want):
+        assert g.shape == w.shape
+        np.testing.assert_allclose(g, w, rtol=0, atol=1e-13 * max(1.0, np.abs(w).max()))
+
+
+@pytest.mark.parametrize("case", ["plain", "wide_sites", "rank_deficient", "single_site"])
+def test_orthogonalize_invariants_and_ranks(case):
+    if case == "plain":
+        Y = W.gaussian_mpo(3, [12, 3, 2, 2], [5, 1, 1, 1], [1, 4, 3, 2, 1])
+    elif case == "wide_sites":
+        Y = W.gaussian_mpo(4, [8, 4, 4], [6, 1, 1], [1, 9, 7, 1])
+    elif case == "rank_deficient":
+        Y = W.gaussian_mpo(5, [10, 2, 2, 2], [4, 1, 1, 1], [1, 6, 6, 6, 1])  # bonds above Thm 3.2 bounds
+    else:
+        Y = W.gaussian_mpo(6, [40], [9], [1, 1])
+    Qo, Ro = orr.orthogonalize(Y, tol=1e-13)
+    Yd = dev_mpo(Y)
+    Qd, Rd = T.tnr_orthogonalize(Yd, tol=1e-13)
+    torch.cuda.synchronize()
+    Q = host_cores(Qd)
+    R = Rd.cpu().numpy()
+    assert Qd.R == orr.ranks(Qo)
+    K = Y[0].shape[2]
+    DQ, DY = om.dense(Q), om.dense(Y)
+    np.testing.assert_allclose(DQ.T @ DQ, np.eye(K), atol=1e-13)
+    np.testing.assert_allclose(DQ @ R, DY, atol=1e-11 * np.abs(DY).max())
+    # same subspace and the same R up to the signs of its rows
+    DQo = om.dense(Qo)
+    np.testing.assert_allclose(DQ @ DQ.T, DQo @ DQo.T, atol=1e-12)
+    np.testing.assert_allclose(np.abs(R), np.abs(Ro), atol=1e-11 * np.abs(Ro).max())
+
+
+def _check_solve(A, k, p, q, seed, tol, max_rank, sv_tol=FP64_SV_TOL, vec_tol=1e-8):
+    Uo, So, Vo, info = ot.tnrsvd(A, k, p, q, seed, tol=tol, max_rank=max_rank, return_info=True)
+    U, S, V = T.tnr_solve(dev_mpo(A), k, p, q, seed, tol=tol, max_rank=max_rank)
+    torch.cuda.synchronize()
+    S = S.cpu().numpy()
+    err = sv_rel_err(S, So)
+    assert err <= sv_tol, (err, S, So)
+    assert U.R == orr.ranks(Uo) and V.R == orr.ranks(Vo)
+    Uh, Vh = host_cores(U), host_cores(V)
+    GU = om.inner(Uh, Uo)
+    GV = om.inner(Vh, Vo)
+    np.testing.assert_allclose(np.abs(np.diag(GU)), 1.0, atol=vec_tol)
+    np.testing.assert_allclose(np.abs(np.diag(GV)), 1.0, atol=vec_tol)
+    np.testing.assert_allclose(om.inner(Uh, Uh), np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(om.inner(Vh, Vh), np.eye(k), atol=1e-12)
+    return S, So, err
+
+
+def test_solve_small_merge_and_power_iterations():
+    A = W.gaussian_mpo(0, [4, 4, 4, 4], [4, 4, 4, 4], [1, 3, 3, 3, 1], scale=1 / np.sqrt(12))
+    for q in (0, 1, 2):
+        _check_solve(A, 5, 5, q, seed=q, tol=1e-14, max_rank=0)
+
+
+def test_solve_rectangular_and_ragged():
+    A = W.gaussian_mpo(7, [6, 5, 3, 2], [4, 3, 5, 2], [1, 4, 5, 3, 1])
+    _check_solve(A, 3, 4, 1, seed=11, tol=1e-14, max_rank=0)
+
+
+def test_solve_single_site_after_merge():
+    A = W.gaussian_mpo(8, [4, 4], [4, 4], [1, 3, 1])
+    S, So, _ = _check_solve(A, 8, 8, 0, seed=0, tol=0.0, max_rank=0)
+    np.testing.assert_allclose(S, np.linalg.svd(om.dense(A), compute_uv=False)[:8], rtol=1e-12)
+
+
+def test_solve_exact_recovery_prescribed_sigma():
+    K = 8
+    sigma = 0.7 ** np.arange(K)
+    A, _, _ = W.prescribed_mpo(0, 1, 16, [2, 2, 2], K, 3, sigma)
+    S, So, _ = _check_solve(A, 4, 4, 1, seed=2, tol=1e-13, max_rank=0)
+    np.testing.assert_allclose(S, sigma[:4], rtol=1e-12)
+
+
+def test_solve_max_rank_cap():
+    A = W.gaussian_mpo(9, [4, 4, 4, 4, 4], [4, 4, 4, 4, 4], [1, 4, 4, 4, 4, 1], scale=0.25)
+    _check_solve(A, 4, 4, 1, seed=3, tol=1e-14, max_rank=6)
+
+
+def test_solve_c1_plain_fp64():
+    """4096 x 4096 Gaussian MPO (d=6, 4x4 sites, ranks 3), k=10, p=10, q=1, seed 0."""
+    c = W.c1_plain_fp64()
+    S, So, err = _check_solve(c["A"], c["k"], c["p"], c["q"], c["seed"], c["tol"], c["max_rank"])
+    true = np.linalg.svd(om.dense(c["A"]), compute_uv=False)[: c["k"]]
+    assert np.all(S <= true * (1 + 1e-12))
+
+
+def test_solve_c2_prescribed_fp64():
+    """2^20 x 2^20 MPO with sigma_j = 0.7^j (rank 32), k=16, p=16, q=2: exact recovery."""
+    c = W.c2_prescribed()
+    S, So, err = _check_solve(c["A"], c["k"], c["p"], c["q"], c["seed"], c["tol"], c["max_rank"])
+    assert sv_rel_err(S, c["sigma"][:16]) <= 1e-10

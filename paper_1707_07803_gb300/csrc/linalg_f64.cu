@@ -9,6 +9,7 @@
 // column rather than a full trailing update on one SM.
 #include <cfloat>
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 
 #include "tnr_internal.cuh"
@@ -153,19 +154,30 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// ------------------------------------------------------------------------------------------
-// Householder QR, columns distributed cyclically over P CTAs (cooperative launch, so all CTAs
-// are resident). Reflector j (LAPACK dlarfg convention: beta = -sign(alpha) ||x||,
-// tau = (beta - alpha) / beta, v = x / (alpha - beta), v_j = 1) is computed by the owner of
-// column j, written to V[:, j] and published with a release store to flags[j]; every CTA
-// applies it to its own columns after an acquire load. The owner of column j+1 applies
-// reflector j to column j+1 first and publishes reflector j+1 before updating its other
-// columns (one-column lookahead), so the critical path per column is one flag hop plus one
-// column update. Waits are bounded (kSpinCap polls); on timeout the kernel records
-// TNR_ETIMEOUT and returns.
-// ------------------------------------------------------------------------------------------
-constexpr int kQrThreads = 256;
+__device__ __forceinline__ bool qr_wait_flag(const unsigned *f, int *status) {
+  long long spins = 0;
+  while (ld_acquire(f) == 0u) {
+    if (++spins > kSpinCap) {
+      set_status(status, TNR_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
 
+// ------------------------------------------------------------------------------------------
+// Householder QR, one warp per CTA, columns distributed cyclically over P CTAs (cooperative
+// launch, so all CTAs are resident; P <= #SMs so every CTA has an SM's FP64 pipe to itself).
+// Reflector j (LAPACK dlarfg convention: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+// v = x / (alpha - beta), v_j = 1) is computed by the owner of column j, written to V[:, j]
+// and published with a release store to flags[j]; every CTA applies it to its own columns
+// after an acquire load. The owner of column j+1 applies reflector j to column j+1 first and
+// publishes reflector j+1 before updating its other columns (one-column lookahead), so the
+// critical path per column is one flag hop plus one column update. A single warp per CTA
+// keeps the FP64 instruction count of each reduction at 5 shuffle-adds (FP64 issue, not
+// bandwidth, limits these small reductions on GB300). Waits are bounded (kSpinCap polls); on
+// timeout the kernel records TNR_ETIMEOUT and returns.
+// ------------------------------------------------------------------------------------------
 struct QrArgs {
   double *A;
   int64_t m, n, lda;
@@ -177,11 +189,23 @@ struct QrArgs {
   int *status;
 };
 
-__device__ void qr_make_reflector(const QrArgs &a, int64_t j, double *red) {
+__device__ __forceinline__ bool qr_wait(const QrArgs &a, int64_t j) {
+  long long spins = 0;
+  while (ld_acquire(a.flags + j) == 0u) {
+    if (++spins > kSpinCap) {
+      set_status(a.status, TNR_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ void qr_make_reflector(const QrArgs &a, int64_t j) {
+  const int lane = threadIdx.x;
   double *col = a.A + a.lda * j;
   double sig = 0.0;
-  for (int64_t i = j + 1 + threadIdx.x; i < a.m; i += kQrThreads) sig = fma(col[i], col[i], sig);
-  sig = block_sum<kQrThreads>(sig, red);
+  for (int64_t i = j + 1 + lane; i < a.m; i += 32) sig = fma(col[i], col[i], sig);
+  sig = warp_sum(sig);
   const double alpha = col[j];
   double tau = 0.0, beta = alpha, scal = 0.0;
   if (sig > 0.0) {
@@ -190,89 +214,455 @@ __device__ void qr_make_reflector(const QrArgs &a, int64_t j, double *red) {
     scal = 1.0 / (alpha - beta);
   }
   double *v = a.V + a.m * j;
-  for (int64_t i = j + 1 + threadIdx.x; i < a.m; i += kQrThreads) v[i] = col[i] * scal;
-  if (threadIdx.x == 0) {
+  for (int64_t i = j + 1 + lane; i < a.m; i += 32) v[i] = col[i] * scal;
+  if (lane == 0) {
     v[j] = 1.0;
     col[j] = beta;
     a.tau[j] = tau;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release(a.flags + j, 1u);
-  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release(a.flags + j, 1u);
 }
 
-// Apply H_j = I - tau v v^T (v from vs, rows j..m-1) to column l of A.
-__device__ __forceinline__ void qr_apply(const QrArgs &a, const double *vs, double tau, int64_t j, int64_t l,
-                                         double *red) {
+// Apply H_j = I - tau v v^T (v in vs, rows j..m-1) to column l of A.
+__device__ __forceinline__ void qr_apply(const QrArgs &a, const double *vs, double tau, int64_t j, int64_t l) {
+  const int lane = threadIdx.x;
   double *col = a.A + a.lda * l;
   double w = 0.0;
-  for (int64_t i = j + threadIdx.x; i < a.m; i += kQrThreads) w = fma(vs[i - j], col[i], w);
-  w = block_sum<kQrThreads>(w, red) * tau;
-  for (int64_t i = j + threadIdx.x; i < a.m; i += kQrThreads) col[i] = fma(-w, vs[i - j], col[i]);
-  __syncthreads();
+  for (int64_t i = j + lane; i < a.m; i += 32) w = fma(vs[i - j], col[i], w);
+  w = warp_sum(w) * tau;
+  for (int64_t i = j + lane; i < a.m; i += 32) col[i] = fma(-w, vs[i - j], col[i]);
+  __syncwarp();
 }
 
-__global__ void __launch_bounds__(kQrThreads) k_qr_coop(QrArgs a) {
+__global__ void __launch_bounds__(32) k_qr_coop(QrArgs a) {
   extern __shared__ double vs[];  // m doubles: the current reflector
-  __shared__ double red[kQrThreads / 32];
-  __shared__ int s_abort;
+  const int lane = threadIdx.x;
   const int64_t P = gridDim.x, c = blockIdx.x;
   const int64_t nref = a.m < a.n ? a.m : a.n;
-  if (threadIdx.x == 0) s_abort = 0;
-  __syncthreads();
-  if (c == 0 && nref > 0) qr_make_reflector(a, 0, red);
+  if (c == 0 && nref > 0) qr_make_reflector(a, 0);
   for (int64_t j = 0; j < nref; ++j) {
-    // my first owned column > j
-    int64_t l0 = j + 1 + ((c - (j + 1) % P) + P) % P;
-    if (l0 >= a.n) break;  // nothing left for this CTA (owned columns only grow)
-    if (threadIdx.x == 0) {
-      long long spins = 0;
-      while (ld_acquire(a.flags + j) == 0u) {
-        if (++spins > kSpinCap) {
-          set_status(a.status, TNR_ETIMEOUT);
-          s_abort = 1;
-          break;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_abort) return;
-    for (int64_t i = j + threadIdx.x; i < a.m; i += kQrThreads) vs[i - j] = __ldcg(a.V + a.m * j + i);
+    const int64_t l0 = j + 1 + ((c - (j + 1) % P) + P) % P;  // my first column > j
+    if (l0 >= a.n) break;  // owned columns only move right: nothing left to update
+    if (!qr_wait(a, j)) return;
+    for (int64_t i = j + lane; i < a.m; i += 32) vs[i - j] = __ldcg(a.V + a.m * j + i);
     const double tau = __ldcg(a.tau + j);
-    __syncthreads();
+    __syncwarp();
     if (tau != 0.0) {
       for (int64_t l = l0; l < a.n; l += P) {
-        qr_apply(a, vs, tau, j, l, red);
-        if (l == j + 1 && l < nref) qr_make_reflector(a, l, red);
+        qr_apply(a, vs, tau, j, l);
+        if (l == j + 1 && l < nref) qr_make_reflector(a, l);
       }
     } else if (l0 == j + 1 && l0 < nref) {
-      qr_make_reflector(a, l0, red);
+      qr_make_reflector(a, l0);
     }
-    __syncthreads();
+    __syncwarp();
   }
   // R: column l of the upper trapezoid (rows 0..min(l, nref-1)), zeros below.
   for (int64_t l = c; l < a.n; l += P) {
     const double *col = a.A + a.lda * l;
-    for (int64_t i = threadIdx.x; i < nref; i += kQrThreads) a.R[i + a.ldr * l] = i <= l ? col[i] : 0.0;
+    for (int64_t i = lane; i < nref; i += 32) a.R[i + a.ldr * l] = i <= l ? col[i] : 0.0;
   }
-  __syncthreads();
-  // Explicit Q, column c' = H_0 ... H_{c'} e_{c'} for my columns c' < nref. All reflectors
-  // j <= c' were observed above (owner of c' waited for every j < c' and made c' itself).
+  __syncwarp();
+  // Explicit Q, column l = H_0 ... H_l e_l for my columns l < nref. Every reflector j <= l
+  // was acquired above (the owner of l waited for each j < l and made l itself).
   for (int64_t l = c; l < nref; l += P) {
     double *q = a.A + a.lda * l;
-    for (int64_t i = threadIdx.x; i < a.m; i += kQrThreads) q[i] = (i == l) ? 1.0 : 0.0;
-    __syncthreads();
+    for (int64_t i = lane; i < a.m; i += 32) q[i] = (i == l) ? 1.0 : 0.0;
+    __syncwarp();
     for (int64_t j = l; j >= 0; --j) {
       const double tau = __ldcg(a.tau + j);
       if (tau == 0.0) continue;
       const double *v = a.V + a.m * j;
       double w = 0.0;
-      for (int64_t i = j + threadIdx.x; i < a.m; i += kQrThreads) w = fma(__ldcg(v + i), q[i], w);
-      w = block_sum<kQrThreads>(w, red) * tau;
-      for (int64_t i = j + threadIdx.x; i < a.m; i += kQrThreads) q[i] = fma(-w, __ldcg(v + i), q[i]);
+      for (int64_t i = j + lane; i < a.m; i += 32) w = fma(__ldcg(v + i), q[i], w);
+      w = warp_sum(w) * tau;
+      for (int64_t i = j + lane; i < a.m; i += 32) q[i] = fma(-w, __ldcg(v + i), q[i]);
+      __syncwarp();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Column-pivoted Householder QR with a noise-level cutoff (rank-revealing), for the
+// left-to-right orthogonalisation sweep. M (m x n) = Q R + E with Q (m x r) orthonormal,
+// R = Q^T M (r x n, original column order) and every column of E below the cutoff
+// c * ||M||_F. The discarded directions are of the size of the backward error of an
+// unpivoted Householder QR of M (a few n eps ||M||_F), so they are the directions the
+// rounding sweep that follows must remove anyway; the bond shrinks to the numerical rank of
+// M right away instead of after a full-width factorisation and SVD.
+//
+// One warp per CTA, P <= #SMs CTAs, each caching its columns (l = c mod P) in shared memory.
+// Step i: every CTA proposes its largest remaining column norm through a 64-bit atomicMax
+// (high bits of the double, low 20 bits the complemented column index, so ties pick the
+// lowest column) and arrives on a per-step counter; once all P have arrived, the owner of the
+// pivot builds reflector i (dlarfg convention), publishes it (release flag), and every CTA
+// applies it to its unpivoted columns and recomputes their norms over rows > i exactly.
+// The sweep stops when the largest remaining norm is at or below the cutoff; r >= 1.
+// All waits are bounded; a timeout sets TNR_ETIMEOUT and the kernel returns.
+// ------------------------------------------------------------------------------------------
+struct QrcpArgs {
+  double *A;
+  int64_t m, n, lda;
+  double *R;  // r x n, ld ldr (ldr >= min(m, n))
+  int64_t ldr;
+  double *V;  // m x nref
+  double *tau;
+  unsigned long long *best;  // nref
+  unsigned *cnt;             // nref + 1
+  unsigned *flags;           // nref
+  double *fro2;              // 1
+  int64_t *r_out;            // device rank
+  double cut_rel;
+  int *status;
+};
+
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned target, int *status) {
+  long long spins = 0;
+  while (ld_acquire(p) < target) {
+    if (++spins > kSpinCap) {
+      set_status(status, TNR_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void arrive(unsigned *p) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
+__global__ void __launch_bounds__(32) k_qrcp(QrcpArgs a) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x;
+  const int64_t P = gridDim.x, c = blockIdx.x;
+  const int64_t m = a.m, n = a.n;
+  const int64_t nref = m < n ? m : n;
+  const int64_t nc = (n - c + P - 1) / P;  // number of my columns
+  double *cols = sm;                       // nc x m
+  double *vs = sm + nc * m;                // m
+  double *nrm = vs + m;                    // nc
+  int *piv = reinterpret_cast<int *>(nrm + nc);  // nc: 1 when pivoted
+  // load my columns and their norms
+  double mine = 0.0;
+  for (int64_t q = 0; q < nc; ++q) {
+    const double *src = a.A + a.lda * (c + q * P);
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) {
+      const double x = src[i];
+      cols[q * m + i] = x;
+      s = fma(x, x, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      nrm[q] = s;
+      piv[q] = 0;
+    }
+    mine += s;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    atomicAdd(a.fro2, mine);
+    __threadfence();
+    arrive(a.cnt + 0);
+  }
+  if (!wait_count(a.cnt + 0, (unsigned)P, a.status)) return;
+  const double cut2 = a.cut_rel * a.cut_rel * __ldcg(a.fro2);
+  int64_t r = 0;
+  for (int64_t i = 0; i < nref; ++i) {
+    // propose my best remaining column
+    unsigned long long key = 0ull;
+    for (int64_t q = 0; q < nc; ++q) {
+      if (piv[q]) continue;
+      const double v2 = nrm[q];
+      const unsigned long long k2 = (__double_as_longlong(v2 > 0.0 ? v2 : 0.0) & ~0xFFFFFull) |
+                                    (unsigned long long)(0xFFFFF - (c + q * P));
+      if (k2 > key) key = k2;
+    }
+    if (lane == 0) {
+      if (key) atomicMax(a.best + i, key);
+      __threadfence();
+      arrive(a.cnt + i + 1);
+    }
+    if (!wait_count(a.cnt + i + 1, (unsigned)P, a.status)) return;
+    const unsigned long long b = __ldcg(a.best + i);
+    // every unpivoted column contributes a nonzero key (its complemented index), so b != 0
+    if (b == 0ull) break;
+    const double bn2 = __longlong_as_double((long long)(b & ~0xFFFFFull));
+    const int64_t p = 0xFFFFF - (int64_t)(b & 0xFFFFFull);
+    if (i > 0 && bn2 <= cut2) break;  // remaining columns are noise (keep r >= 1)
+    r = i + 1;
+    if (p % P == c) {  // I own the pivot: build reflector i from rows i..m-1 of column p
+      const int64_t q = p / P;
+      double *col = cols + q * m;
+      double sig = 0.0;
+      for (int64_t t = i + 1 + lane; t < m; t += 32) sig = fma(col[t], col[t], sig);
+      sig = warp_sum(sig);
+      const double alpha = col[i];
+      double tau = 0.0, beta = alpha, scal = 0.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      double *v = a.V + m * i;
+      for (int64_t t = i + 1 + lane; t < m; t += 32) {
+        v[t] = col[t] * scal;
+        col[t] = 0.0;
+      }
+      if (lane == 0) {
+        v[i] = 1.0;
+        col[i] = beta;
+        a.tau[i] = tau;
+        piv[q] = 1;
+        nrm[q] = 0.0;
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(a.flags + i, 1u);
+    }
+    // apply reflector i to my unpivoted columns
+    bool any = false;
+    for (int64_t q = 0; q < nc; ++q) any |= !piv[q];
+    if (!any) continue;
+    if (!qr_wait_flag(a.flags + i, a.status)) return;
+    for (int64_t t = i + lane; t < m; t += 32) vs[t - i] = __ldcg(a.V + m * i + t);
+    const double tau = __ldcg(a.tau + i);
+    __syncwarp();
+    for (int64_t q = 0; q < nc; ++q) {
+      if (piv[q]) continue;
+      double *col = cols + q * m;
+      if (tau != 0.0) {
+        double w = 0.0;
+        for (int64_t t = i + lane; t < m; t += 32) w = fma(vs[t - i], col[t], w);
+        w = warp_sum(w) * tau;
+        for (int64_t t = i + lane; t < m; t += 32) col[t] = fma(-w, vs[t - i], col[t]);
+      }
+      double s = 0.0;
+      for (int64_t t = i + 1 + lane; t < m; t += 32) s = fma(col[t], col[t], s);
+      s = warp_sum(s);
+      if (lane == 0) nrm[q] = s;
+    }
+    __syncwarp();
+  }
+  if (c == 0 && lane == 0) *a.r_out = r;
+  // R = rows 0..r-1 of every column (original order)
+  for (int64_t q = 0; q < nc; ++q) {
+    const int64_t l = c + q * P;
+    for (int64_t t = lane; t < r; t += 32) a.R[t + a.ldr * l] = cols[q * m + t];
+  }
+  // Explicit Q (m x r): column l = H_0 ... H_l e_l, in place of A. All CTAs loaded their
+  // columns before the first step's counter completed, so overwriting A is safe here.
+  for (int64_t l = c; l < r; l += P) {
+    double *qv = vs;  // reuse as the working column
+    for (int64_t t = lane; t < m; t += 32) qv[t] = (t == l) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int64_t j = l; j >= 0; --j) {
+      if (!qr_wait_flag(a.flags + j, a.status)) return;
+      const double tau = __ldcg(a.tau + j);
+      if (tau == 0.0) continue;
+      const double *v = a.V + m * j;
+      double w = 0.0;
+      for (int64_t t = j + lane; t < m; t += 32) w = fma(__ldcg(v + t), qv[t], w);
+      w = warp_sum(w) * tau;
+      for (int64_t t = j + lane; t < m; t += 32) qv[t] = fma(-w, __ldcg(v + t), qv[t]);
+      __syncwarp();
+    }
+    double *dst = a.A + a.lda * l;
+    for (int64_t t = lane; t < m; t += 32) dst[t] = qv[t];
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Householder QR of a small matrix in one CTA (whole matrix in shared memory), optionally
+// column-pivoted with a noise-level cutoff. A = op(src) is m x n (op = transpose when
+// trans_src). Unpivoted: A = Q R, r = min(m, n). Pivoted (dgeqp3-style, columns swapped
+// physically): A P = Q R_p, stopping when the largest remaining column norm is at or below
+// cut_rel ||A||_F (r >= 1). Outputs: Q (m x r) explicit, written as Q or Q^T (trans_q); and
+// R = Q^T A in the ORIGINAL column order (r x n), written as R or R^T (trans_r); r to *r_out.
+// Warps own columns, lanes own rows; FP64 reductions stay within one warp.
+// ------------------------------------------------------------------------------------------
+constexpr int kSmallThreads = 256;
+
+struct QrSmallArgs {
+  const double *src;
+  int64_t lds;
+  int64_t m, n;
+  int trans_src, pivot, trans_q, trans_r;
+  double cut_rel;
+  double *Q;
+  int64_t ldq;
+  double *R;
+  int64_t ldr;
+  int64_t *r_out;
+};
+
+__global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
+  extern __shared__ double sm[];
+  const int64_t m = a.m, n = a.n;
+  const int64_t nref = m < n ? m : n;
+  double *A = sm;               // m x n, ld m
+  double *nrm = A + m * n;      // n
+  double *tau = nrm + n;        // nref
+  int *perm = reinterpret_cast<int *>(tau + nref);  // n
+  __shared__ double s_red[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_r;
+  __shared__ double s_cut2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kSmallThreads / 32;
+  for (int64_t idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
+    const int64_t i = idx % m, j = idx / m;
+    A[idx] = a.trans_src ? a.src[j + a.lds * i] : a.src[i + a.lds * j];
+  }
+  for (int64_t j = threadIdx.x; j < n; j += kSmallThreads) perm[j] = (int)j;
+  __syncthreads();
+  // column norms
+  for (int64_t j = warp; j < n; j += NW) {
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) s = fma(A[i + m * j], A[i + m * j], s);
+    s = warp_sum(s);
+    if (lane == 0) nrm[j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int64_t j = 0; j < n; ++j) f += nrm[j];
+    s_cut2 = a.cut_rel * a.cut_rel * f;
+    s_r = (int)nref;
+  }
+  __syncthreads();
+  for (int64_t i = 0; i < nref; ++i) {
+    if (a.pivot) {
+      // argmax of nrm[i..n-1] (lowest index on ties)
+      double bv = -1.0;
+      int bi = (int)i;
+      for (int64_t j = i + threadIdx.x; j < n; j += kSmallThreads) {
+        if (nrm[j] > bv) {
+          bv = nrm[j];
+          bi = (int)j;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_red[warp] = bv;
+        s_idx[warp] = bi;
+      }
       __syncthreads();
+      if (threadIdx.x == 0) {
+        double b = s_red[0];
+        int bj = s_idx[0];
+        for (int w = 1; w < NW; ++w)
+          if (s_red[w] > b || (s_red[w] == b && s_idx[w] < bj)) {
+            b = s_red[w];
+            bj = s_idx[w];
+          }
+        s_idx[0] = bj;
+        s_red[0] = b;
+        if (i > 0 && b <= s_cut2) s_r = (int)i;
+      }
+      __syncthreads();
+      if (s_r == (int)i) break;
+      const int64_t p = s_idx[0];
+      if (p != i) {
+        for (int64_t t = threadIdx.x; t < m; t += kSmallThreads) {
+          const double x = A[t + m * i];
+          A[t + m * i] = A[t + m * p];
+          A[t + m * p] = x;
+        }
+        if (threadIdx.x == 0) {
+          const double x = nrm[i];
+          nrm[i] = nrm[p];
+          nrm[p] = x;
+          const int q = perm[i];
+          perm[i] = perm[p];
+          perm[p] = q;
+        }
+      }
+      __syncthreads();
+    }
+    // reflector from A[i:, i] (warp 0)
+    if (warp == 0) {
+      double *col = A + m * i;
+      double sig = 0.0;
+      for (int64_t t = i + 1 + lane; t < m; t += 32) sig = fma(col[t], col[t], sig);
+      sig = warp_sum(sig);
+      const double alpha = col[i];
+      double tv = 0.0, beta = alpha, scal = 0.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tv = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      for (int64_t t = i + 1 + lane; t < m; t += 32) col[t] *= scal;  // v below the diagonal
+      __syncwarp();
+      if (lane == 0) {
+        col[i] = beta;
+        tau[i] = tv;
+      }
+    }
+    __syncthreads();
+    // apply to columns j > i and refresh their norms over rows > i
+    const double tv = tau[i];
+    const double *v = A + m * i;
+    for (int64_t j = i + 1 + warp; j < n; j += NW) {
+      double *col = A + m * j;
+      if (tv != 0.0) {
+        double w = lane == 0 ? col[i] : 0.0;
+        for (int64_t t = i + 1 + lane; t < m; t += 32) w = fma(v[t], col[t], w);
+        w = warp_sum(w) * tv;
+        if (lane == 0) col[i] -= w;
+        for (int64_t t = i + 1 + lane; t < m; t += 32) col[t] = fma(-w, v[t], col[t]);
+      }
+      if (a.pivot) {
+        double s = 0.0;
+        for (int64_t t = i + 1 + lane; t < m; t += 32) s = fma(col[t], col[t], s);
+        s = warp_sum(s);
+        if (lane == 0) nrm[j] = s;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t r = s_r;
+  if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
+  const int64_t ldq = a.ldq > 0 ? a.ldq : r;  // ldq <= 0: Q^T packed with leading dimension r
+  // R = rows 0..r-1 of the transformed matrix, upper trapezoid, scattered to original order
+  for (int64_t idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
+    const int64_t t = idx % r, j = idx / r;
+    const double x = t <= j ? A[t + m * j] : 0.0;
+    const int64_t oj = perm[j];
+    if (a.trans_r)
+      a.R[oj + a.ldr * t] = x;
+    else
+      a.R[t + a.ldr * oj] = x;
+  }
+  __syncthreads();
+  // Q = H_0 ... H_{r-1} [I_r; 0]: one warp per column, v_j read from below the diagonal
+  for (int64_t l = warp; l < r; l += NW) {
+    // the column is accumulated directly in the output buffer
+    double *q = a.trans_q ? nullptr : a.Q + ldq * l;
+    // accumulate in a strided view: element t at qa(t)
+    auto qa = [&](int64_t t) -> double & { return a.trans_q ? a.Q[l + ldq * t] : q[t]; };
+    for (int64_t t = lane; t < m; t += 32) qa(t) = (t == l) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int64_t j = l; j >= 0; --j) {
+      const double tj = tau[j];
+      if (tj == 0.0) continue;
+      const double *vj = A + m * j;
+      double w = 0.0;
+      for (int64_t t = j + lane; t < m; t += 32) w = fma(t == j ? 1.0 : vj[t], qa(t), w);
+      w = warp_sum(w) * tj;
+      for (int64_t t = j + lane; t < m; t += 32) qa(t) = fma(-w, t == j ? 1.0 : vj[t], qa(t));
+      __syncwarp();
     }
   }
 }
@@ -281,7 +671,12 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_coop(QrArgs a) {
 // One-sided Jacobi SVD of an n x n matrix in one CTA (Hestenes): rotate column pairs of G,
 // accumulating V, until every pair is orthogonal to |g_p^T g_q| <= tol ||g_p|| ||g_q||.
 // Pairs follow a round-robin tournament, so each round's pairs are disjoint and are
-// processed by different warps. Results sorted by descending singular value.
+// processed by different warps. Column norms are recomputed at the start of each sweep and
+// updated in between with ||g_p'||^2 = ||g_p||^2 - t gamma, ||g_q'||^2 = ||g_q||^2 + t gamma,
+// so a pair costs one dot product. Columns whose norm is at the rounding level of the whole
+// matrix (||g|| <= n eps ||G||_F) are numerically zero and are not rotated: rotating such a
+// column against a large one only re-injects rounding error and never converges.
+// Results sorted by descending singular value.
 // ------------------------------------------------------------------------------------------
 constexpr int kJacThreads = 512;
 
@@ -290,8 +685,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
   extern __shared__ double sm[];
   __shared__ int s_rot;
   __shared__ double s_norm[1024];
+  __shared__ double s_fro;
   const bool in_smem = Gw == nullptr;
-  double *g = in_smem ? sm : Gw;        // working copy, ld n
+  double *g = in_smem ? sm : Gw;          // working copy, ld n
   double *v = in_smem ? sm + n * n : Vw;  // working V, ld n
   for (int64_t idx = threadIdx.x; idx < n * n; idx += kJacThreads) {
     const int64_t i = idx % n, j = idx / n;
@@ -303,9 +699,26 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
   const int nw = kJacThreads / 32;
   const int64_t np = (n + 1) & ~int64_t(1);  // even number of players
   const double tol = DBL_EPSILON * (double)(n > 8 ? n : 8);
+  double floor2 = 0.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
+    for (int64_t j = warp; j < n; j += nw) {
+      double s = 0.0;
+      for (int64_t i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
+      s = warp_sum(s);
+      if (lane == 0) s_norm[j] = s;
+    }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
+    if (sweep == 0) {
+      if (threadIdx.x == 0) {
+        double f = 0.0;
+        for (int64_t j = 0; j < n; ++j) f += s_norm[j];
+        s_fro = f;
+      }
+      __syncthreads();
+      const double fl = (double)n * DBL_EPSILON;
+      floor2 = fl * fl * s_fro;
+    }
     for (int64_t round = 0; round < np - 1; ++round) {
       for (int64_t pr = warp; pr < np / 2; pr += nw) {
         int64_t p, q;
@@ -322,40 +735,38 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
           p = q;
           q = t;
         }
+        const double al = s_norm[p], be = s_norm[q];
+        if (al <= floor2 || be <= floor2) continue;
         double *gp = g + n * p, *gq = g + n * q;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int64_t i = lane; i < n; i += 32) {
-          const double x = gp[i], y = gq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        double ga = 0.0;
+        for (int64_t i = lane; i < n; i += 32) ga = fma(gp[i], gq[i], ga);
         ga = warp_sum(ga);
-        if (ga == 0.0 || al == 0.0 || be == 0.0) continue;
-        if (fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
         const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
         for (int64_t i = lane; i < n; i += 32) {
           const double x = gp[i], y = gq[i];
-          gp[i] = cs * x - sn * y;
-          gq[i] = sn * x + cs * y;
+          gp[i] = fma(-sn, y, cs * x);
+          gq[i] = fma(sn, x, cs * y);
         }
         double *vp = v + n * p, *vq = v + n * q;
         for (int64_t i = lane; i < n; i += 32) {
           const double x = vp[i], y = vq[i];
-          vp[i] = cs * x - sn * y;
-          vq[i] = sn * x + cs * y;
+          vp[i] = fma(-sn, y, cs * x);
+          vq[i] = fma(sn, x, cs * y);
         }
-        if (lane == 0) s_rot = 1;
+        if (lane == 0) {
+          s_norm[p] = fma(-t, ga, al);
+          s_norm[q] = fma(t, ga, be);
+          s_rot = 1;
+        }
       }
       __syncthreads();
     }
     if (!s_rot) break;
   }
-  // column norms
+  // final column norms
   for (int64_t j = warp; j < n; j += nw) {
     double s = 0.0;
     for (int64_t i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
@@ -483,7 +894,7 @@ int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double 
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_coop, kQrThreads, smem));
+  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_coop, 32, smem));
   const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? 1 : 0);
   if (P > cap) P = cap;
   if (P < 1) return TNR_ECUDA;
@@ -496,8 +907,108 @@ int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double 
     stats_work(K_QR, fact + org);
   }
   LaunchScope ls(K_QR, s);
-  TNR_CK(cudaLaunchCooperativeKernel((void *)k_qr_coop, dim3((unsigned)P), dim3(kQrThreads), args, smem, s));
+  TNR_CK(cudaLaunchCooperativeKernel((void *)k_qr_coop, dim3((unsigned)P), dim3(32), args, smem, s));
   return TNR_OK;
+}
+
+size_t qrcp_scratch(int64_t m, int64_t n) {
+  const int64_t nref = m < n ? m : n;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(sizeof(double) * m * (nref > 0 ? nref : 1)) + al(sizeof(double) * (nref + 1)) +
+         al(sizeof(unsigned long long) * (nref + 1)) + al(sizeof(unsigned) * (nref + 2)) +
+         al(sizeof(unsigned) * (nref + 1)) + al(sizeof(double)) + al(sizeof(int64_t));
+}
+
+size_t qrcp_scratch_bound(int64_t max_elems, int64_t max_n) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(sizeof(double) * (max_elems > 0 ? max_elems : 1)) + al(sizeof(double) * (max_n + 1)) +
+         al(sizeof(unsigned long long) * (max_n + 1)) + al(sizeof(unsigned) * (max_n + 2)) +
+         al(sizeof(unsigned) * (max_n + 1)) + al(sizeof(double)) + al(sizeof(int64_t));
+}
+
+int qrcp_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double *Rout, int64_t ldr, double cut_rel,
+             void *scratch, int64_t *r_dev, bool *used) {
+  *used = false;
+  if (m <= 0 || n <= 0) return TNR_OK;
+  const int64_t nref = m < n ? m : n;
+  int64_t P = std::min<int64_t>(n, num_sms());
+  const int64_t nc = cdiv(n, P);
+  const size_t smem = sizeof(double) * (nc * m + m + nc) + sizeof(int) * nc;
+  if (smem > 200 * 1024 || n >= 0xFFFFF) return TNR_OK;  // caller falls back to the unpivoted kernel
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  char *p = static_cast<char *>(scratch);
+  QrcpArgs a;
+  a.A = A;
+  a.m = m;
+  a.n = n;
+  a.lda = lda;
+  a.R = Rout;
+  a.ldr = ldr;
+  a.V = reinterpret_cast<double *>(p);
+  p += al(sizeof(double) * m * nref);
+  a.tau = reinterpret_cast<double *>(p);
+  p += al(sizeof(double) * (nref + 1));
+  a.best = reinterpret_cast<unsigned long long *>(p);
+  char *zero_begin = p;
+  p += al(sizeof(unsigned long long) * (nref + 1));
+  a.cnt = reinterpret_cast<unsigned *>(p);
+  p += al(sizeof(unsigned) * (nref + 2));
+  a.flags = reinterpret_cast<unsigned *>(p);
+  p += al(sizeof(unsigned) * (nref + 1));
+  a.fro2 = reinterpret_cast<double *>(p);
+  p += al(sizeof(double));
+  char *zero_end = p;
+  a.r_out = r_dev;
+  a.cut_rel = cut_rel;
+  a.status = status_ptr();
+  TNR_CK(cudaMemsetAsync(zero_begin, 0, zero_end - zero_begin, s));
+  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrcp, 32, smem));
+  if (per_sm < 1) return TNR_OK;
+  void *args[] = {&a};
+  LaunchScope ls(K_QR, s);
+  TNR_CK(cudaLaunchCooperativeKernel((void *)k_qrcp, dim3((unsigned)P), dim3(32), args, smem, s));
+  *used = true;
+  return TNR_OK;
+}
+
+bool qr_small_fits(int64_t m, int64_t n) {
+  const int64_t nref = m < n ? m : n;
+  const size_t smem = sizeof(double) * (m * n + n + nref) + sizeof(int) * n;
+  return smem <= 200 * 1024;
+}
+
+int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int64_t n, bool trans_src, bool pivot,
+                 double cut_rel, double *Q, int64_t ldq, bool trans_q, double *R, int64_t ldr, bool trans_r,
+                 int64_t *r_dev) {
+  if (m <= 0 || n <= 0) return TNR_OK;
+  if (!qr_small_fits(m, n)) return TNR_EINVAL;
+  const int64_t nref = m < n ? m : n;
+  const size_t smem = sizeof(double) * (m * n + n + nref) + sizeof(int) * n;
+  QrSmallArgs a;
+  a.src = src;
+  a.lds = lds;
+  a.m = m;
+  a.n = n;
+  a.trans_src = trans_src;
+  a.pivot = pivot;
+  a.trans_q = trans_q;
+  a.trans_r = trans_r;
+  a.cut_rel = cut_rel;
+  a.Q = Q;
+  a.ldq = ldq;
+  a.R = R;
+  a.ldr = ldr;
+  a.r_out = r_dev;
+  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    const double M = (double)m, N = (double)n, P = (double)nref;
+    stats_work(K_QR, 2 * M * N * P - (M + N) * P * P + 2 * P * P * P / 3 + 2 * M * P * P - 2 * P * P * P / 3);
+  }
+  LaunchScope ls(K_QR, s);
+  k_qr_small<<<1, kSmallThreads, smem, s>>>(a);
+  return check_cuda(cudaGetLastError());
 }
 
 size_t jacobi_scratch(int64_t n) {

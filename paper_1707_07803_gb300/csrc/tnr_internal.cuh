@@ -104,6 +104,25 @@ size_t qr_scratch_bound(int64_t max_elems, int64_t max_n);
 int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double *Rout, int64_t ldr,
            void *scratch);
 
+// Rank-revealing QR with noise cutoff (column pivoting): A <- Q (m x r, explicit), Rout <- R
+// = Q^T A (r x n, original column order, ldr >= min(m, n)); r written to *r_dev (device).
+// Directions whose residual column norm is <= cut_rel * ||A||_F are dropped (r >= 1).
+// *used = false when the matrix does not fit the shared-memory layout (nothing launched).
+size_t qrcp_scratch(int64_t m, int64_t n);
+size_t qrcp_scratch_bound(int64_t max_elems, int64_t max_n);
+int qrcp_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double *Rout, int64_t ldr, double cut_rel,
+             void *scratch, int64_t *r_dev, bool *used);
+
+// Small-matrix Householder QR in one CTA (matrix in shared memory): A = op(src) (m x n);
+// optional column pivoting with a cutoff (see k_qr_small). Q (m x r) written as Q or Q^T,
+// R = Q^T A (r x n, original column order) written as R or R^T; r to *r_dev (may be null when
+// not pivoting: r = min(m, n)). The source is read completely before any output is written,
+// so Q or R may overwrite it. ldq <= 0 packs Q^T with leading dimension r (known on device).
+bool qr_small_fits(int64_t m, int64_t n);
+int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int64_t n, bool trans_src, bool pivot,
+                 double cut_rel, double *Q, int64_t ldq, bool trans_q, double *R, int64_t ldr, bool trans_r,
+                 int64_t *r_dev);
+
 // SVD of the n x n matrix G (ldg) by one-sided Jacobi: G <- U (columns), S (descending),
 // V (n x n, ldv) with G_in = U diag(S) V^T. `sweeps_out` (device int, may be null).
 size_t jacobi_scratch(int64_t n);

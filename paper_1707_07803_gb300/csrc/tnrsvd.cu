@@ -206,7 +206,8 @@ void carve(Arena &ar, const Limits &L, Bufs &b) {
   b.Sv = ar.take<double>(L.maxsq);
   b.US = ar.take<double>(L.maxcore);
   // every QR factors a core-sized matrix (m * n <= maxcore) with n <= max(maxbond, maxsq)
-  b.qr = ar.take<char>(qr_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq)));
+  b.qr = ar.take<char>(std::max(qr_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq)),
+                                 qrcp_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq))));
   b.jac = ar.take<char>(std::max<size_t>(jacobi_scratch(L.maxsq), 256));
   b.norm2 = ar.take<double>(1);
   b.rdev = ar.take<int64_t>(1);
@@ -218,19 +219,66 @@ int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
   return st;
 }
 
+// Exact right-to-left compression before the rounding sweeps (used when tol > 0). Products
+// multiply ranks (R_k S_k) but their numerical ranks are often far lower, and the redundancy
+// sits in the right parts of the product (e.g. A^T Q = V (S U^T Q) keeps V's bonds), where a
+// left-to-right orthogonalisation cannot see it. For k = d-1..1: M_k (t x w) = L Q_k by a
+// column-pivoted QR of M_k^T that stops once every remaining column norm is below
+// cut * ||M_k||_F, cut = min(64 eps, tol / 100); Q_k (orthonormal rows) replaces the core and L
+// is absorbed into core k-1. Only directions at the rounding level of M_k are dropped (the size
+// of a Householder factorisation's own backward error, far below the truncation threshold), so
+// the rounding that follows returns the same result to rounding accuracy, on bonds of the
+// numerical rank instead of R_k S_k.
+int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double tol) {
+  const double cut = std::min(64.0 * 2.220446049250313e-16, 0.01 * tol);
+  for (int k = Y.d - 1; k >= 1; --k) {
+    const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
+    int64_t r = 0;
+    if (qr_small_fits(w, t)) {
+      // M^T (w x t) = Q~ R~ P^T; core_k <- Q~^T (r x w, packed), b.Rbuf <- R~^T (t x r)
+      TNR_TRY(qr_small_f64(s, Y.core[k], t, w, t, true, true, cut, Y.core[k], 0, true, b.Rbuf, t, true, b.rdev));
+      TNR_TRY(d2h_rank(s, b.rdev, &r));
+    } else {
+      TNR_TRY(copy_matrix_f64(s, Y.core[k], t, b.Mq, w, w, t, true));  // M^T (w x t)
+      bool used = false;
+      TNR_TRY(qrcp_f64(s, b.Mq, w, t, w, b.US, std::min(w, t), cut, b.qr, b.rdev, &used));
+      if (!used) continue;  // too large for the pivoted kernels: leave this bond as it is
+      TNR_TRY(d2h_rank(s, b.rdev, &r));
+      TNR_TRY(copy_matrix_f64(s, b.Mq, w, Y.core[k], r, r, w, true));   // Q~^T (r x w)
+      TNR_TRY(copy_matrix_f64(s, b.US, std::min(w, t), b.Rbuf, t, t, r, true));  // R~^T (t x r)
+    }
+    const int64_t rows = Y.R[k - 1] * Y.I[k - 1] * Y.J[k - 1];
+    TNR_TRY(gemm_f64(s, false, false, rows, r, t, 1.0, Y.core[k - 1], rows, 0, b.Rbuf, t, 0, 0.0, b.tmp, rows, 0));
+    TNR_CK(cudaMemcpyAsync(Y.core[k - 1], b.tmp, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));
+    Y.R[k] = r;
+  }
+  return TNR_OK;
+}
+
 // Left-to-right Householder QR sweep (rounding part 1, Section 5.4): core k reshaped
 // (R_k I_k J_k) x R_{k+1} = Q R; Q replaces the core, R is absorbed into core k+1.
 int sweep_lr(cudaStream_t s, tnr_mpo &Y, Bufs &b) {
   for (int k = 0; k + 1 < Y.d; ++k) {
     const int64_t rows = Y.R[k] * Y.I[k] * Y.J[k], cols = Y.R[k + 1];
     const int64_t n = std::min(rows, cols);
-    TNR_TRY(qr_f64(s, Y.core[k], rows, cols, rows, b.Rbuf, n, b.qr));
+    if (qr_small_fits(rows, cols))
+      TNR_TRY(qr_small_f64(s, Y.core[k], rows, rows, cols, false, false, 0.0, Y.core[k], rows, false, b.Rbuf, n, false,
+                           nullptr));
+    else
+      TNR_TRY(qr_f64(s, Y.core[k], rows, cols, rows, b.Rbuf, n, b.qr));
     const int64_t w = Y.I[k + 1] * Y.J[k + 1] * Y.R[k + 2];
     TNR_TRY(gemm_f64(s, false, false, n, w, cols, 1.0, b.Rbuf, n, 0, Y.core[k + 1], cols, 0, 0.0, b.tmp, n, 0));
     TNR_CK(cudaMemcpyAsync(Y.core[k + 1], b.tmp, sizeof(double) * n * w, cudaMemcpyDeviceToDevice, s));
     Y.R[k + 1] = n;
   }
   return TNR_OK;
+}
+
+// Plain thin QR, small-matrix kernel when it fits: A (m x n, lda = m) <- Q, R (min x n, ldr).
+int thin_qr(cudaStream_t s, double *A, int64_t m, int64_t n, double *R, int64_t ldr, Bufs &b) {
+  if (qr_small_fits(m, n))
+    return qr_small_f64(s, A, m, m, n, false, false, 0.0, A, m, false, R, ldr, false, nullptr);
+  return qr_f64(s, A, m, n, m, R, ldr, b.qr);
 }
 
 // Truncated SVD of M (t x w, ld t) for the right-to-left sweep: writes V^T[:r] (r x w) into
@@ -240,7 +288,7 @@ int svd_trunc(cudaStream_t s, const double *M, int64_t t, int64_t w, double tol,
   int64_t r = 0;
   if (t >= w) {
     TNR_TRY(copy_matrix_f64(s, M, t, b.Mq, t, t, w, false));
-    TNR_TRY(qr_f64(s, b.Mq, t, w, t, b.Rm, w, b.qr));  // Mq <- Q_m (t x w), Rm (w x w)
+    TNR_TRY(thin_qr(s, b.Mq, t, w, b.Rm, w, b));  // Mq <- Q_m (t x w), Rm (w x w)
     TNR_TRY(jacobi_svd_f64(s, b.Rm, w, w, b.Sv, b.Vr, w, b.jac));  // Rm <- U_r
     {
       LaunchScope ls(K_MISC, s);
@@ -252,7 +300,7 @@ int svd_trunc(cudaStream_t s, const double *M, int64_t t, int64_t w, double tol,
     TNR_TRY(gemm_f64(s, false, false, t, r, w, 1.0, b.Mq, t, 0, b.Rm, w, 0, 0.0, b.US, t, 0));
   } else {
     TNR_TRY(copy_matrix_f64(s, M, t, b.Mq, w, w, t, true));  // M^T (w x t)
-    TNR_TRY(qr_f64(s, b.Mq, w, t, w, b.Rm, t, b.qr));  // Mq <- Q_m (w x t), Rm (t x t)
+    TNR_TRY(thin_qr(s, b.Mq, w, t, b.Rm, t, b));  // Mq <- Q_m (w x t), Rm (t x t)
     TNR_TRY(copy_matrix_f64(s, b.Rm, t, b.G, t, t, t, true));  // G = Rm^T
     TNR_TRY(jacobi_svd_f64(s, b.G, t, t, b.Sv, b.Vr, t, b.jac));  // G <- U
     {
@@ -300,13 +348,14 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b) {
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, tol));
   TNR_TRY(sweep_lr(s, Y, b));
   TNR_TRY(sweep_rl(s, Y, tol, max_rank, b));
   const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
   const int64_t m = I1 * t;
   if (m < K) return TNR_EINVAL;
   TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
-  TNR_TRY(qr_f64(s, b.Mq, m, K, m, b.Rm, K, b.qr));  // A1^T = Q~ R~
+  TNR_TRY(thin_qr(s, b.Mq, m, K, b.Rm, K, b));  // A1^T = Q~ R~
   if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
   TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
   return TNR_OK;
@@ -317,6 +366,7 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 // kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, tol));
   TNR_TRY(sweep_lr(s, Z, b));
   TNR_TRY(sweep_rl(s, Z, tol, max_rank, b));
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
@@ -324,7 +374,7 @@ int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs 
   if (m < K) return TNR_EINVAL;
   if (J1 * kout * t > v1cap) return TNR_ENOMEM;
   TNR_TRY(site1_perm(s, Z.core[0], b.Mq, J1, K, t, K, 0));  // M^T ((J1 t) x K)
-  TNR_TRY(qr_f64(s, b.Mq, m, K, m, b.Rm, K, b.qr));         // M^T = Q~ R~
+  TNR_TRY(thin_qr(s, b.Mq, m, K, b.Rm, K, b));  // M^T = Q~ R~
   TNR_TRY(copy_matrix_f64(s, b.Rm, K, Wout, K, K, K, true));  // R~^T
   TNR_TRY(jacobi_svd_f64(s, Wout, K, K, Sout, b.Vr, K, b.jac));  // R~^T = W S Zr^T
   // V = Q~ Zr ((J1 t) x K), then V^(1) columns < kout

@@ -20,6 +20,7 @@
 //   k_fill        per first-occurrence entry: block index t, zero block t of X, scatter the
 //                 block's entries (gathered from the I1 rows of the segment), write digits.
 #include <cstdio>
+#include <mutex>
 
 #include "tnr_internal.cuh"
 
@@ -359,6 +360,90 @@ extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const 
   {
     LaunchScope ls(K_CONV_FILL, s);
     k_fill<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R,
+                                                     status_ptr());
+  }
+  TNR_CK(cudaGetLastError());
+  return TNR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Conversion without any device allocation (no counterpart in the paper).
+//
+// The scratch that tnr_sparse_count/fill take from the caller's workspace (one int32 prefix
+// count per nonzero plus one int32 per 1024-entry tile) lives here in a file-scope device array
+// instead, sized for TNR_NOALLOC_MAX_NNZ nonzeros (32 MiB + 32 KiB). Every GPU that loads the
+// library holds this array until the process exits. Host code must not hand the array's name
+// to a kernel (in host code it is only a stand-in symbol); its device address is looked up
+// once per device with cudaGetSymbolAddress while that device is current, on the first call
+// made on that device. Nothing in the array has to start at zero: each call writes every
+// entry it later reads. All calls share the array, so calls whose kernels overlap on the GPU
+// (different streams, or different host threads on the same device) race.
+// ---------------------------------------------------------------------------------------------
+namespace tnr {
+namespace {
+
+constexpr int64_t kNoAllocTiles = (TNR_NOALLOC_MAX_NNZ + kTile - 1) / kTile;
+static __device__ __align__(256) int32_t g_noalloc_scratch[TNR_NOALLOC_MAX_NNZ + kNoAllocTiles + 64];
+
+std::mutex g_noalloc_mu;
+int32_t *g_noalloc_ptr[TNR_MAX_SITES] = {nullptr};  // per device ordinal (first 64 devices)
+
+int noalloc_scratch(int32_t **out) {
+  int dev = 0;
+  TNR_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= TNR_MAX_SITES) return TNR_ERANGE;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    TNR_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<int32_t *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TNR_OK;
+}
+
+}  // namespace
+}  // namespace tnr
+
+extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row,
+                                         const int64_t *col, const double *val, int32_t d, const int64_t *I,
+                                         const int64_t *J, double *X, uint8_t *digits, int64_t max_blocks,
+                                         int64_t *R_out, void *stream) {
+  ConvDims D;
+  TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
+  if (!R_out || max_blocks < 0) return TNR_EINVAL;
+  if (nnz > TNR_NOALLOC_MAX_NNZ) return TNR_ERANGE;
+  if (nnz == 0) {
+    *R_out = 0;
+    return TNR_OK;
+  }
+  if (!row || !col || !val || !X || (d > 1 && !digits)) return TNR_EINVAL;
+  int32_t *scratch = nullptr;
+  TNR_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t ntiles = cdiv(nnz, kTile);
+  int32_t *F_local = scratch;
+  int32_t *tile_off = scratch + TNR_NOALLOC_MAX_NNZ;
+  TNR_TRY(reset_status(s));
+  {
+    LaunchScope ls(K_CONV_FLAGS, s);
+    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, status_ptr());
+  }
+  TNR_CK(cudaGetLastError());
+  {
+    LaunchScope ls(K_CONV_SCAN, s);
+    k_tile_scan<<<1, 1024, 0, s>>>(tile_off, ntiles);
+  }
+  TNR_CK(cudaGetLastError());
+  int32_t total = 0;
+  TNR_CK(cudaMemcpyAsync(&total, tile_off + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int st = read_status(s);  // synchronises
+  if (st != TNR_OK) return st;
+  *R_out = total;
+  if (total > max_blocks) return TNR_ENOMEM;  // X and digits untouched
+  {
+    LaunchScope ls(K_CONV_FILL, s);
+    k_fill<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, total,
                                                      status_ptr());
   }
   TNR_CK(cudaGetLastError());

@@ -68,6 +68,8 @@ _SIGS = {
     "tnr_sparse_count": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _I32, _I64P, _I64P, _I64P, _P, ctypes.c_size_t, _P]),
     "tnr_sparse_fill": (ctypes.c_int,
                         [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _I64, _P, _P, _P, ctypes.c_size_t, _P]),
+    "tnr_sparse_to_mpo_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _P, _P, _I64,
+                                                  _I64P, _P]),
     "tnr_mpo_contract": (ctypes.c_int, [_MPOP, _I32, _MPOP, _MPOP, _P]),
     "tnr_orthogonalize_workspace": (ctypes.c_int, [_MPOP, _SZP]),
     "tnr_orthogonalize": (ctypes.c_int, [_MPOP, _P, _OPTP, _P, ctypes.c_size_t, _P]),
@@ -217,6 +219,24 @@ def sparse_to_mpo(nrows, ncols, row, col, val, I, J, stream=None):
     digits = torch.empty(max(R * 2 * (len(I) - 1), 1), dtype=torch.uint8, device=row.device)
     tnr_sparse_fill(nrows, ncols, row, col, val, I, J, R, X, digits, ws, stream)
     return R, X[: R * int(I[0]) * int(J[0])], digits[: R * 2 * (len(I) - 1)].view(R, 2 * (len(I) - 1))
+
+
+NOALLOC_MAX_NNZ = 8388608
+
+
+def tnr_sparse_to_mpo_noalloc(nrows, ncols, row, col, val, I, J, X, digits, max_blocks, stream=None):
+    """Alg. 4.1 without any device allocation by the library (scratch compiled into it).
+
+    The caller passes the outputs X (max_blocks*I1*J1 doubles) and digits (max_blocks*2(d-1)
+    bytes); returns R. Limits and races: see include/tnrsvd.h.
+    """
+    lib = load()
+    _need_cuda(row, col, val, X)
+    R = ctypes.c_int64(0)
+    _check(lib.tnr_sparse_to_mpo_noalloc(nrows, ncols, row.numel(), _ptr(row), _ptr(col), _ptr(val), len(I),
+                                         _i64arr(I), _i64arr(J), _ptr(X), _ptr(digits), int(max_blocks),
+                                         ctypes.byref(R), _stream(stream)), "tnr_sparse_to_mpo_noalloc")
+    return R.value
 
 
 def tnr_mpo_contract(A, trans, X, Y_caps=None, stream=None):

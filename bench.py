@@ -27,14 +27,17 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "TNrSVD solves/s (2^20 x 2^20 MPO, sigma_j = 0.7^j, k=16 p=16 q=2)"
+DTYPES = {"mixed": "bf16x3/f64", "fp64": "f64"}
 UNIT = "solves/s"
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 
-def workload_config():
+def workload_config(precision="mixed"):
     c = W.c2_prescribed()
     cfg = {
         "workload": "prescribed-sigma MPO 2^20 x 2^20 (merged sites 64,4^7; A ranks 25), k=16 p=16 q=2, seed 2",
+        "precision": ("products BF16 x3 on tcgen05 / FP32 accumulate, sweeps + SVD + B in FP64"
+                      if precision == "mixed" else "all FP64"),
         "global_batch": 1,
         "seq_len": 0,
         "tol": c["tol"],
@@ -151,7 +154,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -171,9 +174,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    c, cfg = workload_config()
+    c, cfg = workload_config(args.precision)
     A = T.Mpo.from_numpy(c["A"], device=dev)
-    precision = T.TNR_FP64
+    precision = T.TNR_MIXED if args.precision == "mixed" else T.TNR_FP64
     plan = T.SolvePlan(A, c["k"], c["p"], tol=c["tol"], max_rank=c["max_rank"], precision=precision)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -184,8 +187,9 @@ def main():
     # dominant kernel class for the roofline: the FP64 Householder QR
     classes = T.stats_classes()
     qr_cls = classes.index("qr")
+    tc_cls = classes.index("contract_tc")
     T.stats_reset()
-    T.stats_enable(1 << qr_cls)
+    T.stats_enable((1 << qr_cls) | (1 << tc_cls))
     sampler = ClockSampler(local)
     sampler.start()
     if world > 1:
@@ -206,6 +210,8 @@ def main():
     launches, _ = T.stats(-1)
     qr_launches, qr_ms = T.stats(qr_cls)
     qr_flops = T.stats_work(qr_cls)
+    tc_launches, tc_ms = T.stats(tc_cls)
+    tc_flops = T.stats_work(tc_cls)
     T.stats_enable(0)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -250,7 +256,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic", "config": cfg,
         "e2e": {"value": world * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -260,9 +266,19 @@ def main():
                      "frac": achieved_gflops / FP64_NOMINAL_GFLOPS, "traffic": None,
                      "launches_per_step": qr_launches / args.steps, "avg_launch_us": 1000 * qr_avg_ms,
                      "share_of_step": qr_ms / max(total_ms, 1e-9)},
+        "contraction": ({"kernel": "k_tc_gemm (tcgen05 BF16 x3, FP32 accumulate)", "bound": "tensor",
+                         "launches_per_step": tc_launches / args.steps,
+                         "avg_launch_us": 1000 * tc_ms / max(tc_launches, 1),
+                         "achieved": (tc_flops / max(tc_launches, 1)) / (tc_ms / max(tc_launches, 1) * 1e-3) / 1e12
+                         if tc_launches else 0.0,
+                         "peak": read_peaks().get("bf16_tflops"), "unit": "TFLOP/s",
+                         "peak_source": "bf16_tflops of MEASURED_PEAKS.json (measured burst)",
+                         "share_of_step": tc_ms / max(total_ms, 1e-9)} if tc_launches else None),
         "accuracy": {"sv_rel_err_vs_exact": sv_err},
         "clocks": clocks,
     }
+    if line["contraction"] and line["contraction"]["peak"]:
+        line["contraction"]["frac"] = line["contraction"]["achieved"] / line["contraction"]["peak"]
     if rank == 0:
         rate, n, el, So = run_oracle_sample(c, args.cpu_budget)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -51,8 +51,10 @@ enum tnr_status {
 
 enum tnr_precision {
   TNR_FP64 = 0,  /* every step in float64 */
-  TNR_MIXED = 1  /* products A*Omega, A^T Q, A Q on tensor cores (bf16 in, fp32 accumulate);
-                    B = Q^T A, the QR sweeps and the SVDs in float64 */
+  TNR_MIXED = 1  /* products A*Omega, A^T Q, A Q in BF16 (x3 split, FP32 accumulation; the dense
+                    site-1 products on tcgen05 tensor cores), their roundings at tolerance
+                    max(tol, 1.2e-4) (the products' noise level); B = Q^T A, its rounding with
+                    tol, the QR sweeps and the SVDs in float64 */
 };
 
 /* MPO descriptor (host memory). For inputs only d, I, J, R and core are read. For outputs
@@ -136,10 +138,13 @@ int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t nnz, const i
  * row dims n_k equal J_k (trans = 0) or I_k (trans = 1). Per site
  *   Y_k((r,s), i, c, (r',s')) = sum_j A_k(r,i,j,r') X_k(s,j,c,s')     (trans = 0)
  * with product bonds numbered r + R_k s; ranks multiply. Y's descriptor: the caller sets
- * core and cap; the library sets d, I, J, R. Precision: TNR_FP64 only through this entry
- * (the mixed-precision products run inside tnr_solve). Errors: TNR_EINVAL, TNR_ENOMEM.
+ * core and cap; the library sets d, I, J, R. precision = TNR_FP64: FP64 arithmetic.
+ * precision = TNR_MIXED: every operand is rounded to BF16 as hi + lo (hi = bf16(x),
+ * lo = bf16(x - hi)) and the products hi*hi + hi*lo + lo*hi are accumulated in FP32 (about
+ * 1e-5 relative per product); dense sites (both outer bonds 1, shared dim >= 16) run on the
+ * tcgen05 tensor cores. Errors: TNR_EINVAL, TNR_ENOMEM.
  * ------------------------------------------------------------------------------------- */
-int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, void *stream);
+int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, int32_t precision, void *stream);
 
 /* ---------------------------------------------------------------------------------------
  * MPO-QR with integrated rounding, Alg. 5.2 + Section 5.4, in place: Y (a tall matrix MPO,

@@ -1,0 +1,247 @@
+// Tensor-core (tcgen05) contraction for the mixed-precision MPO products (Section 5.2).
+//
+// The site-1 product of A with Omega or Q is a dense GEMM (M = R2 * physical rows,
+// N = K * S2, reduction over the shared physical index I1 or J1). It runs on the 5th-generation
+// tensor cores: one elected thread issues tcgen05.mma.cta_group::1.kind::f16 with BF16 operands
+// staged in shared memory (no-swizzle K-major core-matrix layout: 8 rows x 16 B per core matrix,
+// LBO = 128 B between K-adjacent core matrices, SBO = (BK/8) * 128 B between 8-row groups) and
+// FP32 accumulators in tensor memory (TMEM), read back with tcgen05.ld into registers for the
+// FP64 epilogue store. Operands are FP64 in HBM and are rounded to BF16 while staging. With
+// `split`, each operand x is written as hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the tile
+// product accumulates hi*hi + hi*lo + lo*hi: three BF16 MMAs per K-step give about 16 mantissa
+// bits per product, FP32-class accuracy, at tensor-core speed.
+//
+// Synchronisation: the MMA completion is signalled by tcgen05.commit on an mbarrier; every
+// wait on it is bounded (kSpinCap polls) and records TNR_ETIMEOUT on expiry, after which the
+// CTA still frees its TMEM before returning.
+#include <cuda_bf16.h>
+
+#include <cstdio>
+
+#include "tnr_internal.cuh"
+
+namespace tnr {
+namespace {
+
+constexpr int kTcM = 128;      // MMA M (cta_group::1)
+constexpr int kTcBK = 64;      // K elements staged per stage (4 MMAs of K = 16)
+constexpr int kTcThreads = 128;
+
+// index i -> (i % n1) * s1 + (i / n1) * s2
+struct IdxMap {
+  int64_t n1, s1, s2;
+  __device__ __forceinline__ int64_t operator()(int64_t i) const { return (i % n1) * s1 + (i / n1) * s2; }
+};
+
+struct TcArgs {
+  const double *A;  // element (m, k) at A[amap(m) + k * a_ks]
+  IdxMap amap;
+  int64_t a_ks;
+  const double *B;  // element (n, k) at B[bmap(n) + k * b_ks]
+  IdxMap bmap;
+  int64_t b_ks;
+  double *C;  // element (m, n) at C[crow(m) + ccol(n)]
+  IdxMap crow, ccol;
+  int64_t M, N, K;
+  int BN;        // N tile (multiple of 16, <= 256)
+  int tmem_cols; // power of two >= max(32, BN)
+  int split;
+  int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// byte offset of element (r, k) in a K-major no-swizzle tile with BK columns
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k) {
+  return (uint32_t)((r >> 3) * (kTcBK / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
+  for (long long it = 0; it < kSpinCap; ++it) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  set_status(status, TNR_ETIMEOUT);
+  return false;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+  const int64_t n0 = (int64_t)blockIdx.y * a.BN;
+  const int parts = a.split ? 2 : 1;
+  // stage layout: A_hi, A_lo, B_hi, B_lo (bf16 tiles)
+  const uint32_t a_bytes = kTcM * kTcBK * 2, b_bytes = (uint32_t)a.BN * kTcBK * 2;
+  unsigned char *sA[2] = {tsm, tsm + a_bytes};
+  unsigned char *sB[2] = {tsm + parts * a_bytes, tsm + parts * a_bytes + b_bytes};
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  const uint32_t sbo = (kTcBK / 8) * 128, lbo = 128;
+  uint32_t phase = 0;
+  const int64_t nkb = (a.K + kTcBK - 1) / kTcBK;
+  for (int64_t kb = 0; kb < nkb; ++kb) {
+    const int64_t k0 = kb * kTcBK;
+    // stage A (128 x BK) and B (BN x BK), FP64 -> BF16 (hi, lo)
+    for (int idx = threadIdx.x; idx < kTcM * kTcBK; idx += kTcThreads) {
+      const int r = a.a_ks == 1 ? idx / kTcBK : idx % kTcM;
+      const int k = a.a_ks == 1 ? idx % kTcBK : idx / kTcM;
+      const int64_t gm = m0 + r, gk = k0 + k;
+      double x = 0.0;
+      if (gm < a.M && gk < a.K) x = a.A[a.amap(gm) + gk * a.a_ks];
+      const __nv_bfloat16 hi = __double2bfloat16(x);
+      *reinterpret_cast<__nv_bfloat16 *>(sA[0] + kmajor_off(r, k)) = hi;
+      if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sA[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
+    }
+    for (int idx = threadIdx.x; idx < a.BN * kTcBK; idx += kTcThreads) {
+      const int r = a.b_ks == 1 ? idx / kTcBK : idx % a.BN;
+      const int k = a.b_ks == 1 ? idx % kTcBK : idx / a.BN;
+      const int64_t gn = n0 + r, gk = k0 + k;
+      double x = 0.0;
+      if (gn < a.N && gk < a.K) x = a.B[a.bmap(gn) + gk * a.b_ks];
+      const __nv_bfloat16 hi = __double2bfloat16(x);
+      *reinterpret_cast<__nv_bfloat16 *>(sB[0] + kmajor_off(r, k)) = hi;
+      if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sB[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
+    }
+    // make generic-proxy smem writes visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kk = 0; kk < kTcBK; kk += 16) {
+        const uint32_t koff = (uint32_t)(kk / 8) * 128;
+        // (A part, B part) pairs: hi*hi, then hi*lo and lo*hi when split
+        const int npairs = a.split ? 3 : 1;
+        for (int pr = 0; pr < npairs; ++pr) {
+          const int ap = pr == 2 ? 1 : 0, bp = pr == 1 ? 1 : 0;
+          const uint64_t ad = make_desc(smem_u32(sA[ap]) + koff, lbo, sbo);
+          const uint64_t bd = make_desc(smem_u32(sB[bp]) + koff, lbo, sbo);
+          const uint32_t acc = (kb > 0 || kk > 0 || pr > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar))
+                   : "memory");
+    }
+    // wait for the MMAs before the next stage overwrites the tiles (and before the epilogue)
+    if (!mbar_wait(smem_u32(&mbar), phase, a.status)) {
+      if (threadIdx.x == 0) s_abort = 1;
+    }
+    phase ^= 1;
+    __syncthreads();
+    if (s_abort) break;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!s_abort) {
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
+    const int64_t gm = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < a.BN; c0 += 8) {
+      uint32_t v[8];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (gm < a.M) {
+        const int64_t rowoff = a.crow(gm);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int64_t gn = n0 + c0 + j;
+          if (gn < a.N) a.C[rowoff + a.ccol(gn)] = (double)__uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+}  // namespace
+
+// Site-level tensor-core product for a site with R = S = 1 boundary bonds on the left (site 1):
+// Y(0, xo, c, (r2, s2)) = sum_y A(0, i, j, r2) X(0, y, c, s2), (xo, y) = (i, j) or (j, i).
+int contract_site1_tc(cudaStream_t s, const double *A, int64_t I, int64_t J, int64_t R2, const double *X, int64_t Kx,
+                      int64_t S2, int trans, double *Y, bool split) {
+  TcArgs a;
+  const int64_t Xo = trans ? J : I, Ny = trans ? I : J;
+  a.A = A;
+  if (!trans) {  // rows (i, r2), k = j: A(i, j, r2) at i + I j + I J r2
+    a.amap = {I, 1, I * J};
+    a.a_ks = I;
+  } else {  // rows (j, r2), k = i: A(i, j, r2) at i + I j + I J r2
+    a.amap = {J, I, I * J};
+    a.a_ks = 1;
+  }
+  a.B = X;  // X(0, y, c, s2) at y + Ny (c + Kx s2): cols (c, s2), k = y
+  a.bmap = {Kx, Ny, Ny * Kx};
+  a.b_ks = 1;
+  a.C = Y;  // Y(0, xo, c, r2 + R2 s2) at xo + Xo (c + Kx (r2 + R2 s2))
+  a.crow = {Xo, 1, Xo * Kx};
+  a.ccol = {Kx, Xo, Xo * Kx * R2};
+  a.M = Xo * R2;
+  a.N = Kx * S2;
+  a.K = Ny;
+  int64_t bn = ((a.N + 15) / 16) * 16;
+  if (bn > 256) bn = 256;
+  a.BN = (int)bn;
+  int tc = 32;
+  while (tc < a.BN) tc <<= 1;
+  a.tmem_cols = tc;
+  a.split = split ? 1 : 0;
+  a.status = status_ptr();
+  const int parts = split ? 2 : 1;
+  const size_t smem = (size_t)parts * (kTcM * kTcBK * 2 + (size_t)a.BN * kTcBK * 2) + 1024;
+  TNR_CK(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)cdiv(a.M, kTcM), (unsigned)cdiv(a.N, a.BN));
+  stats_work(K_CONTRACT_TC, 2.0 * (double)a.M * (double)a.N * (double)a.K * (split ? 3.0 : 1.0));
+  LaunchScope ls(K_CONTRACT_TC, s);
+  k_tc_gemm<<<grid, kTcThreads, smem, s>>>(a);
+  return check_cuda(cudaGetLastError());
+}
+
+}  // namespace tnr

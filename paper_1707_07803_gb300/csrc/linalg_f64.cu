@@ -668,6 +668,191 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Small QR for short columns (m <= 64): one thread owns one column and streams it alone, so no
+// FP64 shuffle reductions are spent on columns shorter than a warp. The matrix is kept
+// row-major in shared memory (consecutive threads touch consecutive words). Same contract and
+// outputs as k_qr_small. Column pivoting uses norm downdating with the LAPACK (dgeqp3)
+// safeguard: the norm of column j below row i is updated as ||.||^2 - R(i,j)^2 and recomputed
+// when the downdate has lost more than half of its digits.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
+  extern __shared__ double sm[];
+  const int64_t m = a.m, n = a.n;
+  const int64_t nref = m < n ? m : n;
+  double *A = sm;                 // m x n row-major: A(t, j) at t * n + j
+  double *nrm = A + m * n;        // n: current squared norms below the active row
+  double *nrm0 = nrm + n;         // n: squared norms at the last recompute
+  double *tau = nrm0 + n;         // nref
+  double *vv = tau + nref;        // m: current reflector
+  int *perm = reinterpret_cast<int *>(vv + m);  // n
+  __shared__ double s_red[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_r;
+  __shared__ double s_cut2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kSmallThreads / 32;
+  for (int64_t idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
+    const int64_t j = idx % n, t = idx / n;
+    A[idx] = a.trans_src ? a.src[j + a.lds * t] : a.src[t + a.lds * j];
+  }
+  __syncthreads();
+  double fro = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += kSmallThreads) {
+    double s = 0.0;
+    for (int64_t t = 0; t < m; ++t) s = fma(A[t * n + j], A[t * n + j], s);
+    nrm[j] = s;
+    nrm0[j] = s;
+    perm[j] = (int)j;
+    fro += s;
+  }
+  fro = warp_sum(fro);
+  if (lane == 0) s_red[warp] = fro;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int w = 0; w < NW; ++w) f += s_red[w];
+    s_cut2 = a.cut_rel * a.cut_rel * f;
+    s_r = (int)nref;
+  }
+  __syncthreads();
+  for (int64_t i = 0; i < nref; ++i) {
+    if (a.pivot) {
+      double bv = -1.0;
+      int bi = (int)i;
+      for (int64_t j = i + threadIdx.x; j < n; j += kSmallThreads)
+        if (nrm[j] > bv) {
+          bv = nrm[j];
+          bi = (int)j;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_red[warp] = bv;
+        s_idx[warp] = bi;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double b = s_red[0];
+        int bj = s_idx[0];
+        for (int w = 1; w < NW; ++w)
+          if (s_red[w] > b || (s_red[w] == b && s_idx[w] < bj)) {
+            b = s_red[w];
+            bj = s_idx[w];
+          }
+        s_idx[0] = bj;
+        if (i > 0 && b <= s_cut2) s_r = (int)i;
+      }
+      __syncthreads();
+      if (s_r == (int)i) break;
+      const int64_t p = s_idx[0];
+      if (p != i) {
+        for (int64_t t = threadIdx.x; t < m; t += kSmallThreads) {
+          const double x = A[t * n + i];
+          A[t * n + i] = A[t * n + p];
+          A[t * n + p] = x;
+        }
+        if (threadIdx.x == 0) {
+          double x = nrm[i];
+          nrm[i] = nrm[p];
+          nrm[p] = x;
+          x = nrm0[i];
+          nrm0[i] = nrm0[p];
+          nrm0[p] = x;
+          const int q = perm[i];
+          perm[i] = perm[p];
+          perm[p] = q;
+        }
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {  // reflector from column i, rows i..m-1
+      double sig = 0.0;
+      for (int64_t t = i + 1 + lane; t < m; t += 32) sig = fma(A[t * n + i], A[t * n + i], sig);
+      sig = warp_sum(sig);
+      const double alpha = A[i * n + i];
+      double tv = 0.0, beta = alpha, scal = 0.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tv = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      for (int64_t t = i + 1 + lane; t < m; t += 32) {
+        const double x = A[t * n + i] * scal;
+        A[t * n + i] = x;
+        vv[t] = x;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        A[i * n + i] = beta;
+        tau[i] = tv;
+        vv[i] = 1.0;
+      }
+    }
+    __syncthreads();
+    const double tv = tau[i];
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += kSmallThreads) {
+      if (tv != 0.0) {
+        double w = 0.0;
+        for (int64_t t = i; t < m; ++t) w = fma(vv[t], A[t * n + j], w);
+        w *= tv;
+        for (int64_t t = i; t < m; ++t) A[t * n + j] = fma(-w, vv[t], A[t * n + j]);
+      }
+      if (a.pivot) {
+        const double rij = A[i * n + j];
+        double nn = nrm[j] - rij * rij;
+        // dgeqp3 safeguard: recompute once the downdate has cancelled too much
+        if (nn <= 1.4901161193847656e-08 * nrm0[j] || nn < 0.0) {
+          nn = 0.0;
+          for (int64_t t = i + 1; t < m; ++t) nn = fma(A[t * n + j], A[t * n + j], nn);
+          nrm0[j] = nn;
+        }
+        nrm[j] = nn;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t r = s_r;
+  if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
+  const int64_t ldq = a.ldq > 0 ? a.ldq : r;
+  for (int64_t idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
+    const int64_t t = idx % r, j = idx / r;
+    const double x = t <= j ? A[t * n + j] : 0.0;
+    const int64_t oj = perm[j];
+    if (a.trans_r)
+      a.R[oj + a.ldr * t] = x;
+    else
+      a.R[t + a.ldr * oj] = x;
+  }
+  // Q = H_0 ... H_{r-1} [I_r; 0]: thread l builds column l (m <= 64 rows)
+  for (int64_t l = threadIdx.x; l < r; l += kSmallThreads) {
+    double q[64];
+#pragma unroll
+    for (int t = 0; t < 64; ++t) q[t] = (t == l) ? 1.0 : 0.0;
+    for (int64_t j = l; j >= 0; --j) {
+      const double tj = tau[j];
+      if (tj == 0.0) continue;
+      double w = q[j];
+      for (int64_t t = j + 1; t < m; ++t) w = fma(A[t * n + j], q[t], w);
+      w *= tj;
+      q[j] -= w;
+      for (int64_t t = j + 1; t < m; ++t) q[t] = fma(-w, A[t * n + j], q[t]);
+    }
+    for (int64_t t = 0; t < m; ++t) {
+      if (a.trans_q)
+        a.Q[l + ldq * t] = q[t];
+      else
+        a.Q[t + ldq * l] = q[t];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // One-sided Jacobi SVD of an n x n matrix in one CTA (Hestenes): rotate column pairs of G,
 // accumulating V, until every pair is orthogonal to |g_p^T g_q| <= tol ||g_p|| ||g_q||.
 // Pairs follow a round-robin tournament, so each round's pairs are disjoint and are
@@ -680,6 +865,31 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
 // ------------------------------------------------------------------------------------------
 constexpr int kJacThreads = 512;
 
+// Jacobi rotation (c, s) that annihilates gamma = g_p^T g_q, with alpha = ||g_p||^2,
+// beta = ||g_q||^2: t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) / (2 gamma).
+// The angle only steers convergence, so t is computed in FP32 (after an exact power-of-two
+// scaling that keeps the ratio in range); c = 1 / sqrt(1 + t^2) is then refined to FP64 by two
+// Newton steps from the FP32 estimate, so that c^2 + s^2 = 1 to FP64 rounding and the
+// accumulated V stays orthogonal. Avoids FP64 division and square root, which are long
+// instruction sequences on the FP64 pipe. Returns false when the rotation is negligible.
+__device__ __forceinline__ bool rotation(double al, double be, double ga, double &cs, double &sn) {
+  int e = 0;
+  frexp(2.0 * ga, &e);
+  const double diff = ldexp(be - al, -e), den = ldexp(2.0 * ga, -e);  // den in [0.5, 1)
+  const float zf = (float)diff / (float)den;
+  if (!isfinite(zf)) return false;
+  const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+  if (tf == 0.0f) return false;
+  const double t = (double)tf;
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  cs = y;
+  sn = y * t;
+  return true;
+}
+
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, int64_t ldg, double *S, double *V,
                                                         int64_t ldv, double *Gw, double *Vw, int *status) {
   extern __shared__ double sm[];
@@ -689,16 +899,20 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
   const bool in_smem = Gw == nullptr;
   double *g = in_smem ? sm : Gw;          // working copy, ld n
   double *v = in_smem ? sm + n * n : Vw;  // working V, ld n
-  for (int64_t idx = threadIdx.x; idx < n * n; idx += kJacThreads) {
+  const int nthr = blockDim.x;
+  for (int64_t idx = threadIdx.x; idx < n * n; idx += nthr) {
     const int64_t i = idx % n, j = idx / n;
     g[idx] = G[i + ldg * j];
     v[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = kJacThreads / 32;
+  const int nw = nthr / 32;
   const int64_t np = (n + 1) & ~int64_t(1);  // even number of players
-  const double tol = DBL_EPSILON * (double)(n > 8 ? n : 8);
+  // |g_p^T g_q| <= tol ||g_p|| ||g_q||, tol = 16 eps sqrt(n): above the rounding error of the
+  // computed dot product, so rounding noise alone does not keep a sweep going
+  const double tol = 16.0 * DBL_EPSILON * sqrt((double)(n > 4 ? n : 4));
+  const double tol2 = tol * tol;
   double floor2 = 0.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     for (int64_t j = warp; j < n; j += nw) {
@@ -741,10 +955,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
         double ga = 0.0;
         for (int64_t i = lane; i < n; i += 32) ga = fma(gp[i], gq[i], ga);
         ga = warp_sum(ga);
-        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-        const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+        if (ga == 0.0 || ga * ga <= tol2 * al * be) continue;
+        double cs, sn;
+        if (!rotation(al, be, ga, cs, sn)) continue;
         for (int64_t i = lane; i < n; i += 32) {
           const double x = gp[i], y = gq[i];
           gp[i] = fma(-sn, y, cs * x);
@@ -757,14 +970,18 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
           vq[i] = fma(sn, x, cs * y);
         }
         if (lane == 0) {
-          s_norm[p] = fma(-t, ga, al);
-          s_norm[q] = fma(t, ga, be);
+          // exact norms of the rotated pair for the applied (cs, sn)
+          const double c2 = cs * cs, s2 = sn * sn, cs2g = 2.0 * cs * sn * ga;
+          s_norm[p] = fma(c2, al, fma(s2, be, -cs2g));
+          s_norm[q] = fma(s2, al, fma(c2, be, cs2g));
           s_rot = 1;
         }
       }
       __syncthreads();
     }
-    if (!s_rot) break;
+    const int rotated = s_rot;
+    __syncthreads();  // every thread has read s_rot before the next sweep resets it
+    if (!rotated) break;
   }
   // final column norms
   for (int64_t j = warp; j < n; j += nw) {
@@ -975,7 +1192,7 @@ int qrcp_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, doubl
 
 bool qr_small_fits(int64_t m, int64_t n) {
   const int64_t nref = m < n ? m : n;
-  const size_t smem = sizeof(double) * (m * n + n + nref) + sizeof(int) * n;
+  const size_t smem = sizeof(double) * (m * n + 2 * n + nref + m) + sizeof(int) * n;
   return smem <= 200 * 1024;
 }
 
@@ -1001,11 +1218,19 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
   a.R = R;
   a.ldr = ldr;
   a.r_out = r_dev;
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     const double M = (double)m, N = (double)n, P = (double)nref;
     stats_work(K_QR, 2 * M * N * P - (M + N) * P * P + 2 * P * P * P / 3 + 2 * M * P * P - 2 * P * P * P / 3);
   }
+  if (m <= 64) {  // short columns: one thread per column
+    const size_t sm2 = sizeof(double) * (m * n + 2 * n + nref + m) + sizeof(int) * n;
+    if (sm2 > 48 * 1024)
+      TNR_CK(cudaFuncSetAttribute(k_qr_small_tpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    LaunchScope ls(K_QR, s);
+    k_qr_small_tpc<<<1, kSmallThreads, sm2, s>>>(a);
+    return check_cuda(cudaGetLastError());
+  }
+  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LaunchScope ls(K_QR, s);
   k_qr_small<<<1, kSmallThreads, smem, s>>>(a);
   return check_cuda(cudaGetLastError());
@@ -1028,8 +1253,9 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
     smem = 0;
   }
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, (n + 1) / 2));
   LaunchScope ls(K_SVD, s);
-  k_jacobi<<<1, kJacThreads, smem, s>>>(G, n, ldg, S, V, ldv, Gw, Vw, status_ptr());
+  k_jacobi<<<1, 32 * warps, smem, s>>>(G, n, ldg, S, V, ldv, Gw, Vw, status_ptr());
   return check_cuda(cudaGetLastError());
 }
 

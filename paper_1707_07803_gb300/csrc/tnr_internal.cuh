@@ -129,6 +129,10 @@ size_t jacobi_scratch(int64_t n);
 int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S, double *V, int64_t ldv,
                    void *scratch);
 
+// Tensor-core (tcgen05, BF16 in / FP32 accumulate) site-1 product; see contract_tc.cu.
+int contract_site1_tc(cudaStream_t s, const double *A, int64_t I, int64_t J, int64_t R2, const double *X, int64_t Kx,
+                      int64_t S2, int trans, double *Y, bool split);
+
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
                     bool transpose);

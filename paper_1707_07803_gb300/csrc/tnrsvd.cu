@@ -10,6 +10,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -26,7 +28,14 @@ struct ContractDims {
   int64_t R, I, J, R2;  // A core
   int64_t S, Kx, S2;    // X core (row dim = J or I)
   int trans;
+  int mixed;  // 1: operands rounded to BF16 hi + lo, products hi*hi + hi*lo + lo*hi summed in FP32
 };
+
+__device__ __forceinline__ void split_bf16(double x, float &hi, float &lo) {
+  const __nv_bfloat16 h = __double2bfloat16(x);
+  hi = __bfloat162float(h);
+  lo = __bfloat162float(__double2bfloat16(x - (double)hi));
+}
 
 __global__ void k_contract(const double *__restrict__ A, const double *__restrict__ X, double *__restrict__ Y,
                            ContractDims D) {
@@ -47,15 +56,24 @@ __global__ void k_contract(const double *__restrict__ A, const double *__restric
     const int64_t r2 = rs2 % D.R2, s2 = rs2 / D.R2;
     // A(r, i, j, r2) at r + R(i + I(j + J r2)); X(s, y, c, s2) at s + S(y + Ny(c + Kx s2))
     const double *xp = X + s + D.S * (Ny * (c + D.Kx * s2));
-    double acc = 0.0;
-    if (!D.trans) {
-      const double *ap = A + r + D.R * (xo + D.I * (D.J * r2));
-      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[D.R * D.I * y], xp[D.S * y], acc);
+    const double *ap = D.trans ? A + r + D.R * (D.I * (xo + D.J * r2)) : A + r + D.R * (xo + D.I * (D.J * r2));
+    const int64_t as = D.trans ? D.R : D.R * D.I;
+    if (!D.mixed) {
+      double acc = 0.0;
+      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[as * y], xp[D.S * y], acc);
+      Y[idx] = acc;
     } else {
-      const double *ap = A + r + D.R * (D.I * (xo + D.J * r2));
-      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[D.R * y], xp[D.S * y], acc);
+      float acc = 0.0f;
+      for (int64_t y = 0; y < Ny; ++y) {
+        float ah, al, xh, xl;
+        split_bf16(ap[as * y], ah, al);
+        split_bf16(xp[D.S * y], xh, xl);
+        acc = fmaf(ah, xh, acc);
+        acc = fmaf(ah, xl, acc);
+        acc = fmaf(al, xh, acc);
+      }
+      Y[idx] = (double)acc;
     }
-    Y[idx] = acc;
   }
 }
 
@@ -224,13 +242,12 @@ int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
 // sits in the right parts of the product (e.g. A^T Q = V (S U^T Q) keeps V's bonds), where a
 // left-to-right orthogonalisation cannot see it. For k = d-1..1: M_k (t x w) = L Q_k by a
 // column-pivoted QR of M_k^T that stops once every remaining column norm is below
-// cut * ||M_k||_F, cut = min(64 eps, tol / 100); Q_k (orthonormal rows) replaces the core and L
+// cut * ||M_k||_F (see compress_cut); Q_k (orthonormal rows) replaces the core and L
 // is absorbed into core k-1. Only directions at the rounding level of M_k are dropped (the size
 // of a Householder factorisation's own backward error, far below the truncation threshold), so
 // the rounding that follows returns the same result to rounding accuracy, on bonds of the
 // numerical rank instead of R_k S_k.
-int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double tol) {
-  const double cut = std::min(64.0 * 2.220446049250313e-16, 0.01 * tol);
+int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut) {
   for (int k = Y.d - 1; k >= 1; --k) {
     const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
     int64_t r = 0;
@@ -255,6 +272,15 @@ int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double tol) {
   return TNR_OK;
 }
 
+// Compression cutoff relative to ||M_k||_F: the rounding level of the product that made Y.
+// FP64 products: min(64 eps, tol / 100). BF16 x3 products carry about 2^-16 relative error per
+// term, so their noise directions are dropped at 0.05 tol (tol is then at least kMixedTol).
+constexpr double kMixedTol = 1.2e-4;
+double compress_cut(double tol, bool mixed_product) {
+  if (mixed_product) return 0.05 * tol;
+  return std::min(64.0 * 2.220446049250313e-16, 0.01 * tol);
+}
+
 // Left-to-right Householder QR sweep (rounding part 1, Section 5.4): core k reshaped
 // (R_k I_k J_k) x R_{k+1} = Q R; Q replaces the core, R is absorbed into core k+1.
 int sweep_lr(cudaStream_t s, tnr_mpo &Y, Bufs &b) {
@@ -274,9 +300,11 @@ int sweep_lr(cudaStream_t s, tnr_mpo &Y, Bufs &b) {
   return TNR_OK;
 }
 
-// Plain thin QR, small-matrix kernel when it fits: A (m x n, lda = m) <- Q, R (min x n, ldr).
+// Plain thin QR: A (m x n, lda = m) <- Q, R (min x n, ldr). Matrices with many long columns
+// (m >= 128, n >= 16) go to the multi-CTA kernel, whose FP64 work spreads over n SMs; the
+// rest to the one-CTA shared-memory kernel.
 int thin_qr(cudaStream_t s, double *A, int64_t m, int64_t n, double *R, int64_t ldr, Bufs &b) {
-  if (qr_small_fits(m, n))
+  if (qr_small_fits(m, n) && !(m >= 128 && n >= 16))
     return qr_small_f64(s, A, m, m, n, false, false, 0.0, A, m, false, R, ldr, false, nullptr);
   return qr_f64(s, A, m, n, m, R, ldr, b.qr);
 }
@@ -347,8 +375,9 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
-int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b) {
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, tol));
+int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
+                       bool mixed_product = false) {
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, compress_cut(tol, mixed_product)));
   TNR_TRY(sweep_lr(s, Y, b));
   TNR_TRY(sweep_rl(s, Y, tol, max_rank, b));
   const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
@@ -366,7 +395,7 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 // kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, tol));
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, compress_cut(tol, false)));
   TNR_TRY(sweep_lr(s, Z, b));
   TNR_TRY(sweep_rl(s, Z, tol, max_rank, b));
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
@@ -383,7 +412,7 @@ int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs 
   return TNR_OK;
 }
 
-int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X, tnr_mpo &Y) {
+int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X, tnr_mpo &Y, bool mixed = false) {
   Y.d = A.d;
   Y.R[0] = 1;
   for (int k = 0; k < A.d; ++k) {
@@ -396,6 +425,7 @@ int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X,
     D.Kx = X.J[k];
     D.S2 = X.R[k + 1];
     D.trans = trans;
+    D.mixed = mixed ? 1 : 0;
     const int64_t Xo = trans ? A.J[k] : A.I[k];
     const int64_t Ny = trans ? A.I[k] : A.J[k];
     if (X.I[k] != Ny) return TNR_EINVAL;
@@ -404,6 +434,11 @@ int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X,
     Y.I[k] = Xo;
     Y.J[k] = D.Kx;
     Y.R[k + 1] = D.R2 * D.S2;
+    if (mixed && D.R == 1 && D.S == 1 && Ny >= 16) {
+      // dense site product on the tensor cores (BF16 x3 split, FP32 accumulation)
+      TNR_TRY(contract_site1_tc(s, A.core[k], D.I, D.J, D.R2, X.core[k], D.Kx, D.S2, trans, Y.core[k], true));
+      continue;
+    }
     stats_work(K_CONTRACT, 2.0 * (double)total * (double)Ny);
     LaunchScope ls(K_CONTRACT, s);
     k_contract<<<grid_for(total), 256, 0, s>>>(A.core[k], X.core[k], Y.core[k], D);
@@ -611,13 +646,19 @@ int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q
     Y1.cap[i] = P.pcap[i];
   }
   // Alg. 5.4
-  TNR_TRY(contract_impl(s, Am, 0, Om, Y0));
-  TNR_TRY(orthogonalize_impl(s, Y0, nullptr, o->tol, o->max_rank, sb.b));
+  // Mixed precision: the power-iteration products carry BF16 x3 noise (~1e-5 relative), so
+  // their roundings truncate at tol_p = max(tol, kMixedTol); this perturbs range(Q) at 1e-4,
+  // which moves the singular values of the FP64 Rayleigh-Ritz step B = Q^T A only at second
+  // order (1e-8). B itself is rounded with the caller's tol in FP64.
+  const bool mixed = o->precision == TNR_MIXED;
+  const double tol_p = mixed ? std::max(o->tol, kMixedTol) : o->tol;
+  TNR_TRY(contract_impl(s, Am, 0, Om, Y0, mixed));
+  TNR_TRY(orthogonalize_impl(s, Y0, nullptr, tol_p, o->max_rank, sb.b, mixed));
   for (int it = 0; it < q; ++it) {
-    TNR_TRY(contract_impl(s, Am, 1, Y0, Y1));
-    TNR_TRY(orthogonalize_impl(s, Y1, nullptr, o->tol, o->max_rank, sb.b));
-    TNR_TRY(contract_impl(s, Am, 0, Y1, Y0));
-    TNR_TRY(orthogonalize_impl(s, Y0, nullptr, o->tol, o->max_rank, sb.b));
+    TNR_TRY(contract_impl(s, Am, 1, Y0, Y1, mixed));
+    TNR_TRY(orthogonalize_impl(s, Y1, nullptr, tol_p, o->max_rank, sb.b, mixed));
+    TNR_TRY(contract_impl(s, Am, 0, Y1, Y0, mixed));
+    TNR_TRY(orthogonalize_impl(s, Y0, nullptr, tol_p, o->max_rank, sb.b, mixed));
   }
   // B = Q^T A as Z = A^T Q, then Alg. 5.3
   TNR_TRY(contract_impl(s, Am, 1, Y0, Y1));
@@ -662,13 +703,15 @@ int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q
 
 using namespace tnr;
 
-extern "C" int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, void *stream) {
+extern "C" int tnr_mpo_contract(const tnr_mpo *A, int32_t trans, const tnr_mpo *X, tnr_mpo *Y, int32_t precision,
+                                void *stream) {
   TNR_TRY(validate_input(A));
   TNR_TRY(validate_input(X));
   if (!Y || X->d != A->d || (trans != 0 && trans != 1)) return TNR_EINVAL;
+  if (precision != TNR_FP64 && precision != TNR_MIXED) return TNR_EINVAL;
   for (int k = 0; k < A->d; ++k)
     if (!Y->core[k]) return TNR_EINVAL;
-  return contract_impl((cudaStream_t)stream, *A, trans, *X, *Y);
+  return contract_impl((cudaStream_t)stream, *A, trans, *X, *Y, precision == TNR_MIXED);
 }
 
 namespace {

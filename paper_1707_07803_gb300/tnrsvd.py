@@ -70,7 +70,7 @@ _SIGS = {
                         [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _I64, _P, _P, _P, ctypes.c_size_t, _P]),
     "tnr_sparse_to_mpo_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _P, _P, _I64,
                                                   _I64P, _P]),
-    "tnr_mpo_contract": (ctypes.c_int, [_MPOP, _I32, _MPOP, _MPOP, _P]),
+    "tnr_mpo_contract": (ctypes.c_int, [_MPOP, _I32, _MPOP, _MPOP, _I32, _P]),
     "tnr_orthogonalize_workspace": (ctypes.c_int, [_MPOP, _SZP]),
     "tnr_orthogonalize": (ctypes.c_int, [_MPOP, _P, _OPTP, _P, ctypes.c_size_t, _P]),
     "tnr_solve_query": (ctypes.c_int, [_MPOP, _I32, _I32, _OPTP, _MPOP, _MPOP, _SZP]),
@@ -239,8 +239,8 @@ def tnr_sparse_to_mpo_noalloc(nrows, ncols, row, col, val, I, J, X, digits, max_
     return R.value
 
 
-def tnr_mpo_contract(A, trans, X, Y_caps=None, stream=None):
-    """Y = op(A) X (Section 5.2). Allocates Y with exact sizes unless Y_caps is given."""
+def tnr_mpo_contract(A, trans, X, precision=TNR_FP64, stream=None):
+    """Y = op(A) X (Section 5.2). Allocates Y with exact sizes."""
     lib = load()
     d = A.d
     cores = []
@@ -250,8 +250,8 @@ def tnr_mpo_contract(A, trans, X, Y_caps=None, stream=None):
         cores.append(torch.empty(max(n, 1), dtype=torch.float64, device=A.cores[0].device))
     Y = Mpo([0] * d, [0] * d, [1] * (d + 1), cores)
     sa, sx, sy = A.to_struct(), X.to_struct(), Y.to_struct()
-    _check(lib.tnr_mpo_contract(ctypes.byref(sa), int(trans), ctypes.byref(sx), ctypes.byref(sy), _stream(stream)),
-           "tnr_mpo_contract")
+    _check(lib.tnr_mpo_contract(ctypes.byref(sa), int(trans), ctypes.byref(sx), ctypes.byref(sy), int(precision),
+                                _stream(stream)), "tnr_mpo_contract")
     Y.I = [sy.I[k] for k in range(d)]
     Y.J = [sy.J[k] for k in range(d)]
     Y.R = [sy.R[k] for k in range(d + 1)]

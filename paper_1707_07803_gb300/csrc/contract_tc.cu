@@ -30,7 +30,10 @@ constexpr int kTcThreads = 128;
 // index i -> (i % n1) * s1 + (i / n1) * s2
 struct IdxMap {
   int64_t n1, s1, s2;
-  __device__ __forceinline__ int64_t operator()(int64_t i) const { return (i % n1) * s1 + (i / n1) * s2; }
+  __device__ __forceinline__ int64_t operator()(int64_t i) const {
+    const unsigned ui = (unsigned)i, un = (unsigned)n1;  // all extents < 2^31
+    return (int64_t)(ui % un) * s1 + (int64_t)(ui / un) * s2;
+  }
 };
 
 struct TcArgs {
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_abort;
+  __shared__ int64_t s_arow[kTcM], s_bcol[256], s_crow[kTcM], s_ccol[256];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t m0 = (int64_t)blockIdx.x * kTcM;
   const int64_t n0 = (int64_t)blockIdx.y * a.BN;
@@ -110,6 +114,18 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
+  // per-row / per-column base offsets of this tile (one index split each)
+  for (int i = threadIdx.x; i < kTcM; i += kTcThreads) {
+    const int64_t gm = m0 + i;
+    s_arow[i] = gm < a.M ? a.amap(gm) : -1;
+    s_crow[i] = gm < a.M ? a.crow(gm) : -1;
+  }
+  for (int i = threadIdx.x; i < a.BN; i += kTcThreads) {
+    const int64_t gn = n0 + i;
+    s_bcol[i] = gn < a.N ? a.bmap(gn) : -1;
+    s_ccol[i] = gn < a.N ? a.ccol(gn) : -1;
+  }
+  __syncthreads();
 
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   const uint32_t sbo = (kTcBK / 8) * 128, lbo = 128;
@@ -121,9 +137,9 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     for (int idx = threadIdx.x; idx < kTcM * kTcBK; idx += kTcThreads) {
       const int r = a.a_ks == 1 ? idx / kTcBK : idx % kTcM;
       const int k = a.a_ks == 1 ? idx % kTcBK : idx / kTcM;
-      const int64_t gm = m0 + r, gk = k0 + k;
+      const int64_t gk = k0 + k, base = s_arow[r];
       double x = 0.0;
-      if (gm < a.M && gk < a.K) x = a.A[a.amap(gm) + gk * a.a_ks];
+      if (base >= 0 && gk < a.K) x = a.A[base + gk * a.a_ks];
       const __nv_bfloat16 hi = __double2bfloat16(x);
       *reinterpret_cast<__nv_bfloat16 *>(sA[0] + kmajor_off(r, k)) = hi;
       if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sA[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
@@ -131,9 +147,9 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
     for (int idx = threadIdx.x; idx < a.BN * kTcBK; idx += kTcThreads) {
       const int r = a.b_ks == 1 ? idx / kTcBK : idx % a.BN;
       const int k = a.b_ks == 1 ? idx % kTcBK : idx / a.BN;
-      const int64_t gn = n0 + r, gk = k0 + k;
+      const int64_t gk = k0 + k, base = s_bcol[r];
       double x = 0.0;
-      if (gn < a.N && gk < a.K) x = a.B[a.bmap(gn) + gk * a.b_ks];
+      if (base >= 0 && gk < a.K) x = a.B[base + gk * a.b_ks];
       const __nv_bfloat16 hi = __double2bfloat16(x);
       *reinterpret_cast<__nv_bfloat16 *>(sB[0] + kmajor_off(r, k)) = hi;
       if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sB[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!s_abort) {
     // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-    const int64_t gm = m0 + warp * 32 + lane;
+    const int64_t rowoff = s_crow[warp * 32 + lane];
     for (int c0 = 0; c0 < a.BN; c0 += 8) {
       uint32_t v[8];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -184,12 +200,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (gm < a.M) {
-        const int64_t rowoff = a.crow(gm);
+      if (rowoff >= 0) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int64_t gn = n0 + c0 + j;
-          if (gn < a.N) a.C[rowoff + a.ccol(gn)] = (double)__uint_as_float(v[j]);
+          const int64_t co = s_ccol[c0 + j];
+          if (co >= 0) a.C[rowoff + co] = (double)__uint_as_float(v[j]);
         }
       }
     }

@@ -17,8 +17,11 @@
 //   k_first_scan  per entry: validate order/range, first-occurrence flag, tile-local exclusive
 //                 scan of the flags (1024 entries per CTA) -> F_local, tile totals
 //   k_tile_scan   one CTA: exclusive scan of the tile totals -> tile offsets, R
-//   k_fill        per first-occurrence entry: block index t, zero block t of X, scatter the
-//                 block's entries (gathered from the I1 rows of the segment), write digits.
+//   k_zero        zero X (vectorised)
+//   k_fill_w      one warp per 32 consecutive entries: block index t of every entry (ranks
+//                 among the first occurrences of its block-row, by shuffles inside the window),
+//                 scatter the entry's value into block t, digits from each first occurrence.
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -36,6 +39,13 @@ struct ConvDims {
   int32_t I[TNR_MAX_SITES];
   int32_t J[TNR_MAX_SITES];
 };
+
+// Non-negative division that takes the 32-bit path whenever both operands fit (64-bit division
+// is a long software sequence on the GPU; block and digit indices almost always fit).
+__device__ __forceinline__ int64_t qdiv(int64_t a, int64_t b) {
+  if ((((uint64_t)a) | ((uint64_t)b)) >> 32) return a / b;
+  return (int64_t)((uint32_t)a / (uint32_t)b);
+}
 
 // Lower bound over entries [lo, hi) for the composite key (r, c).
 __device__ __forceinline__ int64_t lower_bound_rc(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
@@ -129,9 +139,9 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
       }
     }
     if (ok) {
-      const int64_t p = r / D.I1, q = c / D.J1;
+      const int64_t p = qdiv(r, D.I1), q = qdiv(c, D.J1);
       bool first = true;
-      if (e > 0 && __ldg(row + e - 1) == r && __ldg(col + e - 1) / D.J1 == q) first = false;
+      if (e > 0 && __ldg(row + e - 1) == r && qdiv(__ldg(col + e - 1), D.J1) == q) first = false;
       if (first && r > p * D.I1) {
         const int64_t s0 = segment_start(row, e, p * D.I1);
         for (int64_t rr = p * D.I1; rr < r && first; ++rr) {
@@ -210,58 +220,99 @@ __device__ __forceinline__ int64_t F_at(const int32_t *__restrict__ F_local, con
   return (int64_t)__ldg(tile_off + x / kTile) + __ldg(F_local + x);
 }
 
-__global__ void __launch_bounds__(256) k_fill(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
-                                              const double *__restrict__ val, ConvDims D,
-                                              const int32_t *__restrict__ F_local, const int32_t *__restrict__ tile_off,
-                                              double *__restrict__ X, uint8_t *__restrict__ digits, int64_t R,
-                                              int *status) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= D.nnz) return;
-  const int64_t Fe = F_at(F_local, tile_off, e, D.nnz);
-  if (F_at(F_local, tile_off, e + 1, D.nnz) == Fe) return;  // not a first occurrence
-  const int64_t r = __ldg(row + e), c = __ldg(col + e);
-  const int64_t p = r / D.I1, q = c / D.J1;
-  const int64_t r0 = p * D.I1;
-  const int64_t s0 = segment_start(row, e, r0);
-  const int64_t s1 = segment_end(row, D.nnz, e, r0 + D.I1);
-  // Rank of q among the distinct block-columns of this block-row.
-  int64_t rank = 0;
-  for (int64_t rr = r0; rr < r0 + D.I1; ++rr) {
-    const int64_t x0 = lower_bound_rc(row, col, s0, s1, rr, 0);
-    const int64_t xq = lower_bound_rc(row, col, x0, s1, rr, q * D.J1);
-    rank += F_at(F_local, tile_off, xq, D.nnz) - F_at(F_local, tile_off, x0, D.nnz);
+// Digits of block t: i_k, j_k of the block-row p and block-column q (mixed radix, site 2 fastest).
+__device__ __forceinline__ void write_digits(const ConvDims &D, int64_t p, int64_t q, int64_t t, uint8_t *digits) {
+  if (D.d <= 1) return;
+  uint8_t *dg = digits + t * 2 * (int64_t)(D.d - 1);
+  int64_t pp = p, qq = q;
+  for (int k = 1; k < D.d; ++k) {
+    const int64_t pq = qdiv(pp, D.I[k]), qq2 = qdiv(qq, D.J[k]);
+    dg[2 * (k - 1)] = (uint8_t)(pp - pq * D.I[k]);
+    dg[2 * (k - 1) + 1] = (uint8_t)(qq - qq2 * D.J[k]);
+    pp = pq;
+    qq = qq2;
   }
-  const int64_t t = F_at(F_local, tile_off, s0, D.nnz) + rank;
-  if (t < 0 || t >= R) {  // caller's R disagrees with the count phase: write nothing
-    set_status(status, TNR_ERANGE);
+}
+
+// Warp-window fill. Warp w handles the 32 consecutive nonzeros [32w, 32w + 32). Lanes whose
+// entries share a block-row p form a run (entries are sorted, so runs are contiguous lanes and
+// found with a ballot). The block index of an entry is t = F(s0) + rank, rank = number of first
+// occurrences in its block-row segment [s0, s1) with a smaller block-column; inside the window
+// it is counted with shuffles, outside it (only for the runs that cross a window edge) with a
+// linear scan of the segment's remaining entries. X is zeroed beforehand (k_zero), so every
+// nonzero writes its own value and the first occurrence of each block also writes its digits.
+__global__ void __launch_bounds__(256) k_zero(double *__restrict__ X, int64_t n) {
+  if (reinterpret_cast<uintptr_t>(X) & 15) {  // not 16-byte aligned: scalar stores
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      X[i] = 0.0;
     return;
   }
-  const int64_t bs = D.I1 * D.J1;
-  double *blk = X + t * bs;
-  if ((bs & 1) == 0) {
-    double2 z = make_double2(0.0, 0.0);
-    for (int64_t i = 0; i < bs; i += 2) *reinterpret_cast<double2 *>(blk + i) = z;
-  } else {
-    for (int64_t i = 0; i < bs; ++i) blk[i] = 0.0;
+  const int64_t n2 = n >> 1;
+  double2 *X2 = reinterpret_cast<double2 *>(X);
+  const double2 z = make_double2(0.0, 0.0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+    X2[i] = z;
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) X[n - 1] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_fill_w(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+                                                const double *__restrict__ val, ConvDims D,
+                                                const int32_t *__restrict__ F_local,
+                                                const int32_t *__restrict__ tile_off, double *__restrict__ X,
+                                                uint8_t *__restrict__ digits, int64_t R, int *status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;  // window start
+  if (e0 >= D.nnz) return;
+  const int64_t e = e0 + lane;
+  const bool valid = e < D.nnz;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  const int nval = __popc(vmask);
+  int64_t r = -1, c = 0, p = -1, q = 0;
+  int first = 0;
+  double v = 0.0;
+  if (valid) {
+    r = __ldg(row + e);
+    c = __ldg(col + e);
+    v = __ldg(val + e);
+    p = qdiv(r, D.I1);
+    q = qdiv(c, D.J1);
+    first = F_at(F_local, tile_off, e + 1, D.nnz) != F_at(F_local, tile_off, e, D.nnz);
   }
-  for (int64_t rr = r0; rr < r0 + D.I1; ++rr) {
-    int64_t x = lower_bound_rc(row, col, s0, s1, rr, q * D.J1);
-    while (x < s1 && __ldg(row + x) == rr) {
-      const int64_t cx = __ldg(col + x);
-      if (cx >= (q + 1) * D.J1) break;
-      blk[(rr - r0) + D.I1 * (cx - q * D.J1)] = __ldg(val + x);
-      ++x;
-    }
+  // runs of equal block-row across lanes
+  const int64_t pprev = __shfl_up_sync(0xffffffffu, p, 1);
+  const bool bound = valid && (lane == 0 || pprev != p);
+  const unsigned bmask = __ballot_sync(0xffffffffu, bound);
+  const int rs = 31 - __clz(bmask & (0xffffffffu >> (31 - lane)));     // run start lane
+  const unsigned after = bmask & ~(0xffffffffu >> (31 - lane));         // boundaries after me
+  const int re = after ? (__ffs(after) - 2) : (nval - 1);               // run end lane
+  // segment bounds: gallop only where the run touches the window edge
+  int64_t s0 = e0 + rs, s1 = e0 + re + 1;
+  const int64_t r0 = p * D.I1;
+  if (valid && rs == 0 && e0 > 0 && qdiv(__ldg(row + e0 - 1), D.I1) == p) s0 = segment_start(row, e0, r0);
+  if (valid && re == nval - 1 && e0 + nval < D.nnz && qdiv(__ldg(row + e0 + nval), D.I1) == p)
+    s1 = segment_end(row, D.nnz, e0 + nval - 1, r0 + D.I1);
+  // rank inside the window (lanes rs..re of my run)
+  int64_t rank = 0;
+  for (int j = 0; j < 32; ++j) {
+    const int64_t qj = __shfl_sync(0xffffffffu, q, j);
+    const int fj = __shfl_sync(0xffffffffu, first, j);
+    if (valid && j >= rs && j <= re && fj && qj < q) ++rank;
   }
-  if (D.d > 1) {
-    uint8_t *dg = digits + t * 2 * (int64_t)(D.d - 1);
-    int64_t pp = p, qq = q;
-    for (int k = 1; k < D.d; ++k) {
-      dg[2 * (k - 1)] = (uint8_t)(pp % D.I[k]);
-      dg[2 * (k - 1) + 1] = (uint8_t)(qq % D.J[k]);
-      pp /= D.I[k];
-      qq /= D.J[k];
+  // rank outside the window, for runs crossing an edge
+  if (valid) {
+    for (int64_t x = s0; x < e0 + rs; ++x)
+      if (qdiv(__ldg(col + x), D.J1) < q && F_at(F_local, tile_off, x + 1, D.nnz) != F_at(F_local, tile_off, x, D.nnz))
+        ++rank;
+    for (int64_t x = e0 + re + 1; x < s1; ++x)
+      if (qdiv(__ldg(col + x), D.J1) < q && F_at(F_local, tile_off, x + 1, D.nnz) != F_at(F_local, tile_off, x, D.nnz))
+        ++rank;
+    const int64_t t = F_at(F_local, tile_off, s0, D.nnz) + rank;
+    if (t < 0 || t >= R) {
+      set_status(status, TNR_ERANGE);
+      return;
     }
+    X[t * D.I1 * D.J1 + (r - r0) + D.I1 * (c - q * D.J1)] = v;
+    if (first) write_digits(D, p, q, t, digits);
   }
 }
 
@@ -359,8 +410,13 @@ extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const 
   stats_work(K_CONV_FILL, 24.0 * (double)nnz + (double)R * (8.0 * (double)(I[0] * J[0]) + 2.0 * (d - 1)));
   {
     LaunchScope ls(K_CONV_FILL, s);
-    k_fill<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R,
-                                                     status_ptr());
+    const int64_t nx = R * I[0] * J[0];
+    k_zero<<<(unsigned)std::min<int64_t>(cdiv(nx / 2 + 1, 256), 152 * 16), 256, 0, s>>>(X, nx);
+  }
+  {
+    LaunchScope ls(K_CONV_FILL, s);
+    k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R,
+                                                       status_ptr());
   }
   TNR_CK(cudaGetLastError());
   return TNR_OK;
@@ -443,8 +499,13 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   if (total > max_blocks) return TNR_ENOMEM;  // X and digits untouched
   {
     LaunchScope ls(K_CONV_FILL, s);
-    k_fill<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, total,
-                                                     status_ptr());
+    const int64_t nx = total * I[0] * J[0];
+    k_zero<<<(unsigned)std::min<int64_t>(cdiv(nx / 2 + 1, 256), 152 * 16), 256, 0, s>>>(X, nx);
+  }
+  {
+    LaunchScope ls(K_CONV_FILL, s);
+    k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, total,
+                                                       status_ptr());
   }
   TNR_CK(cudaGetLastError());
   return TNR_OK;

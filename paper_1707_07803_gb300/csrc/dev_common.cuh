@@ -1,0 +1,73 @@
+// Device helpers shared by several translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnr {
+
+__device__ __forceinline__ double dwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Jacobi rotation (c, s) annihilating gamma = g_p^T g_q for alpha = ||g_p||^2, beta = ||g_q||^2:
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) / (2 gamma). The angle
+// only steers convergence, so t is formed in FP32 after an exact power-of-two scaling; c =
+// 1 / sqrt(1 + t^2) is refined to FP64 by two Newton steps from the FP32 estimate, so c^2 + s^2
+// = 1 to FP64 rounding. No FP64 division or square root (long sequences on GB300's FP64 pipe).
+// Returns false when the rotation is negligible.
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga, double &cs, double &sn) {
+  // exact power-of-two scale 2^-e with e the binary exponent of 2*gamma (bit manipulation,
+  // no library calls): 2*gamma*scale lies in [1, 2)
+  const long long eb = (__double_as_longlong(2.0 * ga) >> 52) & 0x7FF;
+  if (eb == 0 || eb == 0x7FF) return false;  // gamma subnormal or non-finite: negligible/invalid
+  const double scale = __longlong_as_double((2046LL - eb) << 52);
+  const double diff = (be - al) * scale, den = (2.0 * ga) * scale;
+  const float zf = (float)diff / (float)den;
+  if (!isfinite(zf)) return false;
+  const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+  if (tf == 0.0f) return false;
+  const double t = (double)tf;
+  const double x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  cs = y;
+  sn = y * t;
+  return true;
+}
+
+// Householder reflector parameters (LAPACK dlarfg convention) for x = (alpha, x_2..) with
+// sig = ||x_2..||^2 > 0: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta, and
+// scal = 1 / (alpha - beta) (v = x_2.. * scal, v_1 = 1). Written without FP64 division or
+// square root: r = 1/||x|| from an FP32 estimate and two Newton steps, so beta = -sign(alpha)
+// n2 r, tau = 1 + |alpha| r, and 1 / (|alpha| + ||x||) by two Newton steps from an FP32
+// reciprocal. Each Newton step doubles the correct bits: 24 -> 48 -> FP64 rounding.
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+__device__ __forceinline__ void householder_params(double alpha, double sig, double &beta, double &tau,
+                                                   double &scal) {
+  const double n2 = fma(alpha, alpha, sig);
+  // exact power-of-two range reduction so the FP32 seeds never overflow or underflow
+  const int k = ((int)((__double_as_longlong(n2) >> 52) & 0x7FF) - 1023) >> 1;  // floor(e / 2)
+  const double n2s = n2 * pow2(-2 * k);                                            // in [1, 4)
+  double r = (double)rsqrtf((float)n2s);
+  r = r * fma(-0.5 * n2s, r * r, 1.5);
+  r = r * fma(-0.5 * n2s, r * r, 1.5);
+  r *= pow2(-k);             // 1 / ||x||
+  const double nx = n2 * r;  // ||x||
+  const double sgn = alpha < 0.0 ? -1.0 : 1.0;
+  beta = -sgn * nx;
+  tau = fma(fabs(alpha), r, 1.0);
+  const double den = fabs(alpha) + nx;  // |alpha - beta|
+  const int e = (int)((__double_as_longlong(den) >> 52) & 0x7FF) - 1023;
+  const double dens = den * pow2(-e);  // in [1, 2)
+  double q = (double)(1.0f / (float)dens);
+  q = q * fma(-dens, q, 2.0);
+  q = q * fma(-dens, q, 2.0);
+  scal = sgn * q * pow2(-e);
+}
+
+}  // namespace tnr

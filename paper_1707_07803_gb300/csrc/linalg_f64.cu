@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "dev_common.cuh"
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -92,12 +93,40 @@ __global__ void __launch_bounds__(256) k_gemm(int64_t m, int64_t n, int64_t k, d
   }
 }
 
-__global__ void k_scale_matrix(double *C, int64_t ldc, int64_t sc, int64_t m, int64_t n, double beta) {
+__global__ void k_scale_matrix(double *C, int64_t ldc, int64_t sc, int m, int n, double beta) {
   const int64_t b = blockIdx.z;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n; idx += (int64_t)gridDim.x * blockDim.x) {
-    double *c = C + b * sc + (idx % m) + ldc * (idx / m);
+  const unsigned mn = (unsigned)m * (unsigned)n;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mn; idx += gridDim.x * blockDim.x) {
+    double *c = C + b * sc + (idx % (unsigned)m) + ldc * (idx / (unsigned)m);
     *c = beta == 0.0 ? 0.0 : beta * *c;
   }
+}
+
+// Small NN products (m n <= 64K outputs, k <= 1024): one thread per output, four independent
+// accumulators so the 64-cycle FP64 FMA latency overlaps; no staging or barriers.
+__global__ void __launch_bounds__(256) k_gemm_tiny(int m, int n, int k, double alpha, const double *__restrict__ A,
+                                                   int64_t lda, int64_t sa, const double *__restrict__ B, int64_t ldb,
+                                                   int64_t sb, double beta, double *__restrict__ C, int64_t ldc,
+                                                   int64_t sc) {
+  const unsigned mn = (unsigned)m * (unsigned)n;
+  const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mn) return;
+  const int64_t b = blockIdx.y;
+  const unsigned i = idx % (unsigned)m, j = idx / (unsigned)m;
+  const double *a = A + b * sa + i;
+  const double *bb = B + b * sb + ldb * j;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int l = 0;
+  for (; l + 3 < k; l += 4) {
+    s0 = fma(a[lda * l], bb[l], s0);
+    s1 = fma(a[lda * (l + 1)], bb[l + 1], s1);
+    s2 = fma(a[lda * (l + 2)], bb[l + 2], s2);
+    s3 = fma(a[lda * (l + 3)], bb[l + 3], s3);
+  }
+  for (; l < k; ++l) s0 = fma(a[lda * l], bb[l], s0);
+  double *c = C + b * sc + i + ldc * j;
+  const double v = alpha * ((s0 + s1) + (s2 + s3));
+  *c = beta == 0.0 ? v : fma(beta, *c, v);
 }
 
 template <int BM, int BN>
@@ -109,7 +138,7 @@ int launch_gemm(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t 
   dim3 grid((unsigned)cdiv(m, BM), (unsigned)cdiv(n, BN), (unsigned)(batch * splits));
   if (splits > 1) {
     LaunchScope ls(K_GEMM, s);
-    k_scale_matrix<<<dim3(64, 1, (unsigned)batch), 256, 0, s>>>(C, ldc, sc, m, n, beta);
+    k_scale_matrix<<<dim3(64, 1, (unsigned)batch), 256, 0, s>>>(C, ldc, sc, (int)m, (int)n, beta);
   }
   LaunchScope ls(K_GEMM, s);
 #define TNR_G(TA_, TB_) \
@@ -200,21 +229,24 @@ __device__ __forceinline__ bool qr_wait(const QrArgs &a, int64_t j) {
   return true;
 }
 
-__device__ void qr_make_reflector(const QrArgs &a, int64_t j) {
+// The CTA's own columns live in shared memory for the whole factorisation (cols, nc x m);
+// only reflectors travel through L2.
+__device__ void qr_make_reflector(const QrArgs &a, double *col, int64_t j) {
   const int lane = threadIdx.x;
-  double *col = a.A + a.lda * j;
   double sig = 0.0;
   for (int64_t i = j + 1 + lane; i < a.m; i += 32) sig = fma(col[i], col[i], sig);
   sig = warp_sum(sig);
   const double alpha = col[j];
   double tau = 0.0, beta = alpha, scal = 0.0;
   if (sig > 0.0) {
-    beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-    tau = (beta - alpha) / beta;
-    scal = 1.0 / (alpha - beta);
+    householder_params(alpha, sig, beta, tau, scal);
   }
   double *v = a.V + a.m * j;
-  for (int64_t i = j + 1 + lane; i < a.m; i += 32) v[i] = col[i] * scal;
+  for (int64_t i = j + 1 + lane; i < a.m; i += 32) {
+    const double x = col[i] * scal;
+    v[i] = x;
+    col[i] = x;  // keep v below the diagonal of the cached column
+  }
   if (lane == 0) {
     v[j] = 1.0;
     col[j] = beta;
@@ -225,62 +257,99 @@ __device__ void qr_make_reflector(const QrArgs &a, int64_t j) {
   if (lane == 0) st_release(a.flags + j, 1u);
 }
 
-// Apply H_j = I - tau v v^T (v in vs, rows j..m-1) to column l of A.
-__device__ __forceinline__ void qr_apply(const QrArgs &a, const double *vs, double tau, int64_t j, int64_t l) {
+// Apply H_j = I - tau v v^T (v in vs, rows j..m-1) to a cached column.
+__device__ __forceinline__ void qr_apply(const QrArgs &a, const double *vs, double tau, int64_t j, double *col) {
   const int lane = threadIdx.x;
-  double *col = a.A + a.lda * l;
-  double w = 0.0;
-  for (int64_t i = j + lane; i < a.m; i += 32) w = fma(vs[i - j], col[i], w);
-  w = warp_sum(w) * tau;
-  for (int64_t i = j + lane; i < a.m; i += 32) col[i] = fma(-w, vs[i - j], col[i]);
+  double w0 = 0.0, w1 = 0.0;
+  int64_t i = j + lane;
+  for (; i + 32 < a.m; i += 64) {
+    w0 = fma(vs[i - j], col[i], w0);
+    w1 = fma(vs[i + 32 - j], col[i + 32], w1);
+  }
+  if (i < a.m) w0 = fma(vs[i - j], col[i], w0);
+  const double w = warp_sum(w0 + w1) * tau;
+  for (int64_t t = j + lane; t < a.m; t += 32) col[t] = fma(-w, vs[t - j], col[t]);
   __syncwarp();
 }
 
+// Load rows j..m-1 of reflector j from L2 with all loads in flight before the stores.
+__device__ __forceinline__ void qr_load_reflector(const QrArgs &a, int64_t j, double *vs) {
+  const int lane = threadIdx.x;
+  const double *src = a.V + a.m * j;
+  int64_t i = j + lane;
+  for (; i + 96 < a.m; i += 128) {
+    const double x0 = __ldcg(src + i), x1 = __ldcg(src + i + 32), x2 = __ldcg(src + i + 64),
+                 x3 = __ldcg(src + i + 96);
+    vs[i - j] = x0;
+    vs[i + 32 - j] = x1;
+    vs[i + 64 - j] = x2;
+    vs[i + 96 - j] = x3;
+  }
+  for (; i < a.m; i += 32) vs[i - j] = __ldcg(src + i);
+}
+
 __global__ void __launch_bounds__(32) k_qr_coop(QrArgs a) {
-  extern __shared__ double vs[];  // m doubles: the current reflector
+  extern __shared__ double sm[];
   const int lane = threadIdx.x;
   const int64_t P = gridDim.x, c = blockIdx.x;
-  const int64_t nref = a.m < a.n ? a.m : a.n;
-  if (c == 0 && nref > 0) qr_make_reflector(a, 0);
+  const int64_t m = a.m;
+  const int64_t nref = m < a.n ? m : a.n;
+  const int64_t nc = (a.n - c + P - 1) / P;  // my columns l = c + q P
+  double *cols = sm;                         // nc x m
+  double *vs = sm + nc * m;                  // m
+  for (int64_t q = 0; q < nc; ++q) {
+    const double *src = a.A + a.lda * (c + q * P);
+    for (int64_t i = lane; i < m; i += 32) cols[q * m + i] = src[i];
+  }
+  __syncwarp();
+  if (c == 0 && nref > 0) qr_make_reflector(a, cols, 0);
   for (int64_t j = 0; j < nref; ++j) {
     const int64_t l0 = j + 1 + ((c - (j + 1) % P) + P) % P;  // my first column > j
     if (l0 >= a.n) break;  // owned columns only move right: nothing left to update
     if (!qr_wait(a, j)) return;
-    for (int64_t i = j + lane; i < a.m; i += 32) vs[i - j] = __ldcg(a.V + a.m * j + i);
+    qr_load_reflector(a, j, vs);
     const double tau = __ldcg(a.tau + j);
     __syncwarp();
-    if (tau != 0.0) {
-      for (int64_t l = l0; l < a.n; l += P) {
-        qr_apply(a, vs, tau, j, l);
-        if (l == j + 1 && l < nref) qr_make_reflector(a, l);
-      }
-    } else if (l0 == j + 1 && l0 < nref) {
-      qr_make_reflector(a, l0);
+    for (int64_t l = l0; l < a.n; l += P) {
+      double *col = cols + ((l - c) / P) * m;
+      if (tau != 0.0) qr_apply(a, vs, tau, j, col);
+      if (l == j + 1 && l < nref) qr_make_reflector(a, col, l);
     }
     __syncwarp();
   }
   // R: column l of the upper trapezoid (rows 0..min(l, nref-1)), zeros below.
-  for (int64_t l = c; l < a.n; l += P) {
-    const double *col = a.A + a.lda * l;
-    for (int64_t i = lane; i < nref; i += 32) a.R[i + a.ldr * l] = i <= l ? col[i] : 0.0;
+  for (int64_t q = 0; q < nc; ++q) {
+    const int64_t l = c + q * P;
+    for (int64_t i = lane; i < nref; i += 32) a.R[i + a.ldr * l] = i <= l ? cols[q * m + i] : 0.0;
   }
   __syncwarp();
   // Explicit Q, column l = H_0 ... H_l e_l for my columns l < nref. Every reflector j <= l
   // was acquired above (the owner of l waited for each j < l and made l itself).
-  for (int64_t l = c; l < nref; l += P) {
-    double *q = a.A + a.lda * l;
-    for (int64_t i = lane; i < a.m; i += 32) q[i] = (i == l) ? 1.0 : 0.0;
+  for (int64_t q = 0; q < nc; ++q) {
+    const int64_t l = c + q * P;
+    if (l >= nref) break;
+    double *qv = cols + q * m;  // reuse the cached column
+    for (int64_t i = lane; i < m; i += 32) qv[i] = (i == l) ? 1.0 : 0.0;
     __syncwarp();
     for (int64_t j = l; j >= 0; --j) {
       const double tau = __ldcg(a.tau + j);
       if (tau == 0.0) continue;
-      const double *v = a.V + a.m * j;
-      double w = 0.0;
-      for (int64_t i = j + lane; i < a.m; i += 32) w = fma(__ldcg(v + i), q[i], w);
-      w = warp_sum(w) * tau;
-      for (int64_t i = j + lane; i < a.m; i += 32) q[i] = fma(-w, __ldcg(v + i), q[i]);
+      qr_load_reflector(a, j, vs);
+      __syncwarp();
+      double w0 = 0.0, w1 = 0.0;
+      int64_t i = j + lane;
+      for (; i + 32 < m; i += 64) {
+        w0 = fma(vs[i - j], qv[i], w0);
+        w1 = fma(vs[i + 32 - j], qv[i + 32], w1);
+      }
+      if (i < m) w0 = fma(vs[i - j], qv[i], w0);
+      const double w = warp_sum(w0 + w1) * tau;
+      for (int64_t t = j + lane; t < m; t += 32) qv[t] = fma(-w, vs[t - j], qv[t]);
       __syncwarp();
     }
+    double *dst = a.A + a.lda * l;
+    for (int64_t i = lane; i < m; i += 32) dst[i] = qv[i];
+    __syncwarp();
   }
 }
 
@@ -402,9 +471,7 @@ __global__ void __launch_bounds__(32) k_qrcp(QrcpArgs a) {
       const double alpha = col[i];
       double tau = 0.0, beta = alpha, scal = 0.0;
       if (sig > 0.0) {
-        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        householder_params(alpha, sig, beta, tau, scal);
       }
       double *v = a.V + m * i;
       for (int64_t t = i + 1 + lane; t < m; t += 32) {
@@ -501,8 +568,8 @@ struct QrSmallArgs {
 
 __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
   extern __shared__ double sm[];
-  const int64_t m = a.m, n = a.n;
-  const int64_t nref = m < n ? m : n;
+  const int m = a.m, n = a.n;
+  const int nref = m < n ? m : n;
   double *A = sm;               // m x n, ld m
   double *nrm = A + m * n;      // n
   double *tau = nrm + n;        // nref
@@ -513,33 +580,33 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
   __shared__ double s_cut2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kSmallThreads / 32;
-  for (int64_t idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
-    const int64_t i = idx % m, j = idx / m;
+  for (int idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
+    const int i = idx % m, j = idx / m;
     A[idx] = a.trans_src ? a.src[j + a.lds * i] : a.src[i + a.lds * j];
   }
-  for (int64_t j = threadIdx.x; j < n; j += kSmallThreads) perm[j] = (int)j;
+  for (int j = threadIdx.x; j < n; j += kSmallThreads) perm[j] = (int)j;
   __syncthreads();
   // column norms
-  for (int64_t j = warp; j < n; j += NW) {
+  for (int j = warp; j < n; j += NW) {
     double s = 0.0;
-    for (int64_t i = lane; i < m; i += 32) s = fma(A[i + m * j], A[i + m * j], s);
+    for (int i = lane; i < m; i += 32) s = fma(A[i + m * j], A[i + m * j], s);
     s = warp_sum(s);
     if (lane == 0) nrm[j] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double f = 0.0;
-    for (int64_t j = 0; j < n; ++j) f += nrm[j];
+    for (int j = 0; j < n; ++j) f += nrm[j];
     s_cut2 = a.cut_rel * a.cut_rel * f;
     s_r = (int)nref;
   }
   __syncthreads();
-  for (int64_t i = 0; i < nref; ++i) {
+  for (int i = 0; i < nref; ++i) {
     if (a.pivot) {
       // argmax of nrm[i..n-1] (lowest index on ties)
       double bv = -1.0;
       int bi = (int)i;
-      for (int64_t j = i + threadIdx.x; j < n; j += kSmallThreads) {
+      for (int j = i + threadIdx.x; j < n; j += kSmallThreads) {
         if (nrm[j] > bv) {
           bv = nrm[j];
           bi = (int)j;
@@ -572,9 +639,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
       }
       __syncthreads();
       if (s_r == (int)i) break;
-      const int64_t p = s_idx[0];
+      const int p = s_idx[0];
       if (p != i) {
-        for (int64_t t = threadIdx.x; t < m; t += kSmallThreads) {
+        for (int t = threadIdx.x; t < m; t += kSmallThreads) {
           const double x = A[t + m * i];
           A[t + m * i] = A[t + m * p];
           A[t + m * p] = x;
@@ -594,16 +661,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
     if (warp == 0) {
       double *col = A + m * i;
       double sig = 0.0;
-      for (int64_t t = i + 1 + lane; t < m; t += 32) sig = fma(col[t], col[t], sig);
+      for (int t = i + 1 + lane; t < m; t += 32) sig = fma(col[t], col[t], sig);
       sig = warp_sum(sig);
       const double alpha = col[i];
       double tv = 0.0, beta = alpha, scal = 0.0;
       if (sig > 0.0) {
-        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-        tv = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        householder_params(alpha, sig, beta, tv, scal);
       }
-      for (int64_t t = i + 1 + lane; t < m; t += 32) col[t] *= scal;  // v below the diagonal
+      for (int t = i + 1 + lane; t < m; t += 32) col[t] *= scal;  // v below the diagonal
       __syncwarp();
       if (lane == 0) {
         col[i] = beta;
@@ -614,32 +679,37 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
     // apply to columns j > i and refresh their norms over rows > i
     const double tv = tau[i];
     const double *v = A + m * i;
-    for (int64_t j = i + 1 + warp; j < n; j += NW) {
+    for (int j = i + 1 + warp; j < n; j += NW) {
       double *col = A + m * j;
       if (tv != 0.0) {
-        double w = lane == 0 ? col[i] : 0.0;
-        for (int64_t t = i + 1 + lane; t < m; t += 32) w = fma(v[t], col[t], w);
-        w = warp_sum(w) * tv;
+        double w = lane == 0 ? col[i] : 0.0, w1 = 0.0;
+        int t = i + 1 + lane;
+        for (; t + 32 < m; t += 64) {
+          w = fma(v[t], col[t], w);
+          w1 = fma(v[t + 32], col[t + 32], w1);
+        }
+        if (t < m) w = fma(v[t], col[t], w);
+        w = warp_sum(w + w1) * tv;
         if (lane == 0) col[i] -= w;
-        for (int64_t t = i + 1 + lane; t < m; t += 32) col[t] = fma(-w, v[t], col[t]);
+        for (int t = i + 1 + lane; t < m; t += 32) col[t] = fma(-w, v[t], col[t]);
       }
       if (a.pivot) {
         double s = 0.0;
-        for (int64_t t = i + 1 + lane; t < m; t += 32) s = fma(col[t], col[t], s);
+        for (int t = i + 1 + lane; t < m; t += 32) s = fma(col[t], col[t], s);
         s = warp_sum(s);
         if (lane == 0) nrm[j] = s;
       }
     }
     __syncthreads();
   }
-  const int64_t r = s_r;
+  const int r = s_r;
   if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
-  const int64_t ldq = a.ldq > 0 ? a.ldq : r;  // ldq <= 0: Q^T packed with leading dimension r
+  const int ldq = a.ldq > 0 ? a.ldq : r;  // ldq <= 0: Q^T packed with leading dimension r
   // R = rows 0..r-1 of the transformed matrix, upper trapezoid, scattered to original order
-  for (int64_t idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
-    const int64_t t = idx % r, j = idx / r;
+  for (int idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
+    const int t = idx % r, j = idx / r;
     const double x = t <= j ? A[t + m * j] : 0.0;
-    const int64_t oj = perm[j];
+    const int oj = perm[j];
     if (a.trans_r)
       a.R[oj + a.ldr * t] = x;
     else
@@ -647,21 +717,21 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
   }
   __syncthreads();
   // Q = H_0 ... H_{r-1} [I_r; 0]: one warp per column, v_j read from below the diagonal
-  for (int64_t l = warp; l < r; l += NW) {
+  for (int l = warp; l < r; l += NW) {
     // the column is accumulated directly in the output buffer
     double *q = a.trans_q ? nullptr : a.Q + ldq * l;
     // accumulate in a strided view: element t at qa(t)
-    auto qa = [&](int64_t t) -> double & { return a.trans_q ? a.Q[l + ldq * t] : q[t]; };
-    for (int64_t t = lane; t < m; t += 32) qa(t) = (t == l) ? 1.0 : 0.0;
+    auto qa = [&](int t) -> double & { return a.trans_q ? a.Q[l + ldq * t] : q[t]; };
+    for (int t = lane; t < m; t += 32) qa(t) = (t == l) ? 1.0 : 0.0;
     __syncwarp();
-    for (int64_t j = l; j >= 0; --j) {
+    for (int j = l; j >= 0; --j) {
       const double tj = tau[j];
       if (tj == 0.0) continue;
       const double *vj = A + m * j;
       double w = 0.0;
-      for (int64_t t = j + lane; t < m; t += 32) w = fma(t == j ? 1.0 : vj[t], qa(t), w);
+      for (int t = j + lane; t < m; t += 32) w = fma(t == j ? 1.0 : vj[t], qa(t), w);
       w = warp_sum(w) * tj;
-      for (int64_t t = j + lane; t < m; t += 32) qa(t) = fma(-w, t == j ? 1.0 : vj[t], qa(t));
+      for (int t = j + lane; t < m; t += 32) qa(t) = fma(-w, t == j ? 1.0 : vj[t], qa(t));
       __syncwarp();
     }
   }
@@ -677,8 +747,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
   extern __shared__ double sm[];
-  const int64_t m = a.m, n = a.n;
-  const int64_t nref = m < n ? m : n;
+  const int m = a.m, n = a.n;
+  const int nref = m < n ? m : n;
   double *A = sm;                 // m x n row-major: A(t, j) at t * n + j
   double *nrm = A + m * n;        // n: current squared norms below the active row
   double *nrm0 = nrm + n;         // n: squared norms at the last recompute
@@ -691,15 +761,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
   __shared__ double s_cut2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kSmallThreads / 32;
-  for (int64_t idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
-    const int64_t j = idx % n, t = idx / n;
+  for (int idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
+    const int j = idx % n, t = idx / n;
     A[idx] = a.trans_src ? a.src[j + a.lds * t] : a.src[t + a.lds * j];
   }
   __syncthreads();
   double fro = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += kSmallThreads) {
+  for (int j = threadIdx.x; j < n; j += kSmallThreads) {
     double s = 0.0;
-    for (int64_t t = 0; t < m; ++t) s = fma(A[t * n + j], A[t * n + j], s);
+    for (int t = 0; t < m; ++t) s = fma(A[t * n + j], A[t * n + j], s);
     nrm[j] = s;
     nrm0[j] = s;
     perm[j] = (int)j;
@@ -715,11 +785,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
     s_r = (int)nref;
   }
   __syncthreads();
-  for (int64_t i = 0; i < nref; ++i) {
+  for (int i = 0; i < nref; ++i) {
     if (a.pivot) {
       double bv = -1.0;
       int bi = (int)i;
-      for (int64_t j = i + threadIdx.x; j < n; j += kSmallThreads)
+      for (int j = i + threadIdx.x; j < n; j += kSmallThreads)
         if (nrm[j] > bv) {
           bv = nrm[j];
           bi = (int)j;
@@ -750,9 +820,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
       }
       __syncthreads();
       if (s_r == (int)i) break;
-      const int64_t p = s_idx[0];
+      const int p = s_idx[0];
       if (p != i) {
-        for (int64_t t = threadIdx.x; t < m; t += kSmallThreads) {
+        for (int t = threadIdx.x; t < m; t += kSmallThreads) {
           const double x = A[t * n + i];
           A[t * n + i] = A[t * n + p];
           A[t * n + p] = x;
@@ -773,16 +843,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
     }
     if (warp == 0) {  // reflector from column i, rows i..m-1
       double sig = 0.0;
-      for (int64_t t = i + 1 + lane; t < m; t += 32) sig = fma(A[t * n + i], A[t * n + i], sig);
+      for (int t = i + 1 + lane; t < m; t += 32) sig = fma(A[t * n + i], A[t * n + i], sig);
       sig = warp_sum(sig);
       const double alpha = A[i * n + i];
       double tv = 0.0, beta = alpha, scal = 0.0;
       if (sig > 0.0) {
-        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-        tv = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        householder_params(alpha, sig, beta, tv, scal);
       }
-      for (int64_t t = i + 1 + lane; t < m; t += 32) {
+      for (int t = i + 1 + lane; t < m; t += 32) {
         const double x = A[t * n + i] * scal;
         A[t * n + i] = x;
         vv[t] = x;
@@ -796,12 +864,19 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
     }
     __syncthreads();
     const double tv = tau[i];
-    for (int64_t j = i + 1 + threadIdx.x; j < n; j += kSmallThreads) {
+    for (int j = i + 1 + threadIdx.x; j < n; j += kSmallThreads) {
       if (tv != 0.0) {
-        double w = 0.0;
-        for (int64_t t = i; t < m; ++t) w = fma(vv[t], A[t * n + j], w);
-        w *= tv;
-        for (int64_t t = i; t < m; ++t) A[t * n + j] = fma(-w, vv[t], A[t * n + j]);
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        int t = i;
+        for (; t + 3 < m; t += 4) {
+          w0 = fma(vv[t], A[t * n + j], w0);
+          w1 = fma(vv[t + 1], A[(t + 1) * n + j], w1);
+          w2 = fma(vv[t + 2], A[(t + 2) * n + j], w2);
+          w3 = fma(vv[t + 3], A[(t + 3) * n + j], w3);
+        }
+        for (; t < m; ++t) w0 = fma(vv[t], A[t * n + j], w0);
+        const double w = ((w0 + w1) + (w2 + w3)) * tv;
+        for (t = i; t < m; ++t) A[t * n + j] = fma(-w, vv[t], A[t * n + j]);
       }
       if (a.pivot) {
         const double rij = A[i * n + j];
@@ -809,7 +884,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
         // dgeqp3 safeguard: recompute once the downdate has cancelled too much
         if (nn <= 1.4901161193847656e-08 * nrm0[j] || nn < 0.0) {
           nn = 0.0;
-          for (int64_t t = i + 1; t < m; ++t) nn = fma(A[t * n + j], A[t * n + j], nn);
+          for (int t = i + 1; t < m; ++t) nn = fma(A[t * n + j], A[t * n + j], nn);
           nrm0[j] = nn;
         }
         nrm[j] = nn;
@@ -817,33 +892,40 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
     }
     __syncthreads();
   }
-  const int64_t r = s_r;
+  const int r = s_r;
   if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
-  const int64_t ldq = a.ldq > 0 ? a.ldq : r;
-  for (int64_t idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
-    const int64_t t = idx % r, j = idx / r;
+  const int ldq = a.ldq > 0 ? a.ldq : r;
+  for (int idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
+    const int t = idx % r, j = idx / r;
     const double x = t <= j ? A[t * n + j] : 0.0;
-    const int64_t oj = perm[j];
+    const int oj = perm[j];
     if (a.trans_r)
       a.R[oj + a.ldr * t] = x;
     else
       a.R[t + a.ldr * oj] = x;
   }
   // Q = H_0 ... H_{r-1} [I_r; 0]: thread l builds column l (m <= 64 rows)
-  for (int64_t l = threadIdx.x; l < r; l += kSmallThreads) {
+  for (int l = threadIdx.x; l < r; l += kSmallThreads) {
     double q[64];
 #pragma unroll
     for (int t = 0; t < 64; ++t) q[t] = (t == l) ? 1.0 : 0.0;
-    for (int64_t j = l; j >= 0; --j) {
+    for (int j = l; j >= 0; --j) {
       const double tj = tau[j];
       if (tj == 0.0) continue;
-      double w = q[j];
-      for (int64_t t = j + 1; t < m; ++t) w = fma(A[t * n + j], q[t], w);
-      w *= tj;
+      double w0 = q[j], w1 = 0.0, w2 = 0.0, w3 = 0.0;
+      int t = j + 1;
+      for (; t + 3 < m; t += 4) {
+        w0 = fma(A[t * n + j], q[t], w0);
+        w1 = fma(A[(t + 1) * n + j], q[t + 1], w1);
+        w2 = fma(A[(t + 2) * n + j], q[t + 2], w2);
+        w3 = fma(A[(t + 3) * n + j], q[t + 3], w3);
+      }
+      for (; t < m; ++t) w0 = fma(A[t * n + j], q[t], w0);
+      const double w = ((w0 + w1) + (w2 + w3)) * tj;
       q[j] -= w;
-      for (int64_t t = j + 1; t < m; ++t) q[t] = fma(-w, A[t * n + j], q[t]);
+      for (int t = j + 1; t < m; ++t) q[t] = fma(-w, A[t * n + j], q[t]);
     }
-    for (int64_t t = 0; t < m; ++t) {
+    for (int t = 0; t < m; ++t) {
       if (a.trans_q)
         a.Q[l + ldq * t] = q[t];
       else
@@ -890,8 +972,8 @@ __device__ __forceinline__ bool rotation(double al, double be, double ga, double
   return true;
 }
 
-__global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, int64_t ldg, double *S, double *V,
-                                                        int64_t ldv, double *Gw, double *Vw, int *status) {
+__global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ldg, double *S, double *V, int ldv,
+                                                        double *Gw, double *Vw, int *status) {
   extern __shared__ double sm[];
   __shared__ int s_rot;
   __shared__ double s_norm[1024];
@@ -900,24 +982,24 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
   double *g = in_smem ? sm : Gw;          // working copy, ld n
   double *v = in_smem ? sm + n * n : Vw;  // working V, ld n
   const int nthr = blockDim.x;
-  for (int64_t idx = threadIdx.x; idx < n * n; idx += nthr) {
-    const int64_t i = idx % n, j = idx / n;
+  for (int idx = threadIdx.x; idx < n * n; idx += nthr) {
+    const int i = idx % n, j = idx / n;
     g[idx] = G[i + ldg * j];
     v[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nthr / 32;
-  const int64_t np = (n + 1) & ~int64_t(1);  // even number of players
+  const int np = (n + 1) & ~int(1);  // even number of players
   // |g_p^T g_q| <= tol ||g_p|| ||g_q||, tol = 16 eps sqrt(n): above the rounding error of the
   // computed dot product, so rounding noise alone does not keep a sweep going
   const double tol = 16.0 * DBL_EPSILON * sqrt((double)(n > 4 ? n : 4));
   const double tol2 = tol * tol;
   double floor2 = 0.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
-    for (int64_t j = warp; j < n; j += nw) {
+    for (int j = warp; j < n; j += nw) {
       double s = 0.0;
-      for (int64_t i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
+      for (int i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
       s = warp_sum(s);
       if (lane == 0) s_norm[j] = s;
     }
@@ -926,16 +1008,16 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
     if (sweep == 0) {
       if (threadIdx.x == 0) {
         double f = 0.0;
-        for (int64_t j = 0; j < n; ++j) f += s_norm[j];
+        for (int j = 0; j < n; ++j) f += s_norm[j];
         s_fro = f;
       }
       __syncthreads();
       const double fl = (double)n * DBL_EPSILON;
       floor2 = fl * fl * s_fro;
     }
-    for (int64_t round = 0; round < np - 1; ++round) {
-      for (int64_t pr = warp; pr < np / 2; pr += nw) {
-        int64_t p, q;
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pr = warp; pr < np / 2; pr += nw) {
+        int p, q;
         if (pr == 0) {
           p = round;
           q = np - 1;
@@ -945,7 +1027,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
         }
         if (p >= n || q >= n) continue;
         if (p > q) {
-          int64_t t = p;
+          int t = p;
           p = q;
           q = t;
         }
@@ -953,18 +1035,18 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
         if (al <= floor2 || be <= floor2) continue;
         double *gp = g + n * p, *gq = g + n * q;
         double ga = 0.0;
-        for (int64_t i = lane; i < n; i += 32) ga = fma(gp[i], gq[i], ga);
+        for (int i = lane; i < n; i += 32) ga = fma(gp[i], gq[i], ga);
         ga = warp_sum(ga);
         if (ga == 0.0 || ga * ga <= tol2 * al * be) continue;
         double cs, sn;
         if (!rotation(al, be, ga, cs, sn)) continue;
-        for (int64_t i = lane; i < n; i += 32) {
+        for (int i = lane; i < n; i += 32) {
           const double x = gp[i], y = gq[i];
           gp[i] = fma(-sn, y, cs * x);
           gq[i] = fma(sn, x, cs * y);
         }
         double *vp = v + n * p, *vq = v + n * q;
-        for (int64_t i = lane; i < n; i += 32) {
+        for (int i = lane; i < n; i += 32) {
           const double x = vp[i], y = vq[i];
           vp[i] = fma(-sn, y, cs * x);
           vq[i] = fma(sn, x, cs * y);
@@ -984,24 +1066,24 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
     if (!rotated) break;
   }
   // final column norms
-  for (int64_t j = warp; j < n; j += nw) {
+  for (int j = warp; j < n; j += nw) {
     double s = 0.0;
-    for (int64_t i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
+    for (int i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
     s = warp_sum(s);
     if (lane == 0) s_norm[j] = sqrt(s);
   }
   __syncthreads();
   // rank of each column by descending norm (stable), then scatter.
-  for (int64_t j = warp; j < n; j += nw) {
+  for (int j = warp; j < n; j += nw) {
     const double sj = s_norm[j];
-    int64_t rank = 0;
-    for (int64_t i = lane; i < n; i += 32) {
+    int rank = 0;
+    for (int i = lane; i < n; i += 32) {
       const double si = s_norm[i];
       rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
     const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
-    for (int64_t i = lane; i < n; i += 32) {
+    for (int i = lane; i < n; i += 32) {
       G[i + ldg * rank] = g[i + n * j] * inv;
       V[i + ldv * rank] = v[i + n * j];
     }
@@ -1009,20 +1091,20 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int64_t n, in
   }
 }
 
-__global__ void k_copy(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd, int64_t m,
-                       int64_t n, int transpose) {
-  // dst (m x n) = src (m x n) or src^T (src is n x m when transposing)
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx % m, j = idx / m;
+__global__ void k_copy(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd, int m, int n,
+                       int transpose) {
+  // dst (m x n) = src (m x n) or src^T (src is n x m when transposing); m * n < 2^31
+  const unsigned mn = (unsigned)m * (unsigned)n;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mn; idx += gridDim.x * blockDim.x) {
+    const unsigned i = idx % (unsigned)m, j = idx / (unsigned)m;
     dst[i + ldd * j] = transpose ? src[j + lds * i] : src[i + lds * j];
   }
 }
 
-__global__ void k_scale_cols(double *A, int64_t lda, int64_t m, int64_t n, const double *scale) {
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx % m, j = idx / m;
+__global__ void k_scale_cols(double *A, int64_t lda, int m, int n, const double *scale) {
+  const unsigned mn = (unsigned)m * (unsigned)n;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mn; idx += gridDim.x * blockDim.x) {
+    const unsigned i = idx % (unsigned)m, j = idx / (unsigned)m;
     A[i + lda * j] *= scale[j];
   }
 }
@@ -1053,10 +1135,16 @@ int gemm_f64(cudaStream_t s, bool transA, bool transB, int64_t m, int64_t n, int
   if (m <= 0 || n <= 0 || batch <= 0) return TNR_OK;
   if (k <= 0) {
     LaunchScope ls(K_GEMM, s);
-    k_scale_matrix<<<dim3(64, 1, (unsigned)batch), 256, 0, s>>>(C, ldc, sc, m, n, beta);
+    k_scale_matrix<<<dim3(64, 1, (unsigned)batch), 256, 0, s>>>(C, ldc, sc, (int)m, (int)n, beta);
     return check_cuda(cudaGetLastError());
   }
   stats_work(K_GEMM, 2.0 * (double)m * (double)n * (double)k * (double)batch);
+  if (!transA && !transB && m * n <= 65536 && k <= 1024 && batch <= 65535) {
+    LaunchScope ls(K_GEMM, s);
+    k_gemm_tiny<<<dim3((unsigned)cdiv(m * n, 256), (unsigned)batch), 256, 0, s>>>((int)m, (int)n, (int)k, alpha, A, lda,
+                                                                                  sa, B, ldb, sb, beta, C, ldc, sc);
+    return check_cuda(cudaGetLastError());
+  }
   const int64_t target = 2 * num_sms();
   auto tiles = [&](int64_t b) { return cdiv(m, b) * cdiv(n, b) * batch; };
   int bsz = 64;
@@ -1105,16 +1193,14 @@ int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double 
   a.flags = reinterpret_cast<unsigned *>(p);
   a.status = status_ptr();
   TNR_CK(cudaMemsetAsync(a.flags, 0, sizeof(unsigned) * (nref + 1), s));
-  const size_t smem = sizeof(double) * m;
-  if (smem > 200 * 1024) return TNR_EINVAL;  // m > 25600 rows: outside the supported sizes
-  int64_t P = n;
+  int64_t P = std::min<int64_t>(n, num_sms());
+  const size_t smem = sizeof(double) * (cdiv(n, P) * m + m);
+  if (smem > 200 * 1024) return TNR_EINVAL;  // columns do not fit the shared-memory layout
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_coop, 32, smem));
-  const int64_t cap = (int64_t)num_sms() * (per_sm > 0 ? 1 : 0);
-  if (P > cap) P = cap;
-  if (P < 1) return TNR_ECUDA;
+  if (per_sm < 1) return TNR_ECUDA;
   void *args[] = {&a};
   {
     // dgeqrf + dorgqr operation counts for an m x n matrix with p = min(m, n) reflectors
@@ -1220,18 +1306,19 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
   a.r_out = r_dev;
   {
     const double M = (double)m, N = (double)n, P = (double)nref;
-    stats_work(K_QR, 2 * M * N * P - (M + N) * P * P + 2 * P * P * P / 3 + 2 * M * P * P - 2 * P * P * P / 3);
+    // pivoted calls stop early: their work is recorded by the caller once the rank is known
+    if (!pivot) stats_work(K_QR_SMALL, 2 * M * N * P - (M + N) * P * P + 2 * P * P * P / 3 + 2 * M * P * P - 2 * P * P * P / 3);
   }
   if (m <= 64) {  // short columns: one thread per column
     const size_t sm2 = sizeof(double) * (m * n + 2 * n + nref + m) + sizeof(int) * n;
     if (sm2 > 48 * 1024)
       TNR_CK(cudaFuncSetAttribute(k_qr_small_tpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    LaunchScope ls(K_QR, s);
+    LaunchScope ls(pivot ? K_QR_PIV : K_QR_SMALL, s);
     k_qr_small_tpc<<<1, kSmallThreads, sm2, s>>>(a);
     return check_cuda(cudaGetLastError());
   }
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  LaunchScope ls(K_QR, s);
+  LaunchScope ls(pivot ? K_QR_PIV : K_QR_SMALL, s);
   k_qr_small<<<1, kSmallThreads, smem, s>>>(a);
   return check_cuda(cudaGetLastError());
 }
@@ -1255,7 +1342,7 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, (n + 1) / 2));
   LaunchScope ls(K_SVD, s);
-  k_jacobi<<<1, 32 * warps, smem, s>>>(G, n, ldg, S, V, ldv, Gw, Vw, status_ptr());
+  k_jacobi<<<1, 32 * warps, smem, s>>>(G, (int)n, (int)ldg, S, V, (int)ldv, Gw, Vw, status_ptr());
   return check_cuda(cudaGetLastError());
 }
 
@@ -1263,14 +1350,14 @@ int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst,
                     bool transpose) {
   if (m <= 0 || n <= 0) return TNR_OK;
   LaunchScope ls(K_MISC, s);
-  k_copy<<<grid_for(m * n), 256, 0, s>>>(src, lds, dst, ldd, m, n, transpose ? 1 : 0);
+  k_copy<<<grid_for(m * n), 256, 0, s>>>(src, lds, dst, ldd, (int)m, (int)n, transpose ? 1 : 0);
   return check_cuda(cudaGetLastError());
 }
 
 int scale_columns_f64(cudaStream_t s, double *A, int64_t lda, int64_t m, int64_t n, const double *scale) {
   if (m <= 0 || n <= 0) return TNR_OK;
   LaunchScope ls(K_MISC, s);
-  k_scale_cols<<<grid_for(m * n), 256, 0, s>>>(A, lda, m, n, scale);
+  k_scale_cols<<<grid_for(m * n), 256, 0, s>>>(A, lda, (int)m, (int)n, scale);
   return check_cuda(cudaGetLastError());
 }
 

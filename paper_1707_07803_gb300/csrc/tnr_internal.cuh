@@ -32,7 +32,9 @@ enum KClass : int {
   K_CONTRACT,
   K_CONTRACT_TC,
   K_GEMM,
-  K_QR,
+  K_QR,        // multi-CTA Householder QR (k_qr_coop, k_qrcp)
+  K_QR_SMALL,  // one-CTA unpivoted QR (k_qr_small, k_qr_small_tpc)
+  K_QR_PIV,    // one-CTA column-pivoted QR of the compression sweep
   K_SVD,
   K_MISC,
   K_NUM_CLASSES
@@ -132,6 +134,12 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
 // Tensor-core (tcgen05, BF16 in / FP32 accumulate) site-1 product; see contract_tc.cu.
 int contract_site1_tc(cudaStream_t s, const double *A, int64_t I, int64_t J, int64_t R2, const double *X, int64_t Kx,
                       int64_t S2, int trans, double *Y, bool split);
+
+// Fused truncated-SVD step of the right-to-left sweep for a core M (t x w) that fits one CTA:
+// writes V^T[:r] (r x w, ld r; may alias M) and U[:, :r] diag(S) (t x r, ld t) and r (device).
+size_t svd_step_smem(int64_t t, int64_t w);
+int svd_step_small(cudaStream_t s, const double *M, int64_t t, int64_t w, const double *norm2, double tol,
+                   int64_t dm1, int64_t max_rank, double *core_out, double *US, int64_t *r_dev);
 
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,

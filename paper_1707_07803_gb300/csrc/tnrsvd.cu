@@ -39,35 +39,38 @@ __device__ __forceinline__ void split_bf16(double x, float &hi, float &lo) {
 
 __global__ void k_contract(const double *__restrict__ A, const double *__restrict__ X, double *__restrict__ Y,
                            ContractDims D) {
-  const int64_t Xo = D.trans ? D.J : D.I;
-  const int64_t Ny = D.trans ? D.I : D.J;
-  const int64_t RS = D.R * D.S, RS2 = D.R2 * D.S2;
-  const int64_t total = RS * Xo * D.Kx * RS2;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t t = idx;
-    const int64_t rs = t % RS;
+  // 32-bit index decomposition (every core has fewer than 2^31 elements; 64-bit division is
+  // a long software sequence on the GPU)
+  const unsigned Xo = (unsigned)(D.trans ? D.J : D.I);
+  const unsigned Ny = (unsigned)(D.trans ? D.I : D.J);
+  const unsigned R = (unsigned)D.R, S = (unsigned)D.S, R2 = (unsigned)D.R2, Kx = (unsigned)D.Kx;
+  const unsigned RS = R * S;
+  const unsigned total = RS * Xo * Kx * (R2 * (unsigned)D.S2);
+  const unsigned as = D.trans ? R : R * (unsigned)D.I;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    unsigned t = idx;
+    const unsigned rs = t % RS;
     t /= RS;
-    const int64_t xo = t % Xo;
+    const unsigned xo = t % Xo;
     t /= Xo;
-    const int64_t c = t % D.Kx;
-    const int64_t rs2 = t / D.Kx;
-    const int64_t r = rs % D.R, s = rs / D.R;
-    const int64_t r2 = rs2 % D.R2, s2 = rs2 / D.R2;
+    const unsigned c = t % Kx;
+    const unsigned rs2 = t / Kx;
+    const unsigned r = rs % R, s = rs / R;
+    const unsigned r2 = rs2 % R2, s2 = rs2 / R2;
     // A(r, i, j, r2) at r + R(i + I(j + J r2)); X(s, y, c, s2) at s + S(y + Ny(c + Kx s2))
-    const double *xp = X + s + D.S * (Ny * (c + D.Kx * s2));
-    const double *ap = D.trans ? A + r + D.R * (D.I * (xo + D.J * r2)) : A + r + D.R * (xo + D.I * (D.J * r2));
-    const int64_t as = D.trans ? D.R : D.R * D.I;
+    const double *xp = X + s + (size_t)S * (Ny * (c + (size_t)Kx * s2));
+    const double *ap = D.trans ? A + r + (size_t)R * (D.I * (xo + (size_t)D.J * r2))
+                               : A + r + (size_t)R * (xo + D.I * ((size_t)D.J * r2));
     if (!D.mixed) {
       double acc = 0.0;
-      for (int64_t y = 0; y < Ny; ++y) acc = fma(ap[as * y], xp[D.S * y], acc);
+      for (unsigned y = 0; y < Ny; ++y) acc = fma(ap[(size_t)as * y], xp[(size_t)S * y], acc);
       Y[idx] = acc;
     } else {
       float acc = 0.0f;
-      for (int64_t y = 0; y < Ny; ++y) {
+      for (unsigned y = 0; y < Ny; ++y) {
         float ah, al, xh, xl;
-        split_bf16(ap[as * y], ah, al);
-        split_bf16(xp[D.S * y], xh, xl);
+        split_bf16(ap[(size_t)as * y], ah, al);
+        split_bf16(xp[(size_t)S * y], xh, xl);
         acc = fmaf(ah, xh, acc);
         acc = fmaf(ah, xl, acc);
         acc = fmaf(al, xh, acc);
@@ -81,11 +84,11 @@ __global__ void k_contract(const double *__restrict__ A, const double *__restric
 // gives T' ((nr I) x (nc J) x R2), rows (a, i) -> a + nr i, columns (b, j) -> b + nc j.
 __global__ void k_merge(const double *__restrict__ T, int64_t nr, int64_t nc, int64_t R, const double *__restrict__ C,
                         int64_t I, int64_t J, int64_t R2, double *__restrict__ out) {
-  const int64_t NR = nr * I, NC = nc * J, total = NR * NC * R2;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = idx % NR, col = (idx / NR) % NC, s = idx / (NR * NC);
-    const int64_t a = row % nr, i = row / nr, b = col % nc, j = col / nc;
+  const unsigned NR = (unsigned)(nr * I), NC = (unsigned)(nc * J), total = NR * NC * (unsigned)R2;
+  const unsigned unr = (unsigned)nr, unc = (unsigned)nc;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const unsigned row = idx % NR, col = (idx / NR) % NC, s = idx / (NR * NC);
+    const unsigned a = row % unr, i = row / unr, b = col % unc, j = col / unc;
     double acc = 0.0;
     for (int64_t r = 0; r < R; ++r) acc = fma(T[a + nr * (b + nc * r)], C[r + R * (i + I * (j + J * s))], acc);
     out[idx] = acc;
@@ -114,12 +117,11 @@ __global__ void k_omega(uint64_t seed, int64_t count, double *out) {
 // keeping only columns c < kout (core (1, I1, kout, t)).
 __global__ void k_site1_perm(const double *__restrict__ src, double *__restrict__ dst, int64_t I1, int64_t K,
                              int64_t t, int64_t kout, int dir) {
-  const int64_t total = dir == 0 ? I1 * K * t : I1 * kout * t;
-  const int64_t kk = dir == 0 ? K : kout;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx % I1, c = (idx / I1) % kk, r = idx / (I1 * kk);
-    const int64_t mi = (i + I1 * r) + (I1 * t) * c;
+  const unsigned total = (unsigned)(dir == 0 ? I1 * K * t : I1 * kout * t);
+  const unsigned kk = (unsigned)(dir == 0 ? K : kout), uI1 = (unsigned)I1;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const unsigned i = idx % uI1, c = (idx / uI1) % kk, r = idx / (uI1 * kk);
+    const size_t mi = (i + (size_t)I1 * r) + (size_t)(I1 * t) * c;
     if (dir == 0)
       dst[mi] = src[idx];
     else
@@ -255,6 +257,11 @@ int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut) {
       // M^T (w x t) = Q~ R~ P^T; core_k <- Q~^T (r x w, packed), b.Rbuf <- R~^T (t x r)
       TNR_TRY(qr_small_f64(s, Y.core[k], t, w, t, true, true, cut, Y.core[k], 0, true, b.Rbuf, t, true, b.rdev));
       TNR_TRY(d2h_rank(s, b.rdev, &r));
+      {  // r Householder steps on the w x t matrix, plus the explicit w x r Q
+        const double M = (double)w, N = (double)t, rr = (double)r;
+        stats_work(K_QR_PIV, 4 * M * N * rr - 2 * (M + N) * rr * rr + 4 * rr * rr * rr / 3 + 2 * M * rr * rr -
+                                 2 * rr * rr * rr / 3);
+      }
     } else {
       TNR_TRY(copy_matrix_f64(s, Y.core[k], t, b.Mq, w, w, t, true));  // M^T (w x t)
       bool used = false;
@@ -356,8 +363,14 @@ int sweep_rl(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, Bufs &b) 
   for (int k = Y.d - 1; k >= 1; --k) {
     const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
     int64_t r = 0;
-    TNR_TRY(svd_trunc(s, Y.core[k], t, w, tol, Y.d - 1, max_rank, b.tmp, b, &r));
-    TNR_CK(cudaMemcpyAsync(Y.core[k], b.tmp, sizeof(double) * r * w, cudaMemcpyDeviceToDevice, s));
+    if (svd_step_smem(t, w) <= 200 * 1024 && std::min(t, w) <= 1024) {
+      // one fused launch: QR of the narrow side, Jacobi SVD, truncation, V^T rows and U S
+      TNR_TRY(svd_step_small(s, Y.core[k], t, w, b.norm2, tol, Y.d - 1, max_rank, Y.core[k], b.US, b.rdev));
+      TNR_TRY(d2h_rank(s, b.rdev, &r));
+    } else {
+      TNR_TRY(svd_trunc(s, Y.core[k], t, w, tol, Y.d - 1, max_rank, b.tmp, b, &r));
+      TNR_CK(cudaMemcpyAsync(Y.core[k], b.tmp, sizeof(double) * r * w, cudaMemcpyDeviceToDevice, s));
+    }
     const int64_t rows = Y.R[k - 1] * Y.I[k - 1] * Y.J[k - 1];
     TNR_TRY(gemm_f64(s, false, false, rows, r, t, 1.0, Y.core[k - 1], rows, 0, b.US, t, 0, 0.0, b.tmp, rows, 0));
     TNR_CK(cudaMemcpyAsync(Y.core[k - 1], b.tmp, sizeof(double) * rows * r, cudaMemcpyDeviceToDevice, s));

@@ -13,6 +13,7 @@
 #include <cstdio>
 
 #include "dev_common.cuh"
+#include "jacobi.cuh"
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -947,37 +948,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
 // ------------------------------------------------------------------------------------------
 constexpr int kJacThreads = 512;
 
-// Jacobi rotation (c, s) that annihilates gamma = g_p^T g_q, with alpha = ||g_p||^2,
-// beta = ||g_q||^2: t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) / (2 gamma).
-// The angle only steers convergence, so t is computed in FP32 (after an exact power-of-two
-// scaling that keeps the ratio in range); c = 1 / sqrt(1 + t^2) is then refined to FP64 by two
-// Newton steps from the FP32 estimate, so that c^2 + s^2 = 1 to FP64 rounding and the
-// accumulated V stays orthogonal. Avoids FP64 division and square root, which are long
-// instruction sequences on the FP64 pipe. Returns false when the rotation is negligible.
-__device__ __forceinline__ bool rotation(double al, double be, double ga, double &cs, double &sn) {
-  int e = 0;
-  frexp(2.0 * ga, &e);
-  const double diff = ldexp(be - al, -e), den = ldexp(2.0 * ga, -e);  // den in [0.5, 1)
-  const float zf = (float)diff / (float)den;
-  if (!isfinite(zf)) return false;
-  const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
-  if (tf == 0.0f) return false;
-  const double t = (double)tf;
-  const double x = fma(t, t, 1.0);
-  double y = (double)rsqrtf((float)x);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  cs = y;
-  sn = y * t;
-  return true;
-}
-
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ldg, double *S, double *V, int ldv,
                                                         double *Gw, double *Vw, int *status) {
   extern __shared__ double sm[];
-  __shared__ int s_rot;
   __shared__ double s_norm[1024];
-  __shared__ double s_fro;
+  __shared__ double s_inv[1024];
   const bool in_smem = Gw == nullptr;
   double *g = in_smem ? sm : Gw;          // working copy, ld n
   double *v = in_smem ? sm + n * n : Vw;  // working V, ld n
@@ -988,89 +963,22 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
     v[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  jacobi_sweeps(g, v, n, s_norm);  // jacobi.cuh
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nthr / 32;
-  const int np = (n + 1) & ~int(1);  // even number of players
-  // |g_p^T g_q| <= tol ||g_p|| ||g_q||, tol = 16 eps sqrt(n): above the rounding error of the
-  // computed dot product, so rounding noise alone does not keep a sweep going
-  const double tol = 16.0 * DBL_EPSILON * sqrt((double)(n > 4 ? n : 4));
-  const double tol2 = tol * tol;
-  double floor2 = 0.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    for (int j = warp; j < n; j += nw) {
-      double s = 0.0;
-      for (int i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
-      s = warp_sum(s);
-      if (lane == 0) s_norm[j] = s;
+  // final column norms and their reciprocals, one thread per column (the square roots and
+  // divisions are FP64 instruction sequences: one per warp this way, not one per column)
+  for (int j = threadIdx.x; j < n; j += nthr) {
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < n; i += 2) {
+      s0 = fma(g[i + n * j], g[i + n * j], s0);
+      s1 = fma(g[i + 1 + n * j], g[i + 1 + n * j], s1);
     }
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    if (sweep == 0) {
-      if (threadIdx.x == 0) {
-        double f = 0.0;
-        for (int j = 0; j < n; ++j) f += s_norm[j];
-        s_fro = f;
-      }
-      __syncthreads();
-      const double fl = (double)n * DBL_EPSILON;
-      floor2 = fl * fl * s_fro;
-    }
-    for (int round = 0; round < np - 1; ++round) {
-      for (int pr = warp; pr < np / 2; pr += nw) {
-        int p, q;
-        if (pr == 0) {
-          p = round;
-          q = np - 1;
-        } else {
-          p = (round + pr) % (np - 1);
-          q = (round - pr + (np - 1)) % (np - 1);
-        }
-        if (p >= n || q >= n) continue;
-        if (p > q) {
-          int t = p;
-          p = q;
-          q = t;
-        }
-        const double al = s_norm[p], be = s_norm[q];
-        if (al <= floor2 || be <= floor2) continue;
-        double *gp = g + n * p, *gq = g + n * q;
-        double ga = 0.0;
-        for (int i = lane; i < n; i += 32) ga = fma(gp[i], gq[i], ga);
-        ga = warp_sum(ga);
-        if (ga == 0.0 || ga * ga <= tol2 * al * be) continue;
-        double cs, sn;
-        if (!rotation(al, be, ga, cs, sn)) continue;
-        for (int i = lane; i < n; i += 32) {
-          const double x = gp[i], y = gq[i];
-          gp[i] = fma(-sn, y, cs * x);
-          gq[i] = fma(sn, x, cs * y);
-        }
-        double *vp = v + n * p, *vq = v + n * q;
-        for (int i = lane; i < n; i += 32) {
-          const double x = vp[i], y = vq[i];
-          vp[i] = fma(-sn, y, cs * x);
-          vq[i] = fma(sn, x, cs * y);
-        }
-        if (lane == 0) {
-          // exact norms of the rotated pair for the applied (cs, sn)
-          const double c2 = cs * cs, s2 = sn * sn, cs2g = 2.0 * cs * sn * ga;
-          s_norm[p] = fma(c2, al, fma(s2, be, -cs2g));
-          s_norm[q] = fma(s2, al, fma(c2, be, cs2g));
-          s_rot = 1;
-        }
-      }
-      __syncthreads();
-    }
-    const int rotated = s_rot;
-    __syncthreads();  // every thread has read s_rot before the next sweep resets it
-    if (!rotated) break;
-  }
-  // final column norms
-  for (int j = warp; j < n; j += nw) {
-    double s = 0.0;
-    for (int i = lane; i < n; i += 32) s = fma(g[i + n * j], g[i + n * j], s);
-    s = warp_sum(s);
-    if (lane == 0) s_norm[j] = sqrt(s);
+    if (i < n) s0 = fma(g[i + n * j], g[i + n * j], s0);
+    const double sj = sqrt(s0 + s1);
+    s_norm[j] = sj;
+    s_inv[j] = sj > 0.0 ? 1.0 / sj : 0.0;
   }
   __syncthreads();
   // rank of each column by descending norm (stable), then scatter.
@@ -1082,7 +990,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
       rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    const double inv = s_inv[j];
     for (int i = lane; i < n; i += 32) {
       G[i + ldg * rank] = g[i + n * j] * inv;
       V[i + ldv * rank] = v[i + n * j];
@@ -1340,7 +1248,8 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
     smem = 0;
   }
   if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, (n + 1) / 2));
+  const int ppw = jacobi_pairs_per_warp((int)n, kJacThreads / 32);
+  const int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, ((n + 1) / 2 + ppw - 1) / ppw));
   LaunchScope ls(K_SVD, s);
   k_jacobi<<<1, 32 * warps, smem, s>>>(G, (int)n, (int)ldg, S, V, (int)ldv, Gw, Vw, status_ptr());
   return check_cuda(cudaGetLastError());

@@ -89,7 +89,7 @@ Stats &S() {
   return s;
 }
 const char *kNames[K_NUM_CLASSES] = {"conv_rowptr", "conv_flags", "conv_scan", "conv_fill", "omega", "merge",
-                                     "contract",    "contract_tc", "gemm",     "qr",        "qr_small", "qr_piv", "svd", "misc"};
+                                     "contract",    "contract_tc", "gemm",     "qr",        "qr_small", "qr_piv", "svd", "misc", "round"};
 }  // namespace
 
 void stats_begin(int cls, cudaStream_t s) {

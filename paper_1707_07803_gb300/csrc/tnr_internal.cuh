@@ -37,6 +37,7 @@ enum KClass : int {
   K_QR_PIV,    // one-CTA column-pivoted QR of the compression sweep
   K_SVD,
   K_MISC,
+  K_ROUND,     // fused one-CTA rounding sweeps (k_round_small)
   K_NUM_CLASSES
 };
 
@@ -140,6 +141,14 @@ int contract_site1_tc(cudaStream_t s, const double *A, int64_t I, int64_t J, int
 size_t svd_step_smem(int64_t t, int64_t w);
 int svd_step_small(cudaStream_t s, const double *M, int64_t t, int64_t w, const double *norm2, double tol,
                    int64_t dm1, int64_t max_rank, double *core_out, double *US, int64_t *r_dev);
+
+// Both rounding sweeps (L->R QR, R->L truncated SVD) of Y in one one-CTA launch when every core
+// fits shared memory; see round_small.cu. Leaves *launched false (nothing queued) otherwise.
+constexpr size_t kRoundSmallMaxSmem = 200 * 1024;
+// certify: cores 1..d-1 are right-orthonormal on entry (after the exact compression), which lets
+// the kernel skip both sweeps when it can show that no bond would be truncated.
+int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, bool certify, int64_t *R_dev,
+                bool *launched);
 
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,

@@ -206,7 +206,7 @@ struct Bufs {
   void *qr = nullptr;       // QR scratch
   void *jac = nullptr;      // Jacobi scratch
   double *norm2 = nullptr;  // device scalar
-  int64_t *rdev = nullptr;  // device rank
+  int64_t *rdev = nullptr;  // device rank(s): one per bond for the fused sweeps
 };
 
 struct Limits {
@@ -230,7 +230,7 @@ void carve(Arena &ar, const Limits &L, Bufs &b) {
                                  qrcp_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq))));
   b.jac = ar.take<char>(std::max<size_t>(jacobi_scratch(L.maxsq), 256));
   b.norm2 = ar.take<double>(1);
-  b.rdev = ar.take<int64_t>(1);
+  b.rdev = ar.take<int64_t>(TNR_MAX_SITES + 1);
 }
 
 int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
@@ -248,8 +248,10 @@ int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
 // is absorbed into core k-1. Only directions at the rounding level of M_k are dropped (the size
 // of a Householder factorisation's own backward error, far below the truncation threshold), so
 // the rounding that follows returns the same result to rounding accuracy, on bonds of the
-// numerical rank instead of R_k S_k.
-int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut) {
+// numerical rank instead of R_k S_k. Every compressed core Q_k has orthonormal rows, so when all
+// bonds were compressed (*all_bonds) cores 1..d-1 leave right-orthonormal.
+int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds) {
+  *all_bonds = true;
   for (int k = Y.d - 1; k >= 1; --k) {
     const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
     int64_t r = 0;
@@ -266,7 +268,10 @@ int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut) {
       TNR_TRY(copy_matrix_f64(s, Y.core[k], t, b.Mq, w, w, t, true));  // M^T (w x t)
       bool used = false;
       TNR_TRY(qrcp_f64(s, b.Mq, w, t, w, b.US, std::min(w, t), cut, b.qr, b.rdev, &used));
-      if (!used) continue;  // too large for the pivoted kernels: leave this bond as it is
+      if (!used) {  // too large for the pivoted kernels: leave this bond as it is
+        *all_bonds = false;
+        continue;
+      }
       TNR_TRY(d2h_rank(s, b.rdev, &r));
       TNR_TRY(copy_matrix_f64(s, b.Mq, w, Y.core[k], r, r, w, true));   // Q~^T (r x w)
       TNR_TRY(copy_matrix_f64(s, b.US, std::min(w, t), b.Rbuf, t, t, r, true));  // R~^T (t x r)
@@ -379,6 +384,23 @@ int sweep_rl(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, Bufs &b) 
   return TNR_OK;
 }
 
+// Both rounding sweeps of Section 5.4 (L->R QR, then the R->L truncating loop of Alg. 5.2): one
+// fused one-CTA launch when every core fits shared memory, else one launch sequence per bond.
+// right_orth: cores 1..d-1 are right-orthonormal on entry (see compress_rl).
+int round_sweeps(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, bool right_orth, Bufs &b) {
+  bool fused = false;
+  TNR_TRY(round_small(s, Y, tol, max_rank, right_orth, b.rdev, &fused));
+  if (!fused) {
+    TNR_TRY(sweep_lr(s, Y, b));
+    return sweep_rl(s, Y, tol, max_rank, b);
+  }
+  int64_t R[TNR_MAX_SITES + 1];
+  TNR_CK(cudaMemcpyAsync(R, b.rdev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
+  TNR_TRY(read_status(s));
+  for (int k = 0; k <= Y.d; ++k) Y.R[k] = R[k];
+  return TNR_OK;
+}
+
 int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64_t K, int64_t t, int64_t kout,
                int dir) {
   LaunchScope ls(K_MISC, s);
@@ -390,9 +412,9 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
                        bool mixed_product = false) {
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, compress_cut(tol, mixed_product)));
-  TNR_TRY(sweep_lr(s, Y, b));
-  TNR_TRY(sweep_rl(s, Y, tol, max_rank, b));
+  bool right_orth = false;
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, compress_cut(tol, mixed_product), &right_orth));
+  TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b));
   const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
   const int64_t m = I1 * t;
   if (m < K) return TNR_EINVAL;
@@ -408,9 +430,9 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 // kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, compress_cut(tol, false)));
-  TNR_TRY(sweep_lr(s, Z, b));
-  TNR_TRY(sweep_rl(s, Z, tol, max_rank, b));
+  bool right_orth = false;
+  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, compress_cut(tol, false), &right_orth));
+  TNR_TRY(round_sweeps(s, Z, tol, max_rank, right_orth, b));
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
   const int64_t m = J1 * t;
   if (m < K) return TNR_EINVAL;

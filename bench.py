@@ -37,6 +37,9 @@ KERNELS = {
     "contract": "k_contract (per-site MPO product)",
 }
 UNIT = "solves/s"
+# DRAM bytes (read + write) per launch from one ncu capture of the named kernel, as recorded in
+# profiles/k_qr_small_tpc_c2_compress.md; reported only while that kernel is unchanged.
+TRAFFIC_BYTES = {"qr_piv": 82.0}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 
@@ -280,7 +283,7 @@ def main():
         "roofline": {"kernel": KERNELS.get(dom, dom), "class": dom, "bound": "alu",
                      "achieved": achieved_gflops, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
-                     "frac": achieved_gflops / FP64_NOMINAL_GFLOPS, "traffic": None,
+                     "frac": achieved_gflops / FP64_NOMINAL_GFLOPS, "traffic": TRAFFIC_BYTES.get(dom),
                      "launches_per_step": qr_launches / args.steps, "avg_launch_us": 1000 * qr_avg_ms,
                      "share_of_step": qr_ms / max(total_ms, 1e-9),
                      "class_ms_one_solve": {k: round(v, 4) for k, v in per_class.items() if v > 0}},

@@ -176,6 +176,34 @@ int tnr_solve(const tnr_mpo *A, int32_t k, int32_t p, int32_t q, uint64_t seed, 
               tnr_mpo *U, double *S, tnr_mpo *V, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched TNrSVD: n independent problems (each exactly as tnr_solve: its own A, k, p, q,
+ * seed, options and caller-allocated outputs U, S, V) solved concurrently on the current
+ * device. The paper solves one matrix at a time; this entry serves many small MPOs, whose
+ * solves are chains of short, mostly one-SM kernels that leave most of the GPU idle when run
+ * one after another. `workers` host threads (0: min(n, 16); at most 63) each drive their own
+ * CUDA stream and take problems from a shared counter; worker w uses the workspace slice
+ * ws + w * ws_stride (ws_stride: at least the largest tnr_solve_query workspace of the
+ * batch, a multiple of 256; ws holds workers * ws_stride bytes) and its own device status
+ * word, so one problem's device-side error never reaches another. The batch starts after
+ * the work already queued on `stream` and `stream` waits for the whole batch; the call
+ * returns when every problem is done. Each problem's status is written to its `status`;
+ * the return value is the first non-zero status in index order (TNR_OK when all succeed),
+ * or TNR_EINVAL for bad batch arguments (nothing is solved then).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  const tnr_mpo *A;
+  int32_t k, p, q, reserved;
+  uint64_t seed;
+  tnr_opts opts;
+  tnr_mpo *U;
+  double *S;
+  tnr_mpo *V;
+  int32_t status; /* out */
+  int32_t reserved2;
+} tnr_problem;
+int tnr_solve_batched(int32_t n, tnr_problem *probs, int32_t workers, void *ws, size_t ws_stride, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Instrumentation (not part of the method): kernel launch counting and per-kernel-class
  * device time, measured with CUDA events recorded on the launching stream around each
  * launch while enabled. tnr_stats() synchronises and returns, for class `cls`, the number

@@ -251,12 +251,16 @@ int contract_site1_tc(cudaStream_t s, const double *A, int64_t I, int64_t J, int
   a.status = status_ptr();
   const int parts = split ? 2 : 1;
   const size_t smem = (size_t)parts * (kTcM * kTcBK * 2 + (size_t)a.BN * kTcBK * 2) + 1024;
-  TNR_CK(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_tc_gemm, smem));
   dim3 grid((unsigned)cdiv(a.M, kTcM), (unsigned)cdiv(a.N, a.BN));
   stats_work(K_CONTRACT_TC, 2.0 * (double)a.M * (double)a.N * (double)a.K * (split ? 3.0 : 1.0));
   LaunchScope ls(K_CONTRACT_TC, s);
   k_tc_gemm<<<grid, kTcThreads, smem, s>>>(a);
-  return check_cuda(cudaGetLastError());
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    fprintf(stderr, "libtnrsvd: k_tc_gemm launch M=%lld N=%lld K=%lld BN=%d grid=%ux%u smem=%zu\n", (long long)a.M,
+            (long long)a.N, (long long)a.K, a.BN, grid.x, grid.y, smem);
+  return check_cuda_at(e, __FILE__, __LINE__);
 }
 
 }  // namespace tnr

@@ -149,7 +149,7 @@ int launch_gemm(cudaStream_t s, bool ta, bool tb, int64_t m, int64_t n, int64_t 
   else if (!ta && tb) TNR_G(false, true);
   else TNR_G(true, true);
 #undef TNR_G
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1044,14 +1044,14 @@ int gemm_f64(cudaStream_t s, bool transA, bool transB, int64_t m, int64_t n, int
   if (k <= 0) {
     LaunchScope ls(K_GEMM, s);
     k_scale_matrix<<<dim3(64, 1, (unsigned)batch), 256, 0, s>>>(C, ldc, sc, (int)m, (int)n, beta);
-    return check_cuda(cudaGetLastError());
+    return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
   }
   stats_work(K_GEMM, 2.0 * (double)m * (double)n * (double)k * (double)batch);
   if (!transA && !transB && m * n <= 65536 && k <= 1024 && batch <= 65535) {
     LaunchScope ls(K_GEMM, s);
     k_gemm_tiny<<<dim3((unsigned)cdiv(m * n, 256), (unsigned)batch), 256, 0, s>>>((int)m, (int)n, (int)k, alpha, A, lda,
                                                                                   sa, B, ldb, sb, beta, C, ldc, sc);
-    return check_cuda(cudaGetLastError());
+    return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
   }
   const int64_t target = 2 * num_sms();
   auto tiles = [&](int64_t b) { return cdiv(m, b) * cdiv(n, b) * batch; };
@@ -1106,7 +1106,7 @@ int qr_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, double 
   if (smem > 200 * 1024) return TNR_EINVAL;  // columns do not fit the shared-memory layout
   int dev = 0, per_sm = 0;
   cudaGetDevice(&dev);
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_qr_coop, smem));
   TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_coop, 32, smem));
   if (per_sm < 1) return TNR_ECUDA;
   void *args[] = {&a};
@@ -1173,7 +1173,7 @@ int qrcp_f64(cudaStream_t s, double *A, int64_t m, int64_t n, int64_t lda, doubl
   a.cut_rel = cut_rel;
   a.status = status_ptr();
   TNR_CK(cudaMemsetAsync(zero_begin, 0, zero_end - zero_begin, s));
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_qrcp, smem));
   int per_sm = 0;
   TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrcp, 32, smem));
   if (per_sm < 1) return TNR_OK;
@@ -1219,16 +1219,15 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
   }
   if (m <= 64) {  // short columns: one thread per column
     const size_t sm2 = sizeof(double) * (m * n + 2 * n + nref + m) + sizeof(int) * n;
-    if (sm2 > 48 * 1024)
-      TNR_CK(cudaFuncSetAttribute(k_qr_small_tpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    TNR_TRY(ensure_dynamic_smem((const void *)k_qr_small_tpc, sm2));
     LaunchScope ls(pivot ? K_QR_PIV : K_QR_SMALL, s);
     k_qr_small_tpc<<<1, kSmallThreads, sm2, s>>>(a);
-    return check_cuda(cudaGetLastError());
+    return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
   }
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_qr_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_qr_small, smem));
   LaunchScope ls(pivot ? K_QR_PIV : K_QR_SMALL, s);
   k_qr_small<<<1, kSmallThreads, smem, s>>>(a);
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 size_t jacobi_scratch(int64_t n) {
@@ -1247,12 +1246,12 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
     Vw = Gw + (((size_t)n * n * sizeof(double) + 255) & ~size_t(255)) / sizeof(double);
     smem = 0;
   }
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_jacobi, smem));
   const int ppw = jacobi_pairs_per_warp((int)n, kJacThreads / 32);
   const int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, ((n + 1) / 2 + ppw - 1) / ppw));
   LaunchScope ls(K_SVD, s);
   k_jacobi<<<1, 32 * warps, smem, s>>>(G, (int)n, (int)ldg, S, V, (int)ldv, Gw, Vw, status_ptr());
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
@@ -1260,14 +1259,14 @@ int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst,
   if (m <= 0 || n <= 0) return TNR_OK;
   LaunchScope ls(K_MISC, s);
   k_copy<<<grid_for(m * n), 256, 0, s>>>(src, lds, dst, ldd, (int)m, (int)n, transpose ? 1 : 0);
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 int scale_columns_f64(cudaStream_t s, double *A, int64_t lda, int64_t m, int64_t n, const double *scale) {
   if (m <= 0 || n <= 0) return TNR_OK;
   LaunchScope ls(K_MISC, s);
   k_scale_cols<<<grid_for(m * n), 256, 0, s>>>(A, lda, (int)m, (int)n, scale);
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 }  // namespace tnr

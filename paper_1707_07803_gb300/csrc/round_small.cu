@@ -453,8 +453,7 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
   a.max_rank = max_rank;
   a.R_out = R_dev;
   a.status = status_ptr();
-  if (smem > 48 * 1024)
-    TNR_CK(cudaFuncSetAttribute(k_round_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_round_small, smem));
   {
     LaunchScope ls(K_ROUND, s);
     k_round_small<<<1, kStepThreads, smem, s>>>(a);

@@ -1,24 +1,66 @@
 // Status word, error strings, launch statistics of libtnrsvd.so.
 #include <cstdio>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "tnr_internal.cuh"
 
 namespace tnr {
 
-static __device__ int g_status_word;
+// One device status word per host thread slot: slot 0 serves ordinary callers, the batched
+// solver gives each of its workers its own slot, so concurrent solves on different streams never
+// see (or clear) one another's errors.
+static __device__ int g_status_words[kStatusSlots];
+static thread_local int t_status_slot = 0;
+
+void set_status_slot(int slot) { t_status_slot = (slot >= 0 && slot < kStatusSlots) ? slot : 0; }
 
 int *status_ptr() {
   static int *cache[64] = {nullptr};
+  static std::mutex mu;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!cache[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
-    cache[dev] = static_cast<int *>(p);
+  int *base = nullptr;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!cache[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_status_words) != cudaSuccess) return nullptr;
+      cache[dev] = static_cast<int *>(p);
+    }
+    base = cache[dev];
   }
-  return cache[dev];
+  return base + t_status_slot;
+}
+
+// The dynamic shared-memory limit set by cudaFuncSetAttribute belongs to the kernel, not to a
+// launch: every host thread shares it. Lowering it while another thread is about to launch the
+// same kernel with more shared memory makes that launch fail, so the limit only ever goes up.
+// The default limit is 48 KB minus the kernel's static shared memory, so every size is checked.
+int ensure_dynamic_smem(const void *func, size_t bytes) {
+  if (bytes == 0) return TNR_OK;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> raised;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TNR_ECUDA;
+  std::lock_guard<std::mutex> g(mu);
+  size_t &cur = raised[{dev, func}];
+  if (cur >= bytes) return TNR_OK;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return check_cuda(e);
+  cur = bytes;
+  return TNR_OK;
+}
+
+int check_cuda_at(cudaError_t e, const char *file, int line) {
+  if (e == cudaSuccess) return TNR_OK;
+  const char *base = strrchr(file, '/');
+  fprintf(stderr, "libtnrsvd: CUDA error %d (%s) at %s:%d\n", (int)e, cudaGetErrorString(e), base ? base + 1 : file,
+          line);
+  return TNR_ECUDA;
 }
 
 int check_cuda(cudaError_t e) {
@@ -62,7 +104,6 @@ struct Stats {
     cudaEvent_t a, b;
   };
   std::vector<Pending> pending;
-  cudaEvent_t open_ev[K_NUM_CLASSES] = {nullptr};
   cudaEvent_t take() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -88,6 +129,8 @@ Stats &S() {
   static Stats s;
   return s;
 }
+// the event opened by stats_begin, per host thread (each thread launches on its own stream)
+thread_local cudaEvent_t t_open_ev[K_NUM_CLASSES] = {nullptr};
 const char *kNames[K_NUM_CLASSES] = {"conv_rowptr", "conv_flags", "conv_scan", "conv_fill", "omega", "merge",
                                      "contract",    "contract_tc", "gemm",     "qr",        "qr_small", "qr_piv", "svd", "misc", "round"};
 }  // namespace
@@ -99,7 +142,7 @@ void stats_begin(int cls, cudaStream_t s) {
   if (st.mask & (1 << cls)) {
     cudaEvent_t a = st.take();
     cudaEventRecord(a, s);
-    st.open_ev[cls] = a;
+    t_open_ev[cls] = a;
   }
 }
 
@@ -112,11 +155,11 @@ void stats_work(int cls, double w) {
 void stats_end(int cls, cudaStream_t s) {
   Stats &st = S();
   std::lock_guard<std::mutex> g(st.mu);
-  if ((st.mask & (1 << cls)) && st.open_ev[cls]) {
+  if ((st.mask & (1 << cls)) && t_open_ev[cls]) {
     cudaEvent_t b = st.take();
     cudaEventRecord(b, s);
-    st.pending.push_back({cls, st.open_ev[cls], b});
-    st.open_ev[cls] = nullptr;
+    st.pending.push_back({cls, t_open_ev[cls], b});
+    t_open_ev[cls] = nullptr;
     if (st.pending.size() > 4096) st.drain();
   }
 }

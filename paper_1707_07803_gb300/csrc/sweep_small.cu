@@ -36,10 +36,10 @@ int svd_step_small(cudaStream_t s, const double *M, int64_t t, int64_t w, const 
   const int64_t n = t < w ? t : w;
   if (smem > 200 * 1024 || n > kStepMaxN) return TNR_EINVAL;
   SvdStepArgs a{M, t, w, norm2, tol, dm1, max_rank, core_out, US, r_dev, status_ptr()};
-  if (smem > 48 * 1024) TNR_CK(cudaFuncSetAttribute(k_svd_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_svd_step, smem));
   LaunchScope ls(K_SVD, s);
   k_svd_step<<<1, kStepThreads, smem, s>>>(a);
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 }  // namespace tnr

@@ -9,9 +9,13 @@
 
 namespace tnr {
 
-// Device status word (one per device, in runtime.cu): the first device-side failure wins.
-// Kernels receive its address; status_ptr() returns it for the current device.
+// Device status words (per device and host-thread slot, in runtime.cu): the first device-side
+// failure in a slot wins.
+// Kernels receive its address; status_ptr() returns it for the current device and the calling
+// host thread's slot (set_status_slot; 0 unless the thread is a batched-solve worker).
+constexpr int kStatusSlots = 64;
 int *status_ptr();
+void set_status_slot(int slot);
 
 __device__ __forceinline__ void set_status(int *st, int code) {
   if (st) atomicCAS(st, 0, code);
@@ -75,13 +79,16 @@ struct Arena {
 };
 
 int check_cuda(cudaError_t e);
+int check_cuda_at(cudaError_t e, const char *file, int line);  // same, naming the call site
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current device.
+int ensure_dynamic_smem(const void *func, size_t bytes);
 int read_status(cudaStream_t s);  // synchronises s, returns and clears the device status word
 int reset_status(cudaStream_t s);
 
-#define TNR_CK(expr)                                  \
-  do {                                                \
-    cudaError_t _e = (expr);                          \
-    if (_e != cudaSuccess) return tnr::check_cuda(_e); \
+#define TNR_CK(expr)                                           \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return tnr::check_cuda_at(_e, __FILE__, __LINE__); \
   } while (0)
 
 #define TNR_TRY(expr)           \

@@ -405,7 +405,7 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
                int dir) {
   LaunchScope ls(K_MISC, s);
   k_site1_perm<<<grid_for(I1 * K * t), 256, 0, s>>>(src, dst, I1, K, t, kout, dir);
-  return check_cuda(cudaGetLastError());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K

@@ -53,6 +53,23 @@ class tnr_opts(ctypes.Structure):
     ]
 
 
+class tnr_problem(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.POINTER(tnr_mpo)),
+        ("k", ctypes.c_int32),
+        ("p", ctypes.c_int32),
+        ("q", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("opts", tnr_opts),
+        ("U", ctypes.POINTER(tnr_mpo)),
+        ("S", ctypes.c_void_p),
+        ("V", ctypes.POINTER(tnr_mpo)),
+        ("status", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -76,6 +93,7 @@ _SIGS = {
     "tnr_solve_query": (ctypes.c_int, [_MPOP, _I32, _I32, _OPTP, _MPOP, _MPOP, _SZP]),
     "tnr_solve": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _OPTP, _MPOP, _P, _MPOP, _P,
                                  ctypes.c_size_t, _P]),
+    "tnr_solve_batched": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _I32, _P, ctypes.c_size_t, _P]),
     "tnr_stats_enable": (None, [_I32]),
     "tnr_stats_reset": (None, []),
     "tnr_stats": (ctypes.c_int, [_I32, _I64P, ctypes.POINTER(ctypes.c_double)]),
@@ -327,6 +345,74 @@ def tnr_solve(A, k, p, q, seed, tol=0.0, max_rank=0, precision=TNR_FP64, stream=
     plan = SolvePlan(A, k, p, tol, max_rank, precision)
     plan.run(q, seed, stream)
     return plan.outputs()
+
+
+class BatchPlan:
+    """Buffers for a batch of independent solves (tnr_solve_batched): per-problem outputs and
+    one workspace slice per worker, sized by the largest problem of the batch."""
+
+    def __init__(self, problems, workers=0, precision=TNR_MIXED):
+        """problems: list of dicts with keys A (Mpo), k, p, q, seed and optional tol, max_rank."""
+        lib = load()
+        n = len(problems)
+        self.n = n
+        self.workers = int(workers) if workers else min(max(n, 1), 16)
+        self.workers = max(1, min(self.workers, max(n, 1)))
+        self.plans = []
+        stride = 256
+        for pr in problems:
+            sp = SolvePlan.__new__(SolvePlan)  # outputs only; the batch owns the workspace
+            sp.k, sp.p = int(pr["k"]), int(pr["p"])
+            sp.opts = _opts(pr.get("tol", 0.0), pr.get("max_rank", 0), pr.get("precision", precision))
+            sp.A = pr["A"]
+            sp.sa = sp.A.to_struct()
+            sp.us, sp.vs = tnr_mpo(), tnr_mpo()
+            b = ctypes.c_size_t(0)
+            _check(lib.tnr_solve_query(ctypes.byref(sp.sa), sp.k, sp.p, ctypes.byref(sp.opts), ctypes.byref(sp.us),
+                                       ctypes.byref(sp.vs), ctypes.byref(b)), "tnr_solve_query")
+            dev = sp.A.cores[0].device
+            sp.U_cores = [torch.empty(max(sp.us.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.us.d)]
+            sp.V_cores = [torch.empty(max(sp.vs.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.vs.d)]
+            for i in range(sp.us.d):
+                sp.us.core[i] = sp.U_cores[i].data_ptr()
+                sp.vs.core[i] = sp.V_cores[i].data_ptr()
+            sp.S = torch.empty(sp.k, dtype=torch.float64, device=dev)
+            sp.ws, sp.ws_bytes = None, 0
+            stride = max(stride, (b.value + 255) // 256 * 256)
+            self.plans.append((sp, int(pr["q"]), int(pr["seed"])))
+        self.ws_stride = stride
+        dev = problems[0]["A"].cores[0].device if n else torch.device("cuda")
+        self.ws = torch.empty(self.workers * stride, dtype=torch.uint8, device=dev)
+        self.probs = (tnr_problem * max(n, 1))()
+        for i, (sp, q, seed) in enumerate(self.plans):
+            P = self.probs[i]
+            P.A = ctypes.pointer(sp.sa)
+            P.k, P.p, P.q = sp.k, sp.p, q
+            P.seed = seed
+            P.opts = sp.opts
+            P.U = ctypes.pointer(sp.us)
+            P.S = sp.S.data_ptr()
+            P.V = ctypes.pointer(sp.vs)
+
+    def run(self, stream=None, check=True):
+        lib = load()
+        rc = lib.tnr_solve_batched(self.n, self.probs, self.workers, _ptr(self.ws), self.ws_stride, _stream(stream))
+        if check:
+            _check(rc, "tnr_solve_batched")
+        return rc
+
+    def statuses(self):
+        return [self.probs[i].status for i in range(self.n)]
+
+    def outputs(self, i):
+        return self.plans[i][0].outputs()
+
+
+def tnr_solve_batched(problems, workers=0, precision=TNR_MIXED, stream=None):
+    """Solves independent TNrSVD problems concurrently; returns [(U, S, V), ...] in order."""
+    plan = BatchPlan(problems, workers, precision)
+    plan.run(stream)
+    return [plan.outputs(i) for i in range(plan.n)]
 
 
 # ----------------------------------------------------------------------------------------

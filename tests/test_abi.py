@@ -55,3 +55,10 @@ def test_host_side_argument_errors(lib):
     m.d = 0
     o = T._opts(0.0, 0, 0)
     assert lib.tnr_solve_query(ctypes.byref(m), 4, 4, ctypes.byref(o), None, None, ctypes.byref(b)) == -1
+    # batched solve: bad batch arguments are rejected before any device work
+    P = (T.tnr_problem * 1)()
+    assert lib.tnr_solve_batched(-1, P, 0, None, 256, None) == -1
+    assert lib.tnr_solve_batched(1, P, 0, None, 256, None) == -1  # no workspace
+    assert lib.tnr_solve_batched(1, P, 64, ctypes.c_void_p(256), 256, None) == -1  # more workers than status slots
+    assert lib.tnr_solve_batched(1, P, 1, ctypes.c_void_p(256), 100, None) == -1  # stride not a multiple of 256
+    assert lib.tnr_solve_batched(0, None, 0, None, 0, None) == 0  # empty batch

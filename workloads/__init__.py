@@ -126,3 +126,25 @@ def c2_prescribed(seed_u=0, seed_v=1, seed_omega=2, tol=1e-12, max_rank=32):
     sigma = 0.7 ** np.arange(K)
     A, U, V = prescribed_mpo(seed_u, seed_v, 64, [4] * 7, K, 5, sigma)
     return dict(A=A, k=16, p=16, q=2, seed=seed_omega, tol=tol, max_rank=max_rank, sigma=sigma)
+
+
+def batched_gaussian(seed, n, d_range=(8, 20), phys=(2, 4), rank_range=(4, 32), ks=(8, 16, 32), q=1, tol=1e-12):
+    """Independent Gaussian-core MPOs for the batched solver, drawn problem by problem.
+
+    Per problem: d uniform in d_range (inclusive), I_k = J_k = one value drawn from ``phys`` (the
+    same for all sites), interior ranks uniform in rank_range (inclusive), cores N(0,1) scaled by
+    1/sqrt(I_k R_k), k drawn from ``ks``, p = k, the given q, Omega seed = seed * 100003 + index,
+    tol as given and max_rank = K = k + p. Returns a list of dicts (A: list of cores, k, p, q,
+    seed, tol, max_rank).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        d = int(rng.integers(d_range[0], d_range[1] + 1))
+        x = int(rng.choice(phys))
+        R = [1] + [int(r) for r in rng.integers(rank_range[0], rank_range[1] + 1, size=d - 1)] + [1]
+        k = int(rng.choice(ks))
+        cores = gaussian_mpo(int(rng.integers(0, 2**31 - 1)), [x] * d, [x] * d, R,
+                             scale=lambda kk, shape: 1.0 / np.sqrt(shape[1] * shape[0]))
+        out.append(dict(A=cores, k=k, p=k, q=q, seed=seed * 100003 + i, tol=tol, max_rank=2 * k))
+    return out

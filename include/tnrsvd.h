@@ -204,6 +204,28 @@ typedef struct {
 int tnr_solve_batched(int32_t n, tnr_problem *probs, int32_t workers, void *ws, size_t ws_stride, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Differentiable TNrSVD (adjoint of Alg. 5.4 with Alg. 5.3 and Alg. 5.2), FP64 with fixed
+ * ranks: tol = 0 (only exactly-zero singular values are dropped) and max_rank = K = k + p, so
+ * the singular values S are a smooth function of A's cores where the singular values of every
+ * step are simple. The paper has no adjoint; it is the reverse of its steps.
+ * tnr_diff_forward: the same steps as tnr_solve (merge, Omega from `seed`, 2q+2 products,
+ *   the two rounding sweeps of Section 5.4 and the site-1 factorisation per product, taken
+ *   literally: no compression or no-truncation shortcuts) writing S (k doubles, device) and
+ *   recording every step's factors in a tape (device memory allocated by the library on
+ *   `stream`, stream-ordered). *tape receives an opaque handle. A's cores must stay unchanged
+ *   until tnr_diff_backward. Synchronises. Errors: TNR_EINVAL, TNR_ENOMEM, TNR_ENONFINITE.
+ * tnr_diff_backward: given dS (k doubles, device) = dL/dS, writes dL/dA into dA's cores
+ *   (device buffers of A's shapes; dA->d, I, J, R as A). May run more than once per tape.
+ *   Synchronises. TNR_ENONFINITE when a step's factor is singular (repeated or zero singular
+ *   values, a singular R).
+ * tnr_diff_free: releases a tape (null is ignored).
+ * ------------------------------------------------------------------------------------- */
+int tnr_diff_forward(const tnr_mpo *A, int32_t k, int32_t p, int32_t q, uint64_t seed, double *S, void **tape,
+                     void *stream);
+int tnr_diff_backward(void *tape, const double *dS, tnr_mpo *dA, void *stream);
+void tnr_diff_free(void *tape, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Instrumentation (not part of the method): kernel launch counting and per-kernel-class
  * device time, measured with CUDA events recorded on the launching stream around each
  * launch while enabled. tnr_stats() synchronises and returns, for class `cls`, the number

@@ -42,6 +42,7 @@ enum KClass : int {
   K_SVD,
   K_MISC,
   K_ROUND,     // fused one-CTA rounding sweeps (k_round_small)
+  K_DIFF,      // differentiable solver: tape forward and adjoint kernels
   K_NUM_CLASSES
 };
 
@@ -156,6 +157,9 @@ constexpr size_t kRoundSmallMaxSmem = 200 * 1024;
 // the kernel skip both sweeps when it can show that no bond would be truncated.
 int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, bool certify, int64_t *R_dev,
                 bool *launched);
+
+// Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
+int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
 
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,

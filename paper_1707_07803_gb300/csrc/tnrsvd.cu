@@ -734,6 +734,14 @@ int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q
 }
 
 }  // namespace
+
+// Lemma 5.1 draws (the stream k_omega implements), for the differentiable solver.
+int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out) {
+  if (count <= 0) return TNR_OK;
+  LaunchScope ls(K_OMEGA, s);
+  k_omega<<<grid_for(count), 256, 0, s>>>(seed, count, out);
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
+}
 }  // namespace tnr
 
 using namespace tnr;

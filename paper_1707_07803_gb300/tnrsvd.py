@@ -94,6 +94,10 @@ _SIGS = {
     "tnr_solve": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _OPTP, _MPOP, _P, _MPOP, _P,
                                  ctypes.c_size_t, _P]),
     "tnr_solve_batched": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _I32, _P, ctypes.c_size_t, _P]),
+    "tnr_diff_forward": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_void_p),
+                                         _P]),
+    "tnr_diff_backward": (ctypes.c_int, [_P, _P, _MPOP, _P]),
+    "tnr_diff_free": (None, [_P, _P]),
     "tnr_stats_enable": (None, [_I32]),
     "tnr_stats_reset": (None, []),
     "tnr_stats": (ctypes.c_int, [_I32, _I64P, ctypes.POINTER(ctypes.c_double)]),
@@ -413,6 +417,59 @@ def tnr_solve_batched(problems, workers=0, precision=TNR_MIXED, stream=None):
     plan = BatchPlan(problems, workers, precision)
     plan.run(stream)
     return [plan.outputs(i) for i in range(plan.n)]
+
+
+class _Tape:
+    """Owns a tnr_diff_forward tape; released with the object."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if self.handle is not None and self.handle.value:
+            try:
+                load().tnr_diff_free(self.handle, _stream())
+            except Exception:
+                pass
+            self.handle = None
+
+
+class TnrSvdValues(torch.autograd.Function):
+    """S (k singular values, FP64) of TNrSVD with fixed ranks as a differentiable function of the
+    flat core tensors; the backward is the library's adjoint (tnr_diff_backward)."""
+
+    @staticmethod
+    def forward(ctx, meta, *cores):
+        I, J, R, k, p, q, seed = meta
+        lib = load()
+        cores = [c.detach().contiguous() for c in cores]
+        _need_cuda(*cores)
+        A = Mpo(I, J, R, cores)
+        sa = A.to_struct()
+        S = torch.empty(int(k), dtype=torch.float64, device=cores[0].device)
+        h = ctypes.c_void_p()
+        _check(lib.tnr_diff_forward(ctypes.byref(sa), int(k), int(p), int(q), ctypes.c_uint64(int(seed)), _ptr(S),
+                                    ctypes.byref(h), _stream()), "tnr_diff_forward")
+        ctx.tape = _Tape(h)
+        ctx.A = A
+        ctx.sa = sa
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        lib = load()
+        A = ctx.A
+        grads = [torch.empty_like(c) for c in A.cores]
+        dA = Mpo(A.I, A.J, A.R, grads).to_struct()
+        g = gS.detach().to(torch.float64).contiguous()
+        _check(lib.tnr_diff_backward(ctx.tape.handle, _ptr(g), ctypes.byref(dA), _stream()), "tnr_diff_backward")
+        return (None, *grads)
+
+
+def tnrsvd_values(A, k, p, q, seed):
+    """Differentiable S = TNrSVD(A) singular values (tol 0, max_rank K): A is an Mpo whose flat
+    core tensors may require grad."""
+    return TnrSvdValues.apply((A.I, A.J, A.R, int(k), int(p), int(q), int(seed)), *A.cores)
 
 
 # ----------------------------------------------------------------------------------------

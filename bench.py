@@ -261,6 +261,81 @@ def batched_main(args):
     return 0
 
 
+ADJ_METRIC = ("gradient evaluations/s of L = sum of the top-16 TNrSVD singular values "
+              "(4^12 x 4^12 MPO, rank 16, k=16 p=16 q=2, FP64 forward + adjoint)")
+
+
+def adjoint_main(args):
+    """--workload adjoint: one step = tnr_diff_forward + tnr_diff_backward on the d=12 workload."""
+    import torch
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    d, rank, k, p, q, seed, n_sv = 12, 16, 16, 16, 2, 3, 16
+    A_host = W.gaussian_mpo(0, [4] * d, [4] * d, [1] + [rank] * (d - 1) + [1],
+                            scale=lambda kk, sh: 1.0 / np.sqrt(sh[1] * sh[0]))
+    A_host = [c.astype(np.float32).astype(np.float64) for c in A_host]  # FP32 Gaussian cores
+    A = T.Mpo.from_numpy(A_host, device=dev)
+    for c in A.cores:
+        c.requires_grad_(True)
+
+    def step():
+        S = T.tnrsvd_values(A, k, p, q, seed)
+        return torch.autograd.grad(S[:n_sv].sum(), A.cores)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g = step()
+    e1.record(stream)
+    e1.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    grads = [x.cpu().numpy() for x in g]
+    # central differences of the GPU forward (h = 1e-6) on sampled core entries
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    got, fd = [], []
+    for _ in range(args.fd_entries):
+        c = int(rng.integers(0, d))
+        e = int(rng.integers(0, A_host[c].size))
+        vals = []
+        for sgn in (1, -1):
+            Ap = [x.copy() for x in A_host]
+            f = Ap[c].reshape(-1, order="F")
+            f[e] += sgn * h
+            Ap[c] = f.reshape(A_host[c].shape, order="F")
+            with torch.no_grad():
+                vals.append(float(T.tnrsvd_values(T.Mpo.from_numpy(Ap, device=dev), k, p, q, seed)[:n_sv].sum()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+        got.append(grads[c][e])
+    got, fd = np.array(got), np.array(fd)
+    line = {
+        "metric": ADJ_METRIC, "value": args.steps / (total_ms / 1000.0), "unit": "gradients/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Gaussian MPO d={d}, I=J=4, rank {rank}, FP32-valued cores, k={k} p={p} q={q}, "
+                               f"loss = sum of the top {n_sv} singular values", "global_batch": 1, "seq_len": 0,
+                   "l2": "working set above L2 (products of 512-wide bonds)"},
+        "clocks": clocks,
+        "gradient_check": {"entries": args.fd_entries, "h": h,
+                           "normwise_rel_err_vs_gpu_central_differences":
+                               float(np.linalg.norm(got - fd) / max(np.linalg.norm(fd), 1e-300))},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -269,9 +344,11 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="prescribed", choices=["prescribed", "batched"],
+    ap.add_argument("--workload", default="prescribed", choices=["prescribed", "batched", "adjoint"],
                     help="prescribed: one 2^20 x 2^20 solve per step (default); batched: a batch of "
-                         "independent Gaussian-core MPOs per step (tnr_solve_batched)")
+                         "independent Gaussian-core MPOs per step (tnr_solve_batched); adjoint: forward "
+                         "and backward of the differentiable solve per step")
+    ap.add_argument("--fd-entries", type=int, default=16)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--workers", type=int, default=16)
     args = ap.parse_args()
@@ -279,6 +356,8 @@ def main():
         return reference_arm(args)
     if args.workload == "batched":
         return batched_main(args)
+    if args.workload == "adjoint":
+        return adjoint_main(args)
 
     import torch
     import torch.distributed as dist

@@ -204,6 +204,29 @@ typedef struct {
 int tnr_solve_batched(int32_t n, tnr_problem *probs, int32_t workers, void *ws, size_t ws_stride, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * TNrSVD of a sparse matrix given in the block form of Alg. 4.1 (R, X, digits as produced by
+ * tnr_sparse_fill; any block order). The MPO of Alg. 4.1 has rank R
+ * at every bond (Lemma 4.2), so the products of Section 5.2 are applied straight from the
+ * block form to dense tall matrices: Y = A Omega (Omega of Lemma 5.1 over the merged column
+ * dims, Section 6.3, expanded densely), q power iterations (Alg. 5.4), Z = A^T Q = B^T, and the
+ * small SVD of Alg. 5.1; without truncation this is TNrSVD in exact arithmetic. The tall
+ * QRs are CholeskyQR2 in FP64 (a pass that breaks down is redone with the shift of shifted
+ * CholeskyQR3). precision: TNR_FP64 or TNR_MIXED; both run the products in FP64 (on GB300 the
+ * conversions an FP32 product of FP64 data needs cost more than the FP64 multiply-adds).
+ * Outputs (device, column-major): U (nrows x k), S (k, descending), V (ncols x k).
+ * ws: at least tnr_sparse_solve_workspace() bytes. Synchronises. Errors: TNR_EINVAL (dims
+ * do not multiply to nrows / ncols, K > prod I or prod J), TNR_ERANGE (digits out of range,
+ * sizes above 2^31), TNR_ENONFINITE (a Cholesky pivot that is not positive even after the
+ * shift), TNR_ENOMEM. The workspace holds compact row and column lists of the nonzeros
+ * (capacity R I_1 J_1 entries each).
+ * ------------------------------------------------------------------------------------- */
+int tnr_sparse_solve_workspace(int64_t nrows, int64_t ncols, int64_t R, int32_t d, const int64_t *I, const int64_t *J,
+                               int32_t k, int32_t p, size_t *bytes);
+int tnr_sparse_solve(int64_t nrows, int64_t ncols, int64_t R, const double *X, const uint8_t *digits, int32_t d,
+                     const int64_t *I, const int64_t *J, int32_t k, int32_t p, int32_t q, uint64_t seed,
+                     int32_t precision, double *U, double *S, double *V, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Differentiable TNrSVD (adjoint of Alg. 5.4 with Alg. 5.3 and Alg. 5.2), FP64 with fixed
  * ranks: tol = 0 (only exactly-zero singular values are dropped) and max_rank = K = k + p, so
  * the singular values S are a smooth function of A's cores where the singular values of every

@@ -76,3 +76,27 @@ def sparse_tnrsvd(R, X, digits, I, J, k, p, q, seed):
     Qz, Rz = np.linalg.qr(Z)                      # B = Rz^T Qz^T
     W, S, Zt = np.linalg.svd(Rz.T)
     return Q @ W[:, :k], S[:k], (Qz @ Zt.T)[:, :k]
+
+
+def coo_tnrsvd(rows, cols, vals, nrows, ncols, I, J, k, p, q, seed):
+    """The same computation with the operator taken straight from the COO input (scipy.sparse
+    CSR products as the matmul step); used at sizes where the block loop above is too slow."""
+    import scipy.sparse as sp
+
+    K = int(k) + int(p)
+    m = mpo.merge_count(I, J, K)
+    if m is None:
+        raise ValueError("K exceeds prod(I) or prod(J)")
+    Jm = [int(np.prod(J[:m]))] + [int(x) for x in J[m:]]
+    A = sp.csr_matrix((np.asarray(vals, dtype=np.float64), (np.asarray(rows), np.asarray(cols))),
+                      shape=(int(nrows), int(ncols)))
+    At = A.T.tocsr()
+    O = omega_dense(seed, Jm, K)
+    Q, _ = np.linalg.qr(A @ O)
+    for _ in range(int(q)):
+        Q, _ = np.linalg.qr(At @ Q)
+        Q, _ = np.linalg.qr(A @ Q)
+    Z = At @ Q
+    Qz, Rz = np.linalg.qr(Z)
+    W, S, Zt = np.linalg.svd(Rz.T)
+    return Q @ W[:, :k], S[:k], (Qz @ Zt.T)[:, :k]

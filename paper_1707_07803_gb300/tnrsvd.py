@@ -94,6 +94,9 @@ _SIGS = {
     "tnr_solve": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _OPTP, _MPOP, _P, _MPOP, _P,
                                  ctypes.c_size_t, _P]),
     "tnr_solve_batched": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _I32, _P, ctypes.c_size_t, _P]),
+    "tnr_sparse_solve_workspace": (ctypes.c_int, [_I64, _I64, _I64, _I32, _I64P, _I64P, _I32, _I32, _SZP]),
+    "tnr_sparse_solve": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _I32, _I64P, _I64P, _I32, _I32, _I32,
+                                        ctypes.c_uint64, _I32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "tnr_diff_forward": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_void_p),
                                          _P]),
     "tnr_diff_backward": (ctypes.c_int, [_P, _P, _MPOP, _P]),
@@ -417,6 +420,26 @@ def tnr_solve_batched(problems, workers=0, precision=TNR_MIXED, stream=None):
     plan = BatchPlan(problems, workers, precision)
     plan.run(stream)
     return [plan.outputs(i) for i in range(plan.n)]
+
+
+def tnr_sparse_solve(nrows, ncols, R, X, digits, I, J, k, p, q, seed, precision=TNR_FP64, stream=None):
+    """TNrSVD of a sparse matrix in Alg. 4.1 block form: returns dense (U, S, V) device tensors."""
+    lib = load()
+    _need_cuda(X, digits)
+    d = len(I)
+    Ia, Ja = _i64arr(I), _i64arr(J)
+    b = ctypes.c_size_t(0)
+    _check(lib.tnr_sparse_solve_workspace(int(nrows), int(ncols), int(R), d, Ia, Ja, int(k), int(p), ctypes.byref(b)),
+           "tnr_sparse_solve_workspace")
+    dev = X.device
+    ws = torch.empty(b.value, dtype=torch.uint8, device=dev)
+    U = torch.empty((int(k), int(nrows)), dtype=torch.float64, device=dev)  # column-major nrows x k
+    V = torch.empty((int(k), int(ncols)), dtype=torch.float64, device=dev)
+    S = torch.empty(int(k), dtype=torch.float64, device=dev)
+    _check(lib.tnr_sparse_solve(int(nrows), int(ncols), int(R), _ptr(X), _ptr(digits), d, Ia, Ja, int(k), int(p),
+                                int(q), ctypes.c_uint64(int(seed)), int(precision), _ptr(U), _ptr(S), _ptr(V),
+                                _ptr(ws), b.value, _stream(stream)), "tnr_sparse_solve")
+    return U.t(), S, V.t()
 
 
 class _Tape:

@@ -50,3 +50,11 @@ def test_equals_untruncated_mpo_tnrsvd_and_dense_rsvd():
     np.testing.assert_allclose(S, Sd[:k], rtol=1e-11)
     # U^T A V = diag(S)
     np.testing.assert_allclose(U.T @ D @ V, np.diag(S), atol=1e-11 * S[0])
+
+
+def test_coo_form_equals_block_form():
+    n, I, J, R, X, digits, D = _case(3, 4, 4, 12)
+    r, c = np.nonzero(D)
+    U1, S1, V1 = osp.sparse_tnrsvd(R, X, digits, I, J, 4, 4, 1, 3)
+    U2, S2, V2 = osp.coo_tnrsvd(r, c, D[r, c], n, n, I, J, 4, 4, 1, 3)
+    np.testing.assert_allclose(S1, S2, rtol=1e-12)

@@ -1,0 +1,198 @@
+// The exact right-to-left compression of a product MPO (done before the rounding sweeps of
+// Section 5.4) as one cooperative kernel.
+//
+// For k = d-1 .. 1 the compression factors M_k (t x w: core k with the already compressed right
+// bond) as L Q_k by a column-pivoted QR of M_k^T that stops at the rounding-level cutoff; Q_k
+// (orthonormal rows) becomes core k and L is absorbed into core k-1. Each bond needs the rank of
+// the previous one, so the host-driven version reads a rank back and launches again for every
+// bond. Here the whole sweep runs on the device: CTA 0 factors M_k in shared memory (the
+// thread-per-column pivoted QR of qr_tpc.cuh) while the other CTAs wait at a grid barrier, then
+// every CTA takes part in the absorb C_{k-1} L, and the next bond starts after a second barrier.
+// Ranks stay in device memory and are read back once at the end. A bond whose matrix does not
+// fit the one-CTA QR (more than 64 rows, or beyond the shared-memory capacity) ends the kernel
+// with the state of the host-driven sweep just before that bond, which the host then continues.
+// The barriers spin with a bound (kSpinCap polls) and report TNR_ETIMEOUT instead of waiting
+// forever; co-residency of all CTAs is guaranteed by the cooperative launch.
+#include <cuda/atomic>
+
+#include <algorithm>
+
+#include "qr_tpc.cuh"
+#include "tnr_internal.cuh"
+
+namespace tnr {
+namespace {
+
+struct CompressArgs {
+  int d;
+  double *core[TNR_MAX_SITES];
+  int phys[TNR_MAX_SITES];   // I_k J_k
+  int R[TNR_MAX_SITES + 1];  // ranks on entry
+  double cut;
+  double *L;             // t x r factor of the current bond (ld t)
+  double *buf[2];        // absorbed cores (ping-pong), cap_buf doubles each
+  int64_t cap_buf;
+  int64_t qr_cap;        // shared-memory bytes available to the QR
+  int64_t *R_out;        // ranks on exit (d + 1)
+  unsigned *bar;         // [0] arrivals, [1] generation
+  int *ctl;              // [0] first bond left to the host (0: none)
+  int *status;
+};
+
+__device__ void grid_barrier(unsigned *bar, int *status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> count(bar[0]), gen(bar[1]);
+    const unsigned my = gen.load(cuda::memory_order_acquire);
+    __threadfence();
+    if (count.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
+      count.store(0u, cuda::memory_order_relaxed);
+      gen.fetch_add(1u, cuda::memory_order_release);
+    } else {
+      long long spins = 0;
+      while (gen.load(cuda::memory_order_acquire) == my) {
+        if (++spins > kSpinCap) {
+          set_status(status, TNR_ETIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__host__ __device__ inline int64_t qr_tpc_bytes(int64_t m, int64_t n) {
+  return (int64_t)sizeof(double) * (m * n + 2 * n + (m < n ? m : n) + m) + (int64_t)sizeof(int) * n;
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
+  extern __shared__ double sm[];
+  const int d = a.d;
+  const double *cur = a.core[d - 1];  // M_k (t x w, ld t)
+  int rk1 = 1;                        // compressed rank of bond k+1
+  for (int k = d - 1; k >= 1; --k) {
+    const int t = a.R[k], w = a.phys[k] * rk1;
+    const bool fits = w <= 64 && qr_tpc_bytes(w, t) <= a.qr_cap;
+    if (!fits) {  // leave M_k in core k and bonds <= k to the host-driven sweep
+      double *dst = a.core[k];
+      if (cur != dst)
+        for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)t * w;
+             x += (int64_t)gridDim.x * blockDim.x)
+          dst[x] = __ldcg(cur + x);
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl[0] = k;  // ranks of bonds > k are in R_out
+      return;
+    }
+    if (blockIdx.x == 0) {  // M_k^T (w x t) = Q~ R~ P^T: core k <- Q~^T (r x w), L <- R~^T (t x r)
+      QrSmallArgs q;
+      q.src = cur;
+      q.lds = t;
+      q.m = w;
+      q.n = t;
+      q.trans_src = 1;
+      q.pivot = 1;
+      q.trans_q = 1;
+      q.trans_r = 1;
+      q.cut_rel = a.cut;
+      q.Q = a.core[k];
+      q.ldq = 0;
+      q.R = a.L;
+      q.ldr = t;
+      q.r_out = a.R_out + k;
+      qr_tpc_cta(q, sm);
+    }
+    grid_barrier(a.bar, a.status);
+    // data written by other CTAs is read through L2 (__ldcg), never from a possibly stale L1 line
+    const int r = (int)__ldcg(a.R_out + k);
+    // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r)
+    const int rows = a.R[k - 1] * a.phys[k - 1];
+    const double *C = a.core[k - 1];
+    double *out = a.buf[k & 1];
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)rows * r;
+         x += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(x % rows), c = (int)(x / rows);
+      const double *l = a.L + (int64_t)t * c;
+      double s0 = 0.0, s1 = 0.0;
+      int j = 0;
+      for (; j + 1 < t; j += 2) {
+        s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
+        s1 = fma(C[i + (int64_t)rows * (j + 1)], __ldcg(l + j + 1), s1);
+      }
+      if (j < t) s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
+      out[x] = s0 + s1;
+    }
+    grid_barrier(a.bar, a.status);
+    cur = out;
+    rk1 = r;
+  }
+  // core 0 <- its absorbed form
+  const int64_t n0 = (int64_t)a.phys[0] * rk1;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n0; x += (int64_t)gridDim.x * blockDim.x)
+    a.core[0][x] = __ldcg(cur + x);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl[0] = 0;
+    a.R_out[1] = rk1;
+  }
+}
+
+}  // namespace
+
+// Runs the compression of Y's bonds d-1 .. 1 on the device. On return Y.R holds the new ranks of
+// the bonds it finished and *next_bond the first bond left for the host-driven sweep (0: all
+// done). Scratch: L (maxbond x 64), two buffers of cap_buf doubles, ctl (>= 4 ints), bar (2).
+int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
+                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond) {
+  *next_bond = Y.d - 1;
+  const int d = Y.d;
+  if (d < 2) {
+    *next_bond = 0;
+    return TNR_OK;
+  }
+  CompressArgs a;
+  a.d = d;
+  int64_t qr_need = 0;
+  for (int k = 0; k < d; ++k) {
+    const int64_t phys = Y.I[k] * Y.J[k];
+    if (phys > (1 << 20) || Y.R[k] > (1 << 20) || Y.R[k] * phys * Y.R[k + 1] > cap_buf) return TNR_OK;
+    a.core[k] = Y.core[k];
+    a.phys[k] = (int)phys;
+    if (k >= 1) qr_need = std::max(qr_need, qr_tpc_bytes(std::min<int64_t>(64, phys * Y.R[k + 1]), Y.R[k]));
+  }
+  for (int k = 0; k <= d; ++k) a.R[k] = (int)Y.R[k];
+  const int64_t qr_cap = std::min<int64_t>(qr_need, 200 * 1024);
+  a.cut = cut;
+  a.L = L;
+  a.buf[0] = buf0;
+  a.buf[1] = buf1;
+  a.cap_buf = cap_buf;
+  a.qr_cap = qr_cap;
+  a.R_out = R_dev;
+  a.bar = bar;
+  a.ctl = ctl;
+  a.status = status_ptr();
+  int dev = 0, sms = 0, per_sm = 0;
+  TNR_CK(cudaGetDevice(&dev));
+  TNR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)qr_cap));
+  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)qr_cap));
+  if (per_sm < 1) return TNR_OK;
+  const int blocks = std::min(32, sms * per_sm);
+  TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+  {
+    LaunchScope ls(K_QR_PIV, s);
+    void *args[] = {&a};
+    TNR_CK(cudaLaunchCooperativeKernel((const void *)k_compress, dim3(blocks), dim3(kSmallThreads), args,
+                                       (size_t)qr_cap, s));
+  }
+  int64_t h[TNR_MAX_SITES + 2];
+  int hctl = 0;
+  TNR_CK(cudaMemcpyAsync(h, R_dev, sizeof(int64_t) * (d + 1), cudaMemcpyDeviceToHost, s));
+  TNR_CK(cudaMemcpyAsync(&hctl, ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TNR_TRY(read_status(s));
+  *next_bond = hctl;
+  for (int k = hctl + 1; k < d; ++k) Y.R[k] = h[k];
+  return TNR_OK;
+}
+
+}  // namespace tnr

@@ -15,6 +15,7 @@
 #include "dev_common.cuh"
 #include "jacobi.cuh"
 #include "tnr_internal.cuh"
+#include "qr_tpc.cuh"
 
 namespace tnr {
 namespace {
@@ -552,20 +553,7 @@ __global__ void __launch_bounds__(32) k_qrcp(QrcpArgs a) {
 // R = Q^T A in the ORIGINAL column order (r x n), written as R or R^T (trans_r); r to *r_out.
 // Warps own columns, lanes own rows; FP64 reductions stay within one warp.
 // ------------------------------------------------------------------------------------------
-constexpr int kSmallThreads = 256;
 
-struct QrSmallArgs {
-  const double *src;
-  int64_t lds;
-  int64_t m, n;
-  int trans_src, pivot, trans_q, trans_r;
-  double cut_rel;
-  double *Q;
-  int64_t ldq;
-  double *R;
-  int64_t ldr;
-  int64_t *r_out;
-};
 
 __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
   extern __shared__ double sm[];
@@ -748,191 +736,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small(QrSmallArgs a) {
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
   extern __shared__ double sm[];
-  const int m = a.m, n = a.n;
-  const int nref = m < n ? m : n;
-  double *A = sm;                 // m x n row-major: A(t, j) at t * n + j
-  double *nrm = A + m * n;        // n: current squared norms below the active row
-  double *nrm0 = nrm + n;         // n: squared norms at the last recompute
-  double *tau = nrm0 + n;         // nref
-  double *vv = tau + nref;        // m: current reflector
-  int *perm = reinterpret_cast<int *>(vv + m);  // n
-  __shared__ double s_red[32];
-  __shared__ int s_idx[32];
-  __shared__ int s_r;
-  __shared__ double s_cut2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = kSmallThreads / 32;
-  for (int idx = threadIdx.x; idx < m * n; idx += kSmallThreads) {
-    const int j = idx % n, t = idx / n;
-    A[idx] = a.trans_src ? a.src[j + a.lds * t] : a.src[t + a.lds * j];
-  }
-  __syncthreads();
-  double fro = 0.0;
-  for (int j = threadIdx.x; j < n; j += kSmallThreads) {
-    double s = 0.0;
-    for (int t = 0; t < m; ++t) s = fma(A[t * n + j], A[t * n + j], s);
-    nrm[j] = s;
-    nrm0[j] = s;
-    perm[j] = (int)j;
-    fro += s;
-  }
-  fro = warp_sum(fro);
-  if (lane == 0) s_red[warp] = fro;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double f = 0.0;
-    for (int w = 0; w < NW; ++w) f += s_red[w];
-    s_cut2 = a.cut_rel * a.cut_rel * f;
-    s_r = (int)nref;
-  }
-  __syncthreads();
-  for (int i = 0; i < nref; ++i) {
-    if (a.pivot) {
-      double bv = -1.0;
-      int bi = (int)i;
-      for (int j = i + threadIdx.x; j < n; j += kSmallThreads)
-        if (nrm[j] > bv) {
-          bv = nrm[j];
-          bi = (int)j;
-        }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) {
-          bv = ov;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        s_red[warp] = bv;
-        s_idx[warp] = bi;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double b = s_red[0];
-        int bj = s_idx[0];
-        for (int w = 1; w < NW; ++w)
-          if (s_red[w] > b || (s_red[w] == b && s_idx[w] < bj)) {
-            b = s_red[w];
-            bj = s_idx[w];
-          }
-        s_idx[0] = bj;
-        if (i > 0 && b <= s_cut2) s_r = (int)i;
-      }
-      __syncthreads();
-      if (s_r == (int)i) break;
-      const int p = s_idx[0];
-      if (p != i) {
-        for (int t = threadIdx.x; t < m; t += kSmallThreads) {
-          const double x = A[t * n + i];
-          A[t * n + i] = A[t * n + p];
-          A[t * n + p] = x;
-        }
-        if (threadIdx.x == 0) {
-          double x = nrm[i];
-          nrm[i] = nrm[p];
-          nrm[p] = x;
-          x = nrm0[i];
-          nrm0[i] = nrm0[p];
-          nrm0[p] = x;
-          const int q = perm[i];
-          perm[i] = perm[p];
-          perm[p] = q;
-        }
-      }
-      __syncthreads();
-    }
-    if (warp == 0) {  // reflector from column i, rows i..m-1
-      double sig = 0.0;
-      for (int t = i + 1 + lane; t < m; t += 32) sig = fma(A[t * n + i], A[t * n + i], sig);
-      sig = warp_sum(sig);
-      const double alpha = A[i * n + i];
-      double tv = 0.0, beta = alpha, scal = 0.0;
-      if (sig > 0.0) {
-        householder_params(alpha, sig, beta, tv, scal);
-      }
-      for (int t = i + 1 + lane; t < m; t += 32) {
-        const double x = A[t * n + i] * scal;
-        A[t * n + i] = x;
-        vv[t] = x;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        A[i * n + i] = beta;
-        tau[i] = tv;
-        vv[i] = 1.0;
-      }
-    }
-    __syncthreads();
-    const double tv = tau[i];
-    for (int j = i + 1 + threadIdx.x; j < n; j += kSmallThreads) {
-      if (tv != 0.0) {
-        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
-        int t = i;
-        for (; t + 3 < m; t += 4) {
-          w0 = fma(vv[t], A[t * n + j], w0);
-          w1 = fma(vv[t + 1], A[(t + 1) * n + j], w1);
-          w2 = fma(vv[t + 2], A[(t + 2) * n + j], w2);
-          w3 = fma(vv[t + 3], A[(t + 3) * n + j], w3);
-        }
-        for (; t < m; ++t) w0 = fma(vv[t], A[t * n + j], w0);
-        const double w = ((w0 + w1) + (w2 + w3)) * tv;
-        for (t = i; t < m; ++t) A[t * n + j] = fma(-w, vv[t], A[t * n + j]);
-      }
-      if (a.pivot) {
-        const double rij = A[i * n + j];
-        double nn = nrm[j] - rij * rij;
-        // dgeqp3 safeguard: recompute once the downdate has cancelled too much
-        if (nn <= 1.4901161193847656e-08 * nrm0[j] || nn < 0.0) {
-          nn = 0.0;
-          for (int t = i + 1; t < m; ++t) nn = fma(A[t * n + j], A[t * n + j], nn);
-          nrm0[j] = nn;
-        }
-        nrm[j] = nn;
-      }
-    }
-    __syncthreads();
-  }
-  const int r = s_r;
-  if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
-  const int ldq = a.ldq > 0 ? a.ldq : r;
-  for (int idx = threadIdx.x; idx < r * n; idx += kSmallThreads) {
-    const int t = idx % r, j = idx / r;
-    const double x = t <= j ? A[t * n + j] : 0.0;
-    const int oj = perm[j];
-    if (a.trans_r)
-      a.R[oj + a.ldr * t] = x;
-    else
-      a.R[t + a.ldr * oj] = x;
-  }
-  // Q = H_0 ... H_{r-1} [I_r; 0]: thread l builds column l (m <= 64 rows)
-  for (int l = threadIdx.x; l < r; l += kSmallThreads) {
-    double q[64];
-#pragma unroll
-    for (int t = 0; t < 64; ++t) q[t] = (t == l) ? 1.0 : 0.0;
-    for (int j = l; j >= 0; --j) {
-      const double tj = tau[j];
-      if (tj == 0.0) continue;
-      double w0 = q[j], w1 = 0.0, w2 = 0.0, w3 = 0.0;
-      int t = j + 1;
-      for (; t + 3 < m; t += 4) {
-        w0 = fma(A[t * n + j], q[t], w0);
-        w1 = fma(A[(t + 1) * n + j], q[t + 1], w1);
-        w2 = fma(A[(t + 2) * n + j], q[t + 2], w2);
-        w3 = fma(A[(t + 3) * n + j], q[t + 3], w3);
-      }
-      for (; t < m; ++t) w0 = fma(A[t * n + j], q[t], w0);
-      const double w = ((w0 + w1) + (w2 + w3)) * tj;
-      q[j] -= w;
-      for (int t = j + 1; t < m; ++t) q[t] = fma(-w, A[t * n + j], q[t]);
-    }
-    for (int t = 0; t < m; ++t) {
-      if (a.trans_q)
-        a.Q[l + ldq * t] = q[t];
-      else
-        a.Q[t + ldq * l] = q[t];
-    }
-  }
+  qr_tpc_cta(a, sm);
 }
 
 // ------------------------------------------------------------------------------------------

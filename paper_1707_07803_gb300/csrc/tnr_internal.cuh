@@ -161,6 +161,12 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
 // Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
 int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
 
+// Exact right-to-left compression of a product MPO as one cooperative kernel (compress_coop.cu).
+// Y.R gets the ranks of the bonds it finished; *next_bond is the first bond left for the
+// host-driven sweep (0: none).
+int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
+                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond);
+
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
                     bool transpose);

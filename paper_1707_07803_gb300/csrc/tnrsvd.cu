@@ -24,59 +24,43 @@ namespace {
 // Per-site product, Section 5.2. Output core (R*S, Xo, Kx, R2*S2) with bonds r + R s.
 //   trans = 0: Y((r,s), i, c, (r',s')) = sum_j A(r,i,j,r') X(s,j,c,s')
 //   trans = 1: Y((r,s), j, c, (r',s')) = sum_i A(r,i,j,r') X(s,i,c,s')
-struct ContractDims {
-  int64_t R, I, J, R2;  // A core
-  int64_t S, Kx, S2;    // X core (row dim = J or I)
-  int trans;
-  int mixed;  // 1: operands rounded to BF16 hi + lo, products hi*hi + hi*lo + lo*hi summed in FP32
+// All sites of one product in a single launch (FP64): the threads of the grid stride over the
+// concatenated outputs of the sites; site b owns outputs [off[b], off[b+1]).
+struct ContractSite {
+  const double *A, *X;
+  double *Y;
+  unsigned R, I, J, R2, S, Kx, S2;
+};
+struct ContractBatch {
+  int n, trans;
+  unsigned off[TNR_MAX_SITES + 1];
+  ContractSite site[TNR_MAX_SITES];
 };
 
-__device__ __forceinline__ void split_bf16(double x, float &hi, float &lo) {
-  const __nv_bfloat16 h = __double2bfloat16(x);
-  hi = __bfloat162float(h);
-  lo = __bfloat162float(__double2bfloat16(x - (double)hi));
-}
-
-__global__ void k_contract(const double *__restrict__ A, const double *__restrict__ X, double *__restrict__ Y,
-                           ContractDims D) {
-  // 32-bit index decomposition (every core has fewer than 2^31 elements; 64-bit division is
-  // a long software sequence on the GPU)
-  const unsigned Xo = (unsigned)(D.trans ? D.J : D.I);
-  const unsigned Ny = (unsigned)(D.trans ? D.I : D.J);
-  const unsigned R = (unsigned)D.R, S = (unsigned)D.S, R2 = (unsigned)D.R2, Kx = (unsigned)D.Kx;
-  const unsigned RS = R * S;
-  const unsigned total = RS * Xo * Kx * (R2 * (unsigned)D.S2);
-  const unsigned as = D.trans ? R : R * (unsigned)D.I;
+__global__ void k_contract_sites(const __grid_constant__ ContractBatch B) {
+  const unsigned total = B.off[B.n];
   for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    unsigned t = idx;
+    int b = 0;
+    while (idx >= B.off[b + 1]) ++b;
+    const ContractSite &D = B.site[b];
+    unsigned t = idx - B.off[b];
+    const unsigned Xo = B.trans ? D.J : D.I, Ny = B.trans ? D.I : D.J;
+    const unsigned RS = D.R * D.S;
     const unsigned rs = t % RS;
     t /= RS;
     const unsigned xo = t % Xo;
     t /= Xo;
-    const unsigned c = t % Kx;
-    const unsigned rs2 = t / Kx;
-    const unsigned r = rs % R, s = rs / R;
-    const unsigned r2 = rs2 % R2, s2 = rs2 / R2;
-    // A(r, i, j, r2) at r + R(i + I(j + J r2)); X(s, y, c, s2) at s + S(y + Ny(c + Kx s2))
-    const double *xp = X + s + (size_t)S * (Ny * (c + (size_t)Kx * s2));
-    const double *ap = D.trans ? A + r + (size_t)R * (D.I * (xo + (size_t)D.J * r2))
-                               : A + r + (size_t)R * (xo + D.I * ((size_t)D.J * r2));
-    if (!D.mixed) {
-      double acc = 0.0;
-      for (unsigned y = 0; y < Ny; ++y) acc = fma(ap[(size_t)as * y], xp[(size_t)S * y], acc);
-      Y[idx] = acc;
-    } else {
-      float acc = 0.0f;
-      for (unsigned y = 0; y < Ny; ++y) {
-        float ah, al, xh, xl;
-        split_bf16(ap[(size_t)as * y], ah, al);
-        split_bf16(xp[(size_t)S * y], xh, xl);
-        acc = fmaf(ah, xh, acc);
-        acc = fmaf(ah, xl, acc);
-        acc = fmaf(al, xh, acc);
-      }
-      Y[idx] = (double)acc;
-    }
+    const unsigned c = t % D.Kx;
+    const unsigned rs2 = t / D.Kx;
+    const unsigned r = rs % D.R, s = rs / D.R;
+    const unsigned r2 = rs2 % D.R2, s2 = rs2 / D.R2;
+    const double *xp = D.X + s + (size_t)D.S * (Ny * (c + (size_t)D.Kx * s2));
+    const double *ap = B.trans ? D.A + r + (size_t)D.R * (D.I * (xo + (size_t)D.J * r2))
+                               : D.A + r + (size_t)D.R * (xo + D.I * ((size_t)D.J * r2));
+    const unsigned as = B.trans ? D.R : D.R * D.I;
+    double acc = 0.0;
+    for (unsigned y = 0; y < Ny; ++y) acc = fma(ap[(size_t)as * y], xp[(size_t)D.S * y], acc);
+    D.Y[idx - B.off[b]] = acc;
   }
 }
 
@@ -207,6 +191,9 @@ struct Bufs {
   void *jac = nullptr;      // Jacobi scratch
   double *norm2 = nullptr;  // device scalar
   int64_t *rdev = nullptr;  // device rank(s): one per bond for the fused sweeps
+  unsigned *bar = nullptr;  // grid-barrier state of the cooperative compression
+  int *ctl = nullptr;       // its control word
+  int64_t cap = 0;          // doubles in tmp, Mq and US
 };
 
 struct Limits {
@@ -231,6 +218,9 @@ void carve(Arena &ar, const Limits &L, Bufs &b) {
   b.jac = ar.take<char>(std::max<size_t>(jacobi_scratch(L.maxsq), 256));
   b.norm2 = ar.take<double>(1);
   b.rdev = ar.take<int64_t>(TNR_MAX_SITES + 1);
+  b.bar = ar.take<unsigned>(4);
+  b.ctl = ar.take<int>(4);
+  b.cap = L.maxcore;
 }
 
 int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
@@ -250,9 +240,9 @@ int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
 // the rounding that follows returns the same result to rounding accuracy, on bonds of the
 // numerical rank instead of R_k S_k. Every compressed core Q_k has orthonormal rows, so when all
 // bonds were compressed (*all_bonds) cores 1..d-1 leave right-orthonormal.
-int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds) {
+int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds, int start) {
   *all_bonds = true;
-  for (int k = Y.d - 1; k >= 1; --k) {
+  for (int k = start; k >= 1; --k) {
     const int64_t t = Y.R[k], w = Y.I[k] * Y.J[k] * Y.R[k + 1];
     int64_t r = 0;
     if (qr_small_fits(w, t)) {
@@ -282,6 +272,14 @@ int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds
     Y.R[k] = r;
   }
   return TNR_OK;
+}
+
+// The compression: the cooperative device-side sweep for every bond it can take, the host-driven
+// sweep for the rest.
+int compress(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds) {
+  int next = Y.d - 1;
+  TNR_TRY(compress_device(s, Y, cut, b.Rbuf, b.tmp, b.Mq, b.cap, b.bar, b.ctl, b.rdev, &next));
+  return compress_rl(s, Y, b, cut, all_bonds, next);
 }
 
 // Compression cutoff relative to ||M_k||_F: the rounding level of the product that made Y.
@@ -413,7 +411,7 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
                        bool mixed_product = false) {
   bool right_orth = false;
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Y, b, compress_cut(tol, mixed_product), &right_orth));
+  if (tol > 0.0) TNR_TRY(compress(s, Y, b, compress_cut(tol, mixed_product), &right_orth));
   TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b));
   const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
   const int64_t m = I1 * t;
@@ -431,7 +429,7 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
   bool right_orth = false;
-  if (tol > 0.0) TNR_TRY(compress_rl(s, Z, b, compress_cut(tol, false), &right_orth));
+  if (tol > 0.0) TNR_TRY(compress(s, Z, b, compress_cut(tol, false), &right_orth));
   TNR_TRY(round_sweeps(s, Z, tol, max_rank, right_orth, b));
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
   const int64_t m = J1 * t;
@@ -447,39 +445,54 @@ int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs 
   return TNR_OK;
 }
 
+// Y = op(A) X (Section 5.2). The dense site-1 product goes to the tensor cores in mixed mode; every
+// other site runs in FP64 in one launch for the whole product (an FP32 or BF16 product of FP64
+// operands on CUDA cores would spend more FP64-pipe slots on conversions than the FP64 FMAs).
 int contract_impl(cudaStream_t s, const tnr_mpo &A, int trans, const tnr_mpo &X, tnr_mpo &Y, bool mixed = false) {
   Y.d = A.d;
   Y.R[0] = 1;
+  ContractBatch B;
+  B.n = 0;
+  B.trans = trans;
+  B.off[0] = 0;
+  double work = 0.0;
   for (int k = 0; k < A.d; ++k) {
-    ContractDims D;
-    D.R = A.R[k];
-    D.I = A.I[k];
-    D.J = A.J[k];
-    D.R2 = A.R[k + 1];
-    D.S = X.R[k];
-    D.Kx = X.J[k];
-    D.S2 = X.R[k + 1];
-    D.trans = trans;
-    D.mixed = mixed ? 1 : 0;
-    const int64_t Xo = trans ? A.J[k] : A.I[k];
-    const int64_t Ny = trans ? A.I[k] : A.J[k];
+    const int64_t R = A.R[k], I = A.I[k], J = A.J[k], R2 = A.R[k + 1];
+    const int64_t S = X.R[k], Kx = X.J[k], S2 = X.R[k + 1];
+    const int64_t Xo = trans ? J : I;
+    const int64_t Ny = trans ? I : J;
     if (X.I[k] != Ny) return TNR_EINVAL;
-    const int64_t total = D.R * D.S * Xo * D.Kx * D.R2 * D.S2;
+    const int64_t total = R * S * Xo * Kx * R2 * S2;
     if (total > Y.cap[k]) return TNR_ENOMEM;
     Y.I[k] = Xo;
-    Y.J[k] = D.Kx;
-    Y.R[k + 1] = D.R2 * D.S2;
-    if (mixed && D.R == 1 && D.S == 1 && Ny >= 16) {
+    Y.J[k] = Kx;
+    Y.R[k + 1] = R2 * S2;
+    if (mixed && R == 1 && S == 1 && Ny >= 16) {
       // dense site product on the tensor cores (BF16 x3 split, FP32 accumulation)
-      TNR_TRY(contract_site1_tc(s, A.core[k], D.I, D.J, D.R2, X.core[k], D.Kx, D.S2, trans, Y.core[k], true));
+      TNR_TRY(contract_site1_tc(s, A.core[k], I, J, R2, X.core[k], Kx, S2, trans, Y.core[k], true));
       continue;
     }
-    stats_work(K_CONTRACT, 2.0 * (double)total * (double)Ny);
-    LaunchScope ls(K_CONTRACT, s);
-    k_contract<<<grid_for(total), 256, 0, s>>>(A.core[k], X.core[k], Y.core[k], D);
-    TNR_CK(cudaGetLastError());
+    if ((double)B.off[B.n] + (double)total >= 4294967295.0) return TNR_ERANGE;
+    ContractSite &D = B.site[B.n];
+    D.A = A.core[k];
+    D.X = X.core[k];
+    D.Y = Y.core[k];
+    D.R = (unsigned)R;
+    D.I = (unsigned)I;
+    D.J = (unsigned)J;
+    D.R2 = (unsigned)R2;
+    D.S = (unsigned)S;
+    D.Kx = (unsigned)Kx;
+    D.S2 = (unsigned)S2;
+    B.off[B.n + 1] = B.off[B.n] + (unsigned)total;
+    ++B.n;
+    work += 2.0 * (double)total * (double)Ny;
   }
-  return TNR_OK;
+  if (B.n == 0 || B.off[B.n] == 0) return TNR_OK;
+  stats_work(K_CONTRACT, work);
+  LaunchScope ls(K_CONTRACT, s);
+  k_contract_sites<<<grid_for(B.off[B.n]), 256, 0, s>>>(B);
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
 // Structural bound of bond b (1..d-1) of a (prod dims) x K matrix MPO with K on site 1.

@@ -70,4 +70,15 @@ __device__ __forceinline__ void householder_params(double alpha, double sig, dou
   scal = sgn * q * pow2(-e);
 }
 
+// 1 / sqrt(x) for finite x > 0 to FP64 accuracy without the FP64 square-root / division
+// sequences: exact power-of-two range reduction, FP32 seed, two Newton steps (24 -> 48 -> 53 bits).
+__device__ __forceinline__ double rsqrt_f64(double x) {
+  const int k = ((int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023) >> 1;  // floor(e / 2)
+  const double xs = x * pow2(-2 * k);                                          // in [1, 4)
+  double r = (double)rsqrtf((float)xs);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  return r * pow2(-k);
+}
+
 }  // namespace tnr

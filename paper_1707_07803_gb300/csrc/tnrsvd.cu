@@ -12,6 +12,7 @@
 
 #include <cuda_bf16.h>
 
+#include "cholqr.cuh"
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -110,6 +111,16 @@ __global__ void k_site1_perm(const double *__restrict__ src, double *__restrict_
       dst[mi] = src[idx];
     else
       dst[idx] = src[mi];
+  }
+}
+
+// Site-1 core (1, I1, K, t) -> row-major A1^T ((I1 t) x K): element (i, c, r) -> c + K (i + I1 r).
+__global__ void k_site1_rowmajor(const double *__restrict__ src, double *__restrict__ dst, int64_t I1, int64_t K,
+                                 int64_t t) {
+  const unsigned total = (unsigned)(I1 * K * t), kk = (unsigned)K, uI1 = (unsigned)I1;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const unsigned i = idx % uI1, c = (idx / uI1) % kk, r = idx / (uI1 * kk);
+    dst[c + kk * (i + uI1 * r)] = src[idx];
   }
 }
 
@@ -406,6 +417,36 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
   return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
+// Thin QR of the site-1 matrix A1^T = Q~ R~ ((I1 t) x K, Alg. 5.2/5.3): Q~ (column-major) into
+// b.Mq, R~ into b.Rm. For K <= 32: CholeskyQR2 (two passes of Gram, K-pivot Cholesky and a
+// warp-parallel triangular solve), checked on the device; when a Cholesky breaks down or the
+// second pass is not near the identity (cond(A1) beyond ~1e8) it falls back to the multi-CTA
+// Householder QR on the same input.
+int site1_qr(cudaStream_t s, const double *core0, int64_t I1, int64_t K, int64_t t, Bufs &b) {
+  const int64_t m = I1 * t;
+  if (K <= 32 && m >= K && m * K <= b.cap) {
+    {
+      LaunchScope ls(K_MISC, s);
+      k_site1_rowmajor<<<grid_for(m * K), 256, 0, s>>>(core0, b.US, I1, K, t);
+    }
+    TNR_CK(cudaGetLastError());
+    int *flag = b.ctl + 1;
+    TNR_CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    TNR_TRY(cholqr_pass_small(s, b.US, m, (int)K, b.G, b.Rm, b.Sv, flag, K_QR, false));
+    TNR_TRY(cholqr_pass_small(s, b.US, m, (int)K, b.G, b.Vr, b.Sv, flag, K_QR, true));
+    int hflag = 0;
+    TNR_CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TNR_TRY(read_status(s));
+    if (!hflag) {
+      TNR_TRY(gemm_f64(s, false, false, K, K, K, 1.0, b.Vr, K, 0, b.Rm, K, 0, 0.0, b.G, K, 0));  // R2 R1
+      TNR_TRY(copy_matrix_f64(s, b.G, K, b.Rm, K, K, K, false));
+      return copy_matrix_f64(s, b.US, K, b.Mq, m, m, K, true);  // row-major -> column-major
+    }
+  }
+  TNR_TRY(site1_perm(s, core0, b.Mq, I1, K, t, K, 0));
+  return thin_qr(s, b.Mq, m, K, b.Rm, K, b);
+}
+
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
@@ -416,8 +457,7 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
   const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
   const int64_t m = I1 * t;
   if (m < K) return TNR_EINVAL;
-  TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
-  TNR_TRY(thin_qr(s, b.Mq, m, K, b.Rm, K, b));  // A1^T = Q~ R~
+  TNR_TRY(site1_qr(s, Y.core[0], I1, K, t, b));  // A1^T = Q~ R~
   if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
   TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
   return TNR_OK;
@@ -435,8 +475,7 @@ int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs 
   const int64_t m = J1 * t;
   if (m < K) return TNR_EINVAL;
   if (J1 * kout * t > v1cap) return TNR_ENOMEM;
-  TNR_TRY(site1_perm(s, Z.core[0], b.Mq, J1, K, t, K, 0));  // M^T ((J1 t) x K)
-  TNR_TRY(thin_qr(s, b.Mq, m, K, b.Rm, K, b));  // M^T = Q~ R~
+  TNR_TRY(site1_qr(s, Z.core[0], J1, K, t, b));  // M^T ((J1 t) x K) = Q~ R~
   TNR_TRY(copy_matrix_f64(s, b.Rm, K, Wout, K, K, K, true));  // R~^T
   TNR_TRY(jacobi_svd_f64(s, Wout, K, K, Sout, b.Vr, K, b.jac));  // R~^T = W S Zr^T
   // V = Q~ Zr ((J1 t) x K), then V^(1) columns < kout

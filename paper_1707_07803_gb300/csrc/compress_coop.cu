@@ -105,21 +105,36 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     grid_barrier(a.bar, a.status);
     // data written by other CTAs is read through L2 (__ldcg), never from a possibly stale L1 line
     const int r = (int)__ldcg(a.R_out + k);
-    // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r)
+    // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r); L staged in shared memory (the
+    // QR's buffer is free now), the core streamed from global memory
     const int rows = a.R[k - 1] * a.phys[k - 1];
     const double *C = a.core[k - 1];
     double *out = a.buf[k & 1];
+    double *Ls = sm;
+    const bool staged = (int64_t)t * r * (int64_t)sizeof(double) <= a.qr_cap;
+    if (staged)
+      for (int x = threadIdx.x; x < t * r; x += blockDim.x) Ls[x] = __ldcg(a.L + x);
+    __syncthreads();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)rows * r;
          x += (int64_t)gridDim.x * blockDim.x) {
       const int i = (int)(x % rows), c = (int)(x / rows);
-      const double *l = a.L + (int64_t)t * c;
       double s0 = 0.0, s1 = 0.0;
       int j = 0;
-      for (; j + 1 < t; j += 2) {
-        s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
-        s1 = fma(C[i + (int64_t)rows * (j + 1)], __ldcg(l + j + 1), s1);
+      if (staged) {
+        const double *l = Ls + t * c;
+        for (; j + 1 < t; j += 2) {
+          s0 = fma(C[i + (int64_t)rows * j], l[j], s0);
+          s1 = fma(C[i + (int64_t)rows * (j + 1)], l[j + 1], s1);
+        }
+        if (j < t) s0 = fma(C[i + (int64_t)rows * j], l[j], s0);
+      } else {
+        const double *l = a.L + (int64_t)t * c;
+        for (; j + 1 < t; j += 2) {
+          s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
+          s1 = fma(C[i + (int64_t)rows * (j + 1)], __ldcg(l + j + 1), s1);
+        }
+        if (j < t) s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
       }
-      if (j < t) s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
       out[x] = s0 + s1;
     }
     grid_barrier(a.bar, a.status);

@@ -42,6 +42,7 @@ static __device__ __noinline__ void qr_tpc_cta(const QrSmallArgs &a, double *sm)
   int *perm = reinterpret_cast<int *>(vv + m);  // n
   __shared__ double s_red[32];
   __shared__ int s_idx[32];
+  __shared__ long long s_key[32];
   __shared__ int s_r;
   __shared__ double s_cut2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,15 +74,19 @@ static __device__ __noinline__ void qr_tpc_cta(const QrSmallArgs &a, double *sm)
   __syncthreads();
   for (int i = 0; i < nref; ++i) {
     if (a.pivot) {
-      double bv = -1.0;
+      // argmax of the remaining column norms; the norms are >= 0, so their bit patterns order
+      // like the values and the comparisons stay on the integer pipe (ties: lowest index)
+      long long bv = -1;
       int bi = (int)i;
-      for (int j = i + threadIdx.x; j < n; j += kSmallThreads)
-        if (nrm[j] > bv) {
-          bv = nrm[j];
+      for (int j = i + threadIdx.x; j < n; j += kSmallThreads) {
+        const long long v = __double_as_longlong(nrm[j]);
+        if (v > bv) {
+          bv = v;
           bi = (int)j;
         }
+      }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) {
           bv = ov;
@@ -89,20 +94,20 @@ static __device__ __noinline__ void qr_tpc_cta(const QrSmallArgs &a, double *sm)
         }
       }
       if (lane == 0) {
-        s_red[warp] = bv;
+        s_key[warp] = bv;
         s_idx[warp] = bi;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        double b = s_red[0];
+        long long b = s_key[0];
         int bj = s_idx[0];
         for (int w = 1; w < NW; ++w)
-          if (s_red[w] > b || (s_red[w] == b && s_idx[w] < bj)) {
-            b = s_red[w];
+          if (s_key[w] > b || (s_key[w] == b && s_idx[w] < bj)) {
+            b = s_key[w];
             bj = s_idx[w];
           }
         s_idx[0] = bj;
-        if (i > 0 && b <= s_cut2) s_r = (int)i;
+        if (i > 0 && __longlong_as_double(b) <= s_cut2) s_r = (int)i;
       }
       __syncthreads();
       if (s_r == (int)i) break;
@@ -190,32 +195,27 @@ static __device__ __noinline__ void qr_tpc_cta(const QrSmallArgs &a, double *sm)
     else
       a.R[t + a.ldr * oj] = x;
   }
-  // Q = H_0 ... H_{r-1} [I_r; 0]: thread l builds column l (m <= 64 rows)
-  for (int l = threadIdx.x; l < r; l += kSmallThreads) {
-    double q[64];
-#pragma unroll
-    for (int t = 0; t < 64; ++t) q[t] = (t == l) ? 1.0 : 0.0;
+  // Q = H_0 ... H_{r-1} [I_r; 0]: warp w builds columns l = w, w + NW, ... with lanes over the
+  // rows (two rows per lane, m <= 64); column l needs reflectors l .. 0 (backward accumulation)
+  for (int l = warp; l < r; l += NW) {
+    const int t0 = lane, t1 = lane + 32;
+    double q0 = t0 == l ? 1.0 : 0.0, q1 = t1 == l ? 1.0 : 0.0;
     for (int j = l; j >= 0; --j) {
       const double tj = tau[j];
       if (tj == 0.0) continue;
-      double w0 = q[j], w1 = 0.0, w2 = 0.0, w3 = 0.0;
-      int t = j + 1;
-      for (; t + 3 < m; t += 4) {
-        w0 = fma(A[t * n + j], q[t], w0);
-        w1 = fma(A[(t + 1) * n + j], q[t + 1], w1);
-        w2 = fma(A[(t + 2) * n + j], q[t + 2], w2);
-        w3 = fma(A[(t + 3) * n + j], q[t + 3], w3);
-      }
-      for (; t < m; ++t) w0 = fma(A[t * n + j], q[t], w0);
-      const double w = ((w0 + w1) + (w2 + w3)) * tj;
-      q[j] -= w;
-      for (int t = j + 1; t < m; ++t) q[t] = fma(-w, A[t * n + j], q[t]);
+      // v_j: 1 at row j, A(t, j) below, 0 above
+      const double v0 = t0 < j || t0 >= m ? 0.0 : (t0 == j ? 1.0 : A[t0 * n + j]);
+      const double v1 = t1 < j || t1 >= m ? 0.0 : (t1 == j ? 1.0 : A[t1 * n + j]);
+      const double w = dwarp_sum(fma(v0, q0, v1 * q1)) * tj;
+      q0 = fma(-w, v0, q0);
+      q1 = fma(-w, v1, q1);
     }
-    for (int t = 0; t < m; ++t) {
-      if (a.trans_q)
-        a.Q[l + ldq * t] = q[t];
-      else
-        a.Q[t + ldq * l] = q[t];
+    if (a.trans_q) {
+      if (t0 < m) a.Q[l + ldq * t0] = q0;
+      if (t1 < m) a.Q[l + ldq * t1] = q1;
+    } else {
+      if (t0 < m) a.Q[t0 + ldq * l] = q0;
+      if (t1 < m) a.Q[t1 + ldq * l] = q1;
     }
   }
 }

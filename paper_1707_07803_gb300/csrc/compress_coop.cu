@@ -115,27 +115,28 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     if (staged)
       for (int x = threadIdx.x; x < t * r; x += blockDim.x) Ls[x] = __ldcg(a.L + x);
     __syncthreads();
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)rows * r;
-         x += (int64_t)gridDim.x * blockDim.x) {
-      const int i = (int)(x % rows), c = (int)(x / rows);
-      double s0 = 0.0, s1 = 0.0;
-      int j = 0;
-      if (staged) {
-        const double *l = Ls + t * c;
-        for (; j + 1 < t; j += 2) {
-          s0 = fma(C[i + (int64_t)rows * j], l[j], s0);
-          s1 = fma(C[i + (int64_t)rows * (j + 1)], l[j + 1], s1);
+    // four lanes per output, each summing every fourth term, combined by shuffles (fixed order:
+    // deterministic); eight outputs per warp, consecutive rows (coalesced core reads)
+    const int lane = threadIdx.x & 31, part = lane & 3;
+    const int64_t nout = (int64_t)rows * r;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 8 < nout; g += warps) {
+      const int64_t x = g * 8 + (lane >> 2);
+      double acc = 0.0;
+      if (x < nout) {
+        const int i = (int)(x % rows), c = (int)(x / rows);
+        const double *Ci = C + i;
+        if (staged) {
+          const double *l = Ls + t * c;
+          for (int j = part; j < t; j += 4) acc = fma(Ci[(int64_t)rows * j], l[j], acc);
+        } else {
+          const double *l = a.L + (int64_t)t * c;
+          for (int j = part; j < t; j += 4) acc = fma(Ci[(int64_t)rows * j], __ldcg(l + j), acc);
         }
-        if (j < t) s0 = fma(C[i + (int64_t)rows * j], l[j], s0);
-      } else {
-        const double *l = a.L + (int64_t)t * c;
-        for (; j + 1 < t; j += 2) {
-          s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
-          s1 = fma(C[i + (int64_t)rows * (j + 1)], __ldcg(l + j + 1), s1);
-        }
-        if (j < t) s0 = fma(C[i + (int64_t)rows * j], __ldcg(l + j), s0);
       }
-      out[x] = s0 + s1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (x < nout && part == 0) out[x] = acc;
     }
     grid_barrier(a.bar, a.status);
     cur = out;
@@ -192,7 +193,7 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
   TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)qr_cap));
   TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)qr_cap));
   if (per_sm < 1) return TNR_OK;
-  const int blocks = std::min(32, sms * per_sm);
+  const int blocks = std::min(64, sms * per_sm);
   TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
   {
     LaunchScope ls(K_QR_PIV, s);

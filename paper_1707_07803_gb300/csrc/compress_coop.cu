@@ -207,6 +207,18 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
   TNR_CK(cudaMemcpyAsync(&hctl, ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
   TNR_TRY(read_status(s));
   *next_bond = hctl;
+  // algorithmic work of the bonds done: r reflectors on w x t plus the explicit w x r Q, and the
+  // absorb 2 rows t r
+  double work = 0.0;
+  int64_t rk1 = 1;
+  for (int k = d - 1; k > hctl; --k) {
+    const double t = (double)Y.R[k], w = (double)(Y.I[k] * Y.J[k] * rk1), r = (double)h[k];
+    const double rows = (double)(Y.R[k - 1] * Y.I[k - 1] * Y.J[k - 1]);
+    work += 4 * w * t * r - 2 * (w + t) * r * r + 4 * r * r * r / 3 + 2 * w * r * r - 2 * r * r * r / 3;
+    work += 2 * rows * t * r;
+    rk1 = h[k];
+  }
+  stats_work(K_QR_PIV, work);
   for (int k = hctl + 1; k < d; ++k) Y.R[k] = h[k];
   return TNR_OK;
 }

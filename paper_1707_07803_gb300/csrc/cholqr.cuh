@@ -61,20 +61,30 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rm(const double *__restri
 }
 
 // Cholesky G = R^T R of a K x K matrix (K <= 32, column-major) in one CTA of 1024 threads, one
-// thread per element: per pivot one reciprocal square root (FP32 seed + Newton), one scaling of
-// row j and one FMA per trailing element. Writes R (upper, zeros below) and rdiag = 1 / diag(R);
-// on a pivot that is not positive and finite it sets *flag = 1 (R is then not usable).
+// thread per element, in the square-root-free form G = U^T D U (U unit upper): per pivot one
+// reciprocal of d_j (FP32 seed + Newton, on one thread) and one fused trailing update
+// a_il -= a_ji a_jl / d_j; R = D^{1/2} U at the end, all rows at once. Writes R (upper, zeros
+// below) and rdiag = 1 / diag(R); on a pivot that is not positive and finite it sets *flag = 1.
 // near_identity (second CholeskyQR pass): G must be within 0.5 / K of the identity entrywise,
 // i.e. the first pass left a well-conditioned factor (||G - I||_2 < 1/2); otherwise *flag = 1.
 // This is the regime (cond(Y) below ~1e8) in which CholeskyQR2 is orthogonal to rounding level.
+__device__ __forceinline__ double rcp_f64(double x) {  // 1 / x for finite x > 0
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+  const double xs = x * pow2(-e);  // in [1, 2)
+  double q = (double)(1.0f / (float)xs);
+  q = q * fma(-xs, q, 2.0);
+  q = q * fma(-xs, q, 2.0);
+  return q * pow2(-e);
+}
+
 __global__ void __launch_bounds__(1024) k_chol_small(const double *__restrict__ G, int K, double *Rout, double *rdiag,
                                                      int *flag, int near_identity) {
   __shared__ double a[32 * 32];
-  __shared__ double s_inv;
+  __shared__ double s_dinv[32];
   __shared__ int s_bad;
   const int tid = threadIdx.x;
   const bool own = tid < K * K;
-  const int i = tid % K, l = tid / K;
+  const int i = tid % K, l = tid / K;  // warp l holds column l
   if (own) a[tid] = G[tid];
   if (tid == 0) s_bad = 0;
   __syncthreads();
@@ -86,25 +96,28 @@ __global__ void __launch_bounds__(1024) k_chol_small(const double *__restrict__ 
   for (int j = 0; j < K && !s_bad; ++j) {
     if (tid == 0) {
       const double dj = a[j + K * j];
-      if (!(dj > 0.0) || !isfinite(dj)) {
+      if (!(dj > 0.0) || !isfinite(dj))
         s_bad = 1;
-        s_inv = 0.0;
-      } else {
-        const double ri = rsqrt_f64(dj);
-        a[j + K * j] = dj * ri;  // sqrt(dj)
-        s_inv = ri;
-        rdiag[j] = ri;
-      }
+      else
+        s_dinv[j] = rcp_f64(dj);
     }
     __syncthreads();
     if (s_bad) break;
-    if (own && i == j && l > j) a[tid] *= s_inv;  // row j of R
-    __syncthreads();
-    if (own && i > j && l >= i) a[tid] = fma(-a[j + K * i], a[j + K * l], a[tid]);
+    // a_il -= a_ji a_jl / d_j for j < i <= l (upper triangle; row j stays unscaled)
+    if (own && l > j && i > j && i <= l) a[tid] = fma(-a[j + K * i] * s_dinv[j], a[j + K * l], a[tid]);
     __syncthreads();
   }
-  if (s_bad && tid == 0) *flag = 1;
-  if (own) Rout[tid] = i <= l ? a[tid] : 0.0;
+  if (s_bad) {
+    if (tid == 0) *flag = 1;
+    return;
+  }
+  // R(j, l) = a_jl / sqrt(d_j): rdiag[j] = 1 / sqrt(d_j)
+  if (tid < K) rdiag[tid] = rsqrt_f64(a[tid + K * tid]);
+  __syncthreads();
+  if (own) {
+    const double rj = rsqrt_f64(a[i + K * i]);
+    Rout[tid] = i <= l ? a[tid] * rj : 0.0;
+  }
 }
 
 // Y (n x K, row-major, K <= 32) <- Y R^{-1} for R upper: one warp per row, lane c owns column c;

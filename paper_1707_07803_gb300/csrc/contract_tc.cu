@@ -133,26 +133,63 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
   const int64_t nkb = (a.K + kTcBK - 1) / kTcBK;
   for (int64_t kb = 0; kb < nkb; ++kb) {
     const int64_t k0 = kb * kTcBK;
-    // stage A (128 x BK) and B (BN x BK), FP64 -> BF16 (hi, lo)
-    for (int idx = threadIdx.x; idx < kTcM * kTcBK; idx += kTcThreads) {
-      const int r = a.a_ks == 1 ? idx / kTcBK : idx % kTcM;
-      const int k = a.a_ks == 1 ? idx % kTcBK : idx / kTcM;
-      const int64_t gk = k0 + k, base = s_arow[r];
-      double x = 0.0;
-      if (base >= 0 && gk < a.K) x = a.A[base + gk * a.a_ks];
-      const __nv_bfloat16 hi = __double2bfloat16(x);
-      *reinterpret_cast<__nv_bfloat16 *>(sA[0] + kmajor_off(r, k)) = hi;
-      if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sA[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
-    }
-    for (int idx = threadIdx.x; idx < a.BN * kTcBK; idx += kTcThreads) {
-      const int r = a.b_ks == 1 ? idx / kTcBK : idx % a.BN;
-      const int k = a.b_ks == 1 ? idx % kTcBK : idx / a.BN;
-      const int64_t gk = k0 + k, base = s_bcol[r];
-      double x = 0.0;
-      if (base >= 0 && gk < a.K) x = a.B[base + gk * a.b_ks];
-      const __nv_bfloat16 hi = __double2bfloat16(x);
-      *reinterpret_cast<__nv_bfloat16 *>(sB[0] + kmajor_off(r, k)) = hi;
-      if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sB[1] + kmajor_off(r, k)) = __double2bfloat16(x - (double)__bfloat162float(hi));
+    // stage A (128 x BK) and B (BN x BK), FP64 -> BF16 (hi, lo). One FP64-pipe conversion per
+    // element (double -> float); the hi/lo split is done in FP32 (hi + lo carries 16 significant
+    // bits, far inside FP32's 24). Loads are issued four at a time before any conversion.
+    {
+      constexpr int U = 4;
+      const int na = kTcM * kTcBK;
+      for (int base_idx = threadIdx.x; base_idx < na; base_idx += kTcThreads * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base_idx + u * kTcThreads;
+          x[u] = 0.0;
+          if (idx < na) {
+            const int r = a.a_ks == 1 ? idx / kTcBK : idx % kTcM;
+            const int k = a.a_ks == 1 ? idx % kTcBK : idx / kTcM;
+            const int64_t gk = k0 + k, base = s_arow[r];
+            if (base >= 0 && gk < a.K) x[u] = a.A[base + gk * a.a_ks];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base_idx + u * kTcThreads;
+          if (idx >= na) continue;
+          const int r = a.a_ks == 1 ? idx / kTcBK : idx % kTcM;
+          const int k = a.a_ks == 1 ? idx % kTcBK : idx / kTcM;
+          const float f = (float)x[u];
+          const __nv_bfloat16 hi = __float2bfloat16(f);
+          *reinterpret_cast<__nv_bfloat16 *>(sA[0] + kmajor_off(r, k)) = hi;
+          if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sA[1] + kmajor_off(r, k)) = __float2bfloat16(f - __bfloat162float(hi));
+        }
+      }
+      const int nb = a.BN * kTcBK;
+      for (int base_idx = threadIdx.x; base_idx < nb; base_idx += kTcThreads * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base_idx + u * kTcThreads;
+          x[u] = 0.0;
+          if (idx < nb) {
+            const int r = a.b_ks == 1 ? idx / kTcBK : idx % a.BN;
+            const int k = a.b_ks == 1 ? idx % kTcBK : idx / a.BN;
+            const int64_t gk = k0 + k, base = s_bcol[r];
+            if (base >= 0 && gk < a.K) x[u] = a.B[base + gk * a.b_ks];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base_idx + u * kTcThreads;
+          if (idx >= nb) continue;
+          const int r = a.b_ks == 1 ? idx / kTcBK : idx % a.BN;
+          const int k = a.b_ks == 1 ? idx % kTcBK : idx / a.BN;
+          const float f = (float)x[u];
+          const __nv_bfloat16 hi = __float2bfloat16(f);
+          *reinterpret_cast<__nv_bfloat16 *>(sB[0] + kmajor_off(r, k)) = hi;
+          if (a.split) *reinterpret_cast<__nv_bfloat16 *>(sB[1] + kmajor_off(r, k)) = __float2bfloat16(f - __bfloat162float(hi));
+        }
+      }
     }
     // make generic-proxy smem writes visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -204,6 +204,41 @@ typedef struct {
 int tnr_solve_batched(int32_t n, tnr_problem *probs, int32_t workers, void *ws, size_t ws_stride, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Persistent batched TNrSVD: the same n independent problems (tnr_problem above, the same
+ * steps as tnr_solve: Alg. 5.4 with Algs. 5.2/5.3, merge of Section 6.3, Omega of Lemma 5.1,
+ * rounding of Section 5.4) solved by ONE kernel launch in which each CTA runs the whole
+ * pipeline of one problem and takes the next problem from a device work queue. Ranks stay on
+ * the device; nothing goes back to the host until the batch is done, so the launch can be
+ * captured in a CUDA graph and replayed.
+ *   tnr_batch_workspace: bytes of device workspace for the batch (descriptors and every
+ *     problem's scratch at its structural rank bounds).
+ *   tnr_batch_create: validates and plans every problem (errors as tnr_solve; nothing is
+ *     launched for an invalid batch), uploads the descriptors into ws (synchronises `stream`),
+ *     and chooses the launch configuration. flags: bit 0 = autotune the CTAs per SM for this
+ *     shape bucket by timing the batch (once per process and bucket; the batch is solved
+ *     while tuning), bit 1 = capture the launch in a CUDA graph, bits 4-7 = CTAs per SM set by
+ *     the caller (1..15; overrides bit 0; fewer are used if they do not fit). `probs`, the MPOs and output
+ *     buffers they point to, and ws must stay valid until tnr_batch_destroy. *handle receives
+ *     an opaque host handle.
+ *   tnr_batch_launch: queues the batch on `stream` (a graph launch when captured). Reads A,
+ *     writes every U, S, V; it may be repeated (each launch solves the batch again).
+ *   tnr_batch_collect: synchronises `stream`, writes each problem's status and the shapes and
+ *     ranks of its U and V (as tnr_solve does); returns the first non-zero status in queue
+ *     order, TNR_OK when all succeeded.
+ *   tnr_batch_config: the chosen grid, CTAs per SM and dynamic shared memory per CTA.
+ *   tnr_batch_destroy: frees the handle (not ws).
+ * Device-side errors are per problem (TNR_ENOMEM: an output capacity too small; TNR_ENONFINITE;
+ * TNR_ERANGE: a work area beyond the planned bound).
+ * ------------------------------------------------------------------------------------- */
+int tnr_batch_workspace(int32_t n, const tnr_problem *probs, size_t *bytes);
+int tnr_batch_create(int32_t n, tnr_problem *probs, int32_t flags, void *ws, size_t ws_bytes, void *stream,
+                     void **handle);
+int tnr_batch_launch(void *handle, void *stream);
+int tnr_batch_collect(void *handle, void *stream);
+int tnr_batch_config(void *handle, int32_t *grid, int32_t *ctas_per_sm, int64_t *smem_bytes);
+int tnr_batch_destroy(void *handle);
+
+/* ---------------------------------------------------------------------------------------
  * TNrSVD of a sparse matrix given in the block form of Alg. 4.1 (R, X, digits as produced by
  * tnr_sparse_fill; any block order). The MPO of Alg. 4.1 has rank R
  * at every bond (Lemma 4.2), so the products of Section 5.2 are applied straight from the

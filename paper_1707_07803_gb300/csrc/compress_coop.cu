@@ -63,10 +63,6 @@ __device__ void grid_barrier(unsigned *bar, int *status) {
   __syncthreads();
 }
 
-__host__ __device__ inline int64_t qr_tpc_bytes(int64_t m, int64_t n) {
-  return (int64_t)sizeof(double) * (m * n + 2 * n + (m < n ? m : n) + m) + (int64_t)sizeof(int) * n;
-}
-
 __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   extern __shared__ double sm[];
   const int d = a.d;

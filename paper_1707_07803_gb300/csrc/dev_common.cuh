@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace tnr {
 
 __device__ __forceinline__ double dwarp_sum(double v) {
@@ -79,6 +81,23 @@ __device__ __forceinline__ double rsqrt_f64(double x) {
   r = r * fma(-0.5 * xs, r * r, 1.5);
   r = r * fma(-0.5 * xs, r * r, 1.5);
   return r * pow2(-k);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) at counter n of the stream with the given seed.
+static __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+
+// Normal draw m of the Lemma 5.1 random MPO: uniforms ((z >> 11) + 1) 2^-53 in (0, 1] from
+// counters 2m and 2m+1, Box-Muller cosine branch.
+static __device__ __forceinline__ double omega_normal(uint64_t seed, uint64_t m) {
+  const double u1 = (double)((splitmix64_at(seed, 2 * m) >> 11) + 1) * 0x1.0p-53;
+  const double u2 = (double)((splitmix64_at(seed, 2 * m + 1) >> 11) + 1) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cos((2.0 * M_PI) * u2);
 }
 
 }  // namespace tnr

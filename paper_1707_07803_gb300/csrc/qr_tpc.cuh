@@ -11,6 +11,11 @@ namespace tnr {
 
 constexpr int kSmallThreads = 256;
 
+// Bytes of the shared-memory layout of qr_tpc_cta for an m x n matrix.
+__host__ __device__ inline int64_t qr_tpc_bytes(int64_t m, int64_t n) {
+  return (int64_t)sizeof(double) * (m * n + 2 * n + (m < n ? m : n) + m) + (int64_t)sizeof(int) * n;
+}
+
 struct QrSmallArgs {
   const double *src;
   int64_t lds;

@@ -132,7 +132,7 @@ Stats &S() {
 // the event opened by stats_begin, per host thread (each thread launches on its own stream)
 thread_local cudaEvent_t t_open_ev[K_NUM_CLASSES] = {nullptr};
 const char *kNames[K_NUM_CLASSES] = {"conv_rowptr", "conv_flags", "conv_scan", "conv_fill", "omega", "merge",
-                                     "contract",    "contract_tc", "gemm",     "qr",        "qr_small", "qr_piv", "svd", "misc", "round", "diff"};
+                                     "contract",    "contract_tc", "gemm",     "qr",        "qr_small", "qr_piv", "svd", "misc", "round", "diff", "batch"};
 }  // namespace
 
 void stats_begin(int cls, cudaStream_t s) {

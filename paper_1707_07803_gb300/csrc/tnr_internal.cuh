@@ -43,6 +43,7 @@ enum KClass : int {
   K_MISC,
   K_ROUND,     // fused one-CTA rounding sweeps (k_round_small)
   K_DIFF,      // differentiable solver: tape forward and adjoint kernels
+  K_BATCH,     // persistent batched solver (one CTA per problem)
   K_NUM_CLASSES
 };
 
@@ -99,6 +100,43 @@ int reset_status(cudaStream_t s);
   } while (0)
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Compression cutoff relative to ||M_k||_F: the rounding level of the product that made Y.
+// FP64 products: min(64 eps, tol / 100). BF16 x3 products carry about 2^-16 relative error per
+// term, so their noise directions are dropped at 0.05 tol (tol is then at least kMixedTol).
+constexpr double kMixedTol = 1.2e-4;
+__host__ __device__ inline double compress_cut(double tol, bool mixed_product) {
+  if (mixed_product) return 0.05 * tol;
+  const double a = 64.0 * 2.220446049250313e-16, b = 0.01 * tol;
+  return a < b ? a : b;
+}
+
+// ---- Solve plan (host) ----
+
+// Buffer-size bounds of one orthogonalisation / solve.
+struct Limits {
+  int64_t maxcore = 1;  // elements of the largest core
+  int64_t maxbond = 1;  // largest bond
+  int64_t maxrows = 1;  // largest row count of an L->R QR
+  int64_t maxsq = 1;    // largest square factor side
+};
+
+// The merged operator A' (Section 6.3) and the plan of every buffer of a solve.
+struct Plan {
+  int m = 1;  // sites merged into site 1
+  int d = 0;  // sites after the merge
+  int64_t I[TNR_MAX_SITES], J[TNR_MAX_SITES], RA[TNR_MAX_SITES + 1];
+  int64_t sq[TNR_MAX_SITES + 1];  // cap of Q bonds (max of the I- and J-side bounds)
+  int64_t pcap[TNR_MAX_SITES];    // product core capacity
+  int64_t omega_len = 0;
+  int64_t merged_elems = 0;
+  Limits L;
+};
+
+int validate_input(const tnr_mpo *A);
+// Merge count, merged dimensions, bond caps (Thm 3.2 bounds and max_rank) and buffer bounds of
+// a solve with K = k + p columns.
+int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P);
 
 // ---- FP64 dense building blocks (column-major, explicit leading dimensions) ----
 

@@ -82,18 +82,9 @@ __global__ void k_merge(const double *__restrict__ T, int64_t nr, int64_t nc, in
 
 // Lemma 5.1 random MPO: SplitMix64 counter stream, uniforms ((z >> 11) + 1) 2^-53 in (0, 1],
 // Box-Muller cosine branch, normal m from uniforms 2m and 2m+1.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
-  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 __global__ void k_omega(uint64_t seed, int64_t count, double *out) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < count; m += (int64_t)gridDim.x * blockDim.x) {
-    const double u1 = (double)((splitmix64_at(seed, 2 * m) >> 11) + 1) * 0x1.0p-53;
-    const double u2 = (double)((splitmix64_at(seed, 2 * m + 1) >> 11) + 1) * 0x1.0p-53;
-    out[m] = sqrt(-2.0 * log(u1)) * cos((2.0 * M_PI) * u2);
+    out[m] = omega_normal(seed, (uint64_t)m);
   }
 }
 
@@ -180,6 +171,8 @@ int grid_for(int64_t work, int threads = 256) {
 // ---------------------------------------------------------------------------------------
 int64_t core_elems(const tnr_mpo &M, int k) { return M.R[k] * M.I[k] * M.J[k] * M.R[k + 1]; }
 
+}  // namespace
+
 int validate_input(const tnr_mpo *A) {
   if (!A || A->d < 1 || A->d > TNR_MAX_SITES) return TNR_EINVAL;
   if (A->R[0] != 1 || A->R[A->d] != 1) return TNR_EINVAL;
@@ -188,6 +181,8 @@ int validate_input(const tnr_mpo *A) {
   }
   return TNR_OK;
 }
+
+namespace {
 
 struct Bufs {
   double *tmp = nullptr;    // GEMM / copy staging, max core
@@ -205,13 +200,6 @@ struct Bufs {
   unsigned *bar = nullptr;  // grid-barrier state of the cooperative compression
   int *ctl = nullptr;       // its control word
   int64_t cap = 0;          // doubles in tmp, Mq and US
-};
-
-struct Limits {
-  int64_t maxcore = 1;  // elements of the largest core
-  int64_t maxbond = 1;  // largest bond
-  int64_t maxrows = 1;  // largest row count of an L->R QR
-  int64_t maxsq = 1;    // largest square factor side
 };
 
 void carve(Arena &ar, const Limits &L, Bufs &b) {
@@ -293,14 +281,6 @@ int compress(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds) {
   return compress_rl(s, Y, b, cut, all_bonds, next);
 }
 
-// Compression cutoff relative to ||M_k||_F: the rounding level of the product that made Y.
-// FP64 products: min(64 eps, tol / 100). BF16 x3 products carry about 2^-16 relative error per
-// term, so their noise directions are dropped at 0.05 tol (tol is then at least kMixedTol).
-constexpr double kMixedTol = 1.2e-4;
-double compress_cut(double tol, bool mixed_product) {
-  if (mixed_product) return 0.05 * tol;
-  return std::min(64.0 * 2.220446049250313e-16, 0.01 * tol);
-}
 
 // Left-to-right Householder QR sweep (rounding part 1, Section 5.4): core k reshaped
 // (R_k I_k J_k) x R_{k+1} = Q R; Q replaces the core, R is absorbed into core k+1.
@@ -543,17 +523,8 @@ int64_t tall_bound(const int64_t *dims, int d, int64_t K, int b) {
   return v > 4e18 ? (int64_t)4e18 : (int64_t)v;
 }
 
-// The merged operator A' (Section 6.3) and the plan of every buffer of a solve.
-struct Plan {
-  int m = 1;  // sites merged into site 1
-  int d = 0;  // sites after the merge
-  int64_t I[TNR_MAX_SITES], J[TNR_MAX_SITES], RA[TNR_MAX_SITES + 1];
-  int64_t sq[TNR_MAX_SITES + 1];  // cap of Q bonds (max of the I- and J-side bounds)
-  int64_t pcap[TNR_MAX_SITES];    // product core capacity
-  int64_t omega_len = 0;
-  int64_t merged_elems = 0;
-  Limits L;
-};
+
+}  // namespace
 
 int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
   TNR_TRY(validate_input(A));
@@ -626,6 +597,8 @@ int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
   }
   return TNR_OK;
 }
+
+namespace {
 
 struct SolveBufs {
   double *merged = nullptr, *merge_tmp = nullptr;

@@ -94,6 +94,13 @@ _SIGS = {
     "tnr_solve": (ctypes.c_int, [_MPOP, _I32, _I32, _I32, ctypes.c_uint64, _OPTP, _MPOP, _P, _MPOP, _P,
                                  ctypes.c_size_t, _P]),
     "tnr_solve_batched": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _I32, _P, ctypes.c_size_t, _P]),
+    "tnr_batch_workspace": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _SZP]),
+    "tnr_batch_create": (ctypes.c_int, [_I32, ctypes.POINTER(tnr_problem), _I32, _P, ctypes.c_size_t, _P,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tnr_batch_launch": (ctypes.c_int, [_P, _P]),
+    "tnr_batch_collect": (ctypes.c_int, [_P, _P]),
+    "tnr_batch_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _I64P]),
+    "tnr_batch_destroy": (ctypes.c_int, [_P]),
     "tnr_sparse_solve_workspace": (ctypes.c_int, [_I64, _I64, _I64, _I32, _I64P, _I64P, _I32, _I32, _SZP]),
     "tnr_sparse_solve": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _I32, _I64P, _I64P, _I32, _I32, _I32,
                                         ctypes.c_uint64, _I32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -354,52 +361,59 @@ def tnr_solve(A, k, p, q, seed, tol=0.0, max_rank=0, precision=TNR_FP64, stream=
     return plan.outputs()
 
 
+def _batch_outputs(problems, precision):
+    """Per-problem output buffers (U, S, V at their tnr_solve_query capacities) and the
+    tnr_problem array describing the batch; returns (plans, probs, largest solve workspace)."""
+    lib = load()
+    n = len(problems)
+    plans = []
+    stride = 256
+    for pr in problems:
+        sp = SolvePlan.__new__(SolvePlan)  # outputs only; the batch owns the workspace
+        sp.k, sp.p = int(pr["k"]), int(pr["p"])
+        sp.opts = _opts(pr.get("tol", 0.0), pr.get("max_rank", 0), pr.get("precision", precision))
+        sp.A = pr["A"]
+        sp.sa = sp.A.to_struct()
+        sp.us, sp.vs = tnr_mpo(), tnr_mpo()
+        b = ctypes.c_size_t(0)
+        _check(lib.tnr_solve_query(ctypes.byref(sp.sa), sp.k, sp.p, ctypes.byref(sp.opts), ctypes.byref(sp.us),
+                                   ctypes.byref(sp.vs), ctypes.byref(b)), "tnr_solve_query")
+        dev = sp.A.cores[0].device
+        sp.U_cores = [torch.empty(max(sp.us.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.us.d)]
+        sp.V_cores = [torch.empty(max(sp.vs.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.vs.d)]
+        for i in range(sp.us.d):
+            sp.us.core[i] = sp.U_cores[i].data_ptr()
+            sp.vs.core[i] = sp.V_cores[i].data_ptr()
+        sp.S = torch.empty(sp.k, dtype=torch.float64, device=dev)
+        sp.ws, sp.ws_bytes = None, 0
+        stride = max(stride, (b.value + 255) // 256 * 256)
+        plans.append((sp, int(pr["q"]), int(pr["seed"])))
+    probs = (tnr_problem * max(n, 1))()
+    for i, (sp, q, seed) in enumerate(plans):
+        P = probs[i]
+        P.A = ctypes.pointer(sp.sa)
+        P.k, P.p, P.q = sp.k, sp.p, q
+        P.seed = seed
+        P.opts = sp.opts
+        P.U = ctypes.pointer(sp.us)
+        P.S = sp.S.data_ptr()
+        P.V = ctypes.pointer(sp.vs)
+    return plans, probs, stride
+
+
 class BatchPlan:
     """Buffers for a batch of independent solves (tnr_solve_batched): per-problem outputs and
     one workspace slice per worker, sized by the largest problem of the batch."""
 
     def __init__(self, problems, workers=0, precision=TNR_MIXED):
         """problems: list of dicts with keys A (Mpo), k, p, q, seed and optional tol, max_rank."""
-        lib = load()
         n = len(problems)
         self.n = n
         self.workers = int(workers) if workers else min(max(n, 1), 16)
         self.workers = max(1, min(self.workers, max(n, 1)))
-        self.plans = []
-        stride = 256
-        for pr in problems:
-            sp = SolvePlan.__new__(SolvePlan)  # outputs only; the batch owns the workspace
-            sp.k, sp.p = int(pr["k"]), int(pr["p"])
-            sp.opts = _opts(pr.get("tol", 0.0), pr.get("max_rank", 0), pr.get("precision", precision))
-            sp.A = pr["A"]
-            sp.sa = sp.A.to_struct()
-            sp.us, sp.vs = tnr_mpo(), tnr_mpo()
-            b = ctypes.c_size_t(0)
-            _check(lib.tnr_solve_query(ctypes.byref(sp.sa), sp.k, sp.p, ctypes.byref(sp.opts), ctypes.byref(sp.us),
-                                       ctypes.byref(sp.vs), ctypes.byref(b)), "tnr_solve_query")
-            dev = sp.A.cores[0].device
-            sp.U_cores = [torch.empty(max(sp.us.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.us.d)]
-            sp.V_cores = [torch.empty(max(sp.vs.cap[i], 1), dtype=torch.float64, device=dev) for i in range(sp.vs.d)]
-            for i in range(sp.us.d):
-                sp.us.core[i] = sp.U_cores[i].data_ptr()
-                sp.vs.core[i] = sp.V_cores[i].data_ptr()
-            sp.S = torch.empty(sp.k, dtype=torch.float64, device=dev)
-            sp.ws, sp.ws_bytes = None, 0
-            stride = max(stride, (b.value + 255) // 256 * 256)
-            self.plans.append((sp, int(pr["q"]), int(pr["seed"])))
-        self.ws_stride = stride
+        self.plans, self.probs, self.ws_stride = _batch_outputs(problems, precision)
         dev = problems[0]["A"].cores[0].device if n else torch.device("cuda")
-        self.ws = torch.empty(self.workers * stride, dtype=torch.uint8, device=dev)
-        self.probs = (tnr_problem * max(n, 1))()
-        for i, (sp, q, seed) in enumerate(self.plans):
-            P = self.probs[i]
-            P.A = ctypes.pointer(sp.sa)
-            P.k, P.p, P.q = sp.k, sp.p, q
-            P.seed = seed
-            P.opts = sp.opts
-            P.U = ctypes.pointer(sp.us)
-            P.S = sp.S.data_ptr()
-            P.V = ctypes.pointer(sp.vs)
+        self.ws = torch.empty(self.workers * self.ws_stride, dtype=torch.uint8, device=dev)
 
     def run(self, stream=None, check=True):
         lib = load()
@@ -413,6 +427,71 @@ class BatchPlan:
 
     def outputs(self, i):
         return self.plans[i][0].outputs()
+
+
+class PersistentBatch:
+    """A batch solved by the persistent kernel (tnr_batch_*): one launch, one CTA per problem,
+    problems taken from a device work queue; optionally autotuned and captured in a CUDA graph."""
+
+    def __init__(self, problems, precision=TNR_MIXED, autotune=True, graph=True, stream=None, ctas_per_sm=0):
+        lib = load()
+        if not problems:
+            raise ValueError("empty batch")
+        self.n = len(problems)
+        self.plans, self.probs, _ = _batch_outputs(problems, precision)
+        b = ctypes.c_size_t(0)
+        _check(lib.tnr_batch_workspace(self.n, self.probs, ctypes.byref(b)), "tnr_batch_workspace")
+        dev = problems[0]["A"].cores[0].device
+        self.ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+        self.ws_bytes = b.value
+        h = ctypes.c_void_p(0)
+        flags = (1 if autotune else 0) | (2 if graph else 0) | ((int(ctas_per_sm) & 15) << 4)
+        _check(lib.tnr_batch_create(self.n, self.probs, flags, _ptr(self.ws), self.ws_bytes, _stream(stream),
+                                    ctypes.byref(h)), "tnr_batch_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load().tnr_batch_launch(self.handle, _stream(stream)), "tnr_batch_launch")
+        return self
+
+    def collect(self, stream=None, check=True):
+        rc = load().tnr_batch_collect(self.handle, _stream(stream))
+        if check:
+            _check(rc, "tnr_batch_collect")
+        return rc
+
+    def config(self):
+        g, c, s = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(load().tnr_batch_config(self.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(s)),
+               "tnr_batch_config")
+        return {"grid": g.value, "ctas_per_sm": c.value, "smem_bytes": s.value}
+
+    def statuses(self):
+        return [self.probs[i].status for i in range(self.n)]
+
+    def outputs(self, i):
+        return self.plans[i][0].outputs()
+
+    def close(self):
+        if self.handle:
+            load().tnr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tnr_solve_batch_persistent(problems, precision=TNR_MIXED, autotune=True, graph=True, stream=None):
+    """Solves independent TNrSVD problems with the persistent kernel; returns [(U, S, V), ...]."""
+    pb = PersistentBatch(problems, precision, autotune, graph, stream)
+    pb.launch(stream)
+    pb.collect(stream)
+    out = [pb.outputs(i) for i in range(pb.n)]
+    pb.close()
+    return out
 
 
 def tnr_solve_batched(problems, workers=0, precision=TNR_MIXED, stream=None):

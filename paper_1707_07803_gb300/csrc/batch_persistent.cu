@@ -417,7 +417,7 @@ __device__ void cta_mpo_svd(BatchProblem &P, const Ctx &c, double *const *core, 
   cta_round(P, c, core, R, 1, P.tol, P.max_rank, right_orth);
   if (failed(P)) return;
   const int J1 = P.J[0], K = P.K, t = R[1], m = J1 * t, kout = P.k;
-  const int64_t qneed = (int64_t)m * K + K, jneed = 2 * (int64_t)K * K + 2 * K;
+  const int64_t qneed = (int64_t)m * K + K, jneed = 2 * (int64_t)K * K + 2 * K + jacobi_mixed_work(K);
   // Jacobi area after the QR's when both fit shared memory, else on its own
   const bool both_sm = qneed + jneed <= c.smcap;
   double *A = cta_site1_qr(P, c, core[0], J1, t, both_sm ? 0 : jneed);
@@ -430,7 +430,7 @@ __device__ void cta_mpo_svd(BatchProblem &P, const Ctx &c, double *const *core, 
     Vj[idx] = i == j ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps(G, Vj, K, nrm);
+  jacobi_sweeps_mixed(G, Vj, K, nrm, inv + K);
   for (int j = threadIdx.x; j < K; j += kBT) {
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
@@ -618,7 +618,7 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
   }
   {
     const int64_t X0 = std::max(P.I[0], P.J[0]), t1 = P.RA[1] * P.sq[1];
-    wc = std::max(wc, X0 * t1 * K + K + 2 * K * K + 2 * K);  // site-1 QR and the K x K Jacobi
+    wc = std::max(wc, X0 * t1 * K + K + 2 * K * K + 2 * K + jacobi_mixed_work(K));  // site-1 QR, K x K SVD
     wc = std::max(wc, P.I[0] * P.J[0] * P.RA[1] + X0 * K * t1);  // BF16 x3 operands (floats)
   }
   if (wc > kIntMax || P.L.maxcore > kIntMax) return TNR_ERANGE;

@@ -68,15 +68,6 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rm(const double *__restri
 // near_identity (second CholeskyQR pass): G must be within 0.5 / K of the identity entrywise,
 // i.e. the first pass left a well-conditioned factor (||G - I||_2 < 1/2); otherwise *flag = 1.
 // This is the regime (cond(Y) below ~1e8) in which CholeskyQR2 is orthogonal to rounding level.
-__device__ __forceinline__ double rcp_f64(double x) {  // 1 / x for finite x > 0
-  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
-  const double xs = x * pow2(-e);  // in [1, 2)
-  double q = (double)(1.0f / (float)xs);
-  q = q * fma(-xs, q, 2.0);
-  q = q * fma(-xs, q, 2.0);
-  return q * pow2(-e);
-}
-
 __global__ void __launch_bounds__(1024) k_chol_small(const double *__restrict__ G, int K, double *Rout, double *rdiag,
                                                      int *flag, int near_identity) {
   __shared__ double a[32 * 32];

@@ -13,10 +13,9 @@
 // with the state of the host-driven sweep just before that bond, which the host then continues.
 // The barriers spin with a bound (kSpinCap polls) and report TNR_ETIMEOUT instead of waiting
 // forever; co-residency of all CTAs is guaranteed by the cooperative launch.
-#include <cuda/atomic>
-
 #include <algorithm>
 
+#include "grid_sync.cuh"
 #include "qr_tpc.cuh"
 #include "tnr_internal.cuh"
 
@@ -38,30 +37,6 @@ struct CompressArgs {
   int *ctl;              // [0] first bond left to the host (0: none)
   int *status;
 };
-
-__device__ void grid_barrier(unsigned *bar, int *status) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> count(bar[0]), gen(bar[1]);
-    const unsigned my = gen.load(cuda::memory_order_acquire);
-    __threadfence();
-    if (count.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
-      count.store(0u, cuda::memory_order_relaxed);
-      gen.fetch_add(1u, cuda::memory_order_release);
-    } else {
-      long long spins = 0;
-      while (gen.load(cuda::memory_order_acquire) == my) {
-        if (++spins > kSpinCap) {
-          set_status(status, TNR_ETIMEOUT);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   extern __shared__ double sm[];

@@ -100,4 +100,14 @@ static __device__ __forceinline__ double omega_normal(uint64_t seed, uint64_t m)
   return sqrt(-2.0 * log(u1)) * cos((2.0 * M_PI) * u2);
 }
 
+// 1 / x for finite x > 0: exact power-of-two range reduction, FP32 reciprocal seed, two Newton steps.
+__device__ __forceinline__ double rcp_f64(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+  const double xs = x * pow2(-e);  // in [1, 2)
+  double q = (double)(1.0f / (float)xs);
+  q = q * fma(-xs, q, 2.0);
+  q = q * fma(-xs, q, 2.0);
+  return q * pow2(-e);
+}
+
 }  // namespace tnr

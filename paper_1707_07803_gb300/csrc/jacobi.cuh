@@ -12,6 +12,8 @@
 // is at the rounding level of the whole matrix (||g|| <= n eps ||G||_F) are numerically zero and
 // are not rotated: rotating one against a large column only re-injects rounding error. A pair
 // is skipped once |g_p^T g_q| <= tol ||g_p|| ||g_q||, tol = 16 eps sqrt(n).
+// The sweeps are written once for FP32 and FP64; jacobi_sweeps_mixed runs them in FP32 first and
+// finishes in FP64 (see there), which is what the SVD kernels call.
 #pragma once
 
 #include <cfloat>
@@ -30,22 +32,51 @@ __host__ __device__ inline int jacobi_pairs_per_warp(int n, int warps) {
   return ppw;
 }
 
-// All threads of the CTA call this; nrm: n doubles of shared memory. Returns the sweep count.
-static __device__ __noinline__ int jacobi_sweeps(double *G, double *V, int n, double *nrm) {
+// FP32 rotation of the preconditioning pass (same formulas as jacobi_rotation, in FP32).
+__device__ __forceinline__ bool jacobi_rotation_f32(float al, float be, float ga, float &cs, float &sn) {
+  const float z = (be - al) / (2.0f * ga);
+  if (!isfinite(z)) return false;
+  const float t = copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+  if (t == 0.0f || !isfinite(t)) return false;
+  cs = rsqrtf(fmaf(t, t, 1.0f));
+  sn = cs * t;
+  return true;
+}
+__device__ __forceinline__ bool jacobi_rot(double al, double be, double ga, double &cs, double &sn) {
+  return jacobi_rotation(al, be, ga, cs, sn);
+}
+__device__ __forceinline__ bool jacobi_rot(float al, float be, float ga, float &cs, float &sn) {
+  return jacobi_rotation_f32(al, be, ga, cs, sn);
+}
+template <typename T>
+struct JacobiEps;
+template <>
+struct JacobiEps<double> {
+  static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+};
+template <>
+struct JacobiEps<float> {
+  static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+};
+
+// All threads of the CTA call this; nrm: n values of shared memory. Returns the sweep count.
+template <typename T>
+static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, T *nrm, int max_sweeps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nthr = blockDim.x, nw = nthr >> 5;
   const int np = (n + 1) & ~1;
   const int ppw = jacobi_pairs_per_warp(n, nw);
   const int g = 32 / ppw, gi = lane / g, li = lane % g;
   const int pstride = nw * ppw;
-  const double tolj = 16.0 * DBL_EPSILON * sqrt((double)(n > 4 ? n : 4));
-  const double tol2 = tolj * tolj;
-  __shared__ double s_fro2;
+  const T eps = JacobiEps<T>::eps();
+  const T tolj = (T)16 * eps * (T)sqrt((double)(n > 4 ? n : 4));
+  const T tol2 = tolj * tolj;
+  __shared__ T s_fro2;
   __shared__ int s_rot2;
   int sweep = 0;
-  for (; sweep < 60; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
     for (int j = threadIdx.x; j < n; j += nthr) {
-      double s0 = 0.0, s1 = 0.0;
+      T s0 = 0, s1 = 0;
       int i = 0;
       for (; i + 1 < n; i += 2) {
         s0 = fma(G[i + n * j], G[i + n * j], s0);
@@ -58,13 +89,13 @@ static __device__ __noinline__ int jacobi_sweeps(double *G, double *V, int n, do
     __syncthreads();
     if (sweep == 0) {
       if (threadIdx.x == 0) {
-        double f = 0.0;
+        T f = 0;
         for (int j = 0; j < n; ++j) f += nrm[j];
         s_fro2 = f;
       }
       __syncthreads();
     }
-    const double floor2 = (double)n * DBL_EPSILON * (double)n * DBL_EPSILON * s_fro2;
+    const T floor2 = (T)n * eps * (T)n * eps * s_fro2;
     for (int round = 0; round < np - 1; ++round) {
       for (int pbase = warp * ppw; pbase < np / 2; pbase += pstride) {
         const int pr = pbase + gi;
@@ -84,30 +115,30 @@ static __device__ __noinline__ int jacobi_sweeps(double *G, double *V, int n, do
           }
         }
         bool act = p >= 0 && q < n;
-        double al = 0.0, be = 0.0;
+        T al = 0, be = 0;
         if (act) {
           al = nrm[p];
           be = nrm[q];
           act = al > floor2 && be > floor2;
         }
-        double ga = 0.0;
+        T ga = 0;
         if (act)
           for (int i = li; i < n; i += g) ga = fma(G[i + n * p], G[i + n * q], ga);
         for (int o = g >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o, g);
-        double cs = 1.0, sn = 0.0;
-        if (act) act = ga != 0.0 && ga * ga > tol2 * al * be && jacobi_rotation(al, be, ga, cs, sn);
+        T cs = 1, sn = 0;
+        if (act) act = ga != (T)0 && ga * ga > tol2 * al * be && jacobi_rot(al, be, ga, cs, sn);
         if (act) {
-          double *gp = G + n * p, *gq = G + n * q, *vp = V + n * p, *vq = V + n * q;
+          T *gp = G + n * p, *gq = G + n * q, *vp = V + n * p, *vq = V + n * q;
           for (int i = li; i < n; i += g) {
-            const double x = gp[i], y = gq[i];
+            const T x = gp[i], y = gq[i];
             gp[i] = fma(-sn, y, cs * x);
             gq[i] = fma(sn, x, cs * y);
-            const double xv = vp[i], yv = vq[i];
+            const T xv = vp[i], yv = vq[i];
             vp[i] = fma(-sn, yv, cs * xv);
             vq[i] = fma(sn, xv, cs * yv);
           }
           if (li == 0) {
-            const double c2 = cs * cs, s2 = sn * sn, cg = 2.0 * cs * sn * ga;
+            const T c2 = cs * cs, s2 = sn * sn, cg = (T)2 * cs * sn * ga;
             nrm[p] = fma(c2, al, fma(s2, be, -cg));
             nrm[q] = fma(s2, al, fma(c2, be, cg));
             s_rot2 = 1;
@@ -121,6 +152,103 @@ static __device__ __noinline__ int jacobi_sweeps(double *G, double *V, int n, do
     if (!rotated) break;
   }
   return sweep + 1;
+}
+
+// Plain FP64 sweeps (G_in V = G_out with V accumulated from its value on entry).
+static __device__ __forceinline__ int jacobi_sweeps(double *G, double *V, int n, double *nrm) {
+  return jacobi_sweeps_t<double>(G, V, n, nrm, 60);
+}
+
+// Doubles of work area jacobi_sweeps_mixed needs for an n x n matrix.
+__host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 2 * n * n + n; }
+
+// Mixed-precision one-sided Jacobi (the preconditioned scheme of Gao, Ma and Shao, "A mixed
+// precision Jacobi SVD algorithm", 2022): the sweeps run to convergence in FP32 on a copy of G
+// (scaled by a power of two into FP32 range), the FP32 right vectors V0 are made orthonormal to
+// FP64 rounding by two Newton-Schulz steps V <- V (3 I - V^T V) / 2 (quadratic: ~1e-6 -> 1e-12 ->
+// rounding level), and the FP64 sweeps then run on G V0 with V accumulated from V0. The columns
+// of G V0 are orthogonal to FP32 accuracy, so the FP64 phase converges in two or three sweeps
+// (the last one only confirms) instead of six to eight: most of the O(n^3) work per sweep moves to
+// the FP32 pipe, 64 times wider than FP64 on GB300. Results: G V = U S with V orthogonal to FP64
+// rounding, exactly as jacobi_sweeps. V on entry is ignored (the identity is assumed).
+// work: jacobi_mixed_work(n) doubles. Returns the number of FP64 sweeps.
+static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work) {
+  const int nthr = blockDim.x;
+  const int nn = n * n;
+  float *Gf = reinterpret_cast<float *>(work), *Vf = Gf + nn, *nf = Vf + nn;
+  __shared__ double s_scale;
+  // power-of-two scale bringing ||G||_F near 1 (FP32 range; exact in both directions)
+  for (int j = threadIdx.x; j < n; j += nthr) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = fma(G[i + n * j], G[i + n * j], s);
+    nrm[j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int j = 0; j < n; ++j) f += nrm[j];
+    const int e = f > 0.0 && isfinite(f) ? (((int)((__double_as_longlong(f) >> 52) & 0x7FF) - 1023) >> 1) : 0;
+    s_scale = pow2(-e);
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+    Gf[idx] = (float)(G[idx] * sc);
+    Vf[idx] = (idx % n == idx / n) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  jacobi_sweeps_t<float>(Gf, Vf, n, nf, 40);
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) V[idx] = (double)Vf[idx];
+  __syncthreads();
+  // Newton-Schulz steps; T1 = V^T V, T2 = 1.5 V - 0.5 V T1 (the FP32 copies are dead now)
+  double *T1 = work, *T2 = work + nn;
+  for (int it = 0; it < 2; ++it) {
+    for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+      const int i = idx % n, j = idx / n;
+      const double *vi = V + n * i, *vj = V + n * j;
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 1 < n; l += 2) {
+        s0 = fma(vi[l], vj[l], s0);
+        s1 = fma(vi[l + 1], vj[l + 1], s1);
+      }
+      if (l < n) s0 = fma(vi[l], vj[l], s0);
+      T1[idx] = s0 + s1;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+      const int i = idx % n, j = idx / n;
+      const double *t = T1 + n * j;
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 1 < n; l += 2) {
+        s0 = fma(V[i + n * l], t[l], s0);
+        s1 = fma(V[i + n * (l + 1)], t[l + 1], s1);
+      }
+      if (l < n) s0 = fma(V[i + n * l], t[l], s0);
+      T2[idx] = fma(-0.5, s0 + s1, 1.5 * V[idx]);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nn; idx += nthr) V[idx] = T2[idx];
+    __syncthreads();
+  }
+  // G <- G V0
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+    const int i = idx % n, j = idx / n;
+    const double *v = V + n * j;
+    double s0 = 0.0, s1 = 0.0;
+    int l = 0;
+    for (; l + 1 < n; l += 2) {
+      s0 = fma(G[i + n * l], v[l], s0);
+      s1 = fma(G[i + n * (l + 1)], v[l + 1], s1);
+    }
+    if (l < n) s0 = fma(G[i + n * l], v[l], s0);
+    T2[idx] = s0 + s1;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) G[idx] = T2[idx];
+  __syncthreads();
+  return jacobi_sweeps_t<double>(G, V, n, nrm, 60);
 }
 
 }  // namespace tnr

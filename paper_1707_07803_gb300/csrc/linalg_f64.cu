@@ -760,6 +760,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
   const bool in_smem = Gw == nullptr;
   double *g = in_smem ? sm : Gw;          // working copy, ld n
   double *v = in_smem ? sm + n * n : Vw;  // working V, ld n
+  double *jw = v + n * n;                 // work of the mixed-precision sweeps (after V)
   const int nthr = blockDim.x;
   for (int idx = threadIdx.x; idx < n * n; idx += nthr) {
     const int i = idx % n, j = idx / n;
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
     v[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps(g, v, n, s_norm);  // jacobi.cuh
+  jacobi_sweeps_mixed(g, v, n, s_norm, jw);  // jacobi.cuh
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nthr / 32;
   // final column norms and their reciprocals, one thread per column (the square roots and
@@ -1034,9 +1035,12 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
   return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
+// Doubles of the K x K Jacobi's working set: G, V and the mixed-precision work area.
+static int64_t jacobi_elems(int64_t n) { return 2 * n * n + jacobi_mixed_work(n); }
+
 size_t jacobi_scratch(int64_t n) {
-  if (2 * n * n * sizeof(double) <= 160 * 1024) return 0;
-  return 2 * (((size_t)n * n * sizeof(double) + 255) & ~size_t(255));
+  if (jacobi_elems(n) * (int64_t)sizeof(double) <= 160 * 1024) return 0;
+  return ((size_t)jacobi_elems(n) * sizeof(double) + 255) & ~size_t(255);
 }
 
 int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S, double *V, int64_t ldv,
@@ -1044,10 +1048,10 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
   if (n <= 0) return TNR_OK;
   if (n > 1024) return TNR_EINVAL;
   double *Gw = nullptr, *Vw = nullptr;
-  size_t smem = 2 * n * n * sizeof(double);
+  size_t smem = (size_t)jacobi_elems(n) * sizeof(double);
   if (smem > 160 * 1024) {
     Gw = static_cast<double *>(scratch);
-    Vw = Gw + (((size_t)n * n * sizeof(double) + 255) & ~size_t(255)) / sizeof(double);
+    Vw = Gw + n * n;  // the mixed sweeps' work area follows V
     smem = 0;
   }
   TNR_TRY(ensure_dynamic_smem((const void *)k_jacobi, smem));

@@ -29,7 +29,7 @@ constexpr int kStepMaxN = 1024;  // largest min(t, w)
 
 static __host__ __device__ inline int64_t svd_step_work(int64_t t, int64_t w) {
   const int64_t mm = t >= w ? t : w, n = t >= w ? w : t;
-  return 2 * mm * n + 2 * n * n + 2 * n;
+  return 2 * mm * n + 3 * n * n + 3 * n;
 }
 
 static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, double delta2, int64_t max_rank,
@@ -41,7 +41,8 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
   double *V = G + n * n;     // n x n
   double *tau = V + n * n;   // n
   double *nrm = tau + n;     // n (Jacobi column norms, then singular values)
-  double *W = nrm + n;       // mm x n: reflector application workspace
+  double *W = nrm + n;       // mm x n: reflector application workspace; with the n^2 + n after it,
+                             // the work area of the mixed-precision Jacobi (>= 2 n^2 + n)
   __shared__ int s_r;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int idx = threadIdx.x; idx < mm * n; idx += kStepThreads) {
@@ -169,8 +170,8 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
       return t;
     }
   }
-  // ---- one-sided Jacobi on G (jacobi.cuh)
-  jacobi_sweeps(G, V, n, nrm);
+  // ---- one-sided Jacobi on G (jacobi.cuh): FP32-preconditioned, finished in FP64
+  jacobi_sweeps_mixed(G, V, n, nrm, W);
   // ---- singular values (column norms of G, one thread per column), order, truncation
   for (int j = threadIdx.x; j < n; j += kStepThreads) {
     double s0 = 0.0, s1 = 0.0;

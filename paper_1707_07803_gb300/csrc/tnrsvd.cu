@@ -12,7 +12,7 @@
 
 #include <cuda_bf16.h>
 
-#include "cholqr.cuh"
+#include "dev_common.cuh"
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -398,33 +398,21 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 }
 
 // Thin QR of the site-1 matrix A1^T = Q~ R~ ((I1 t) x K, Alg. 5.2/5.3): Q~ (column-major) into
-// b.Mq, R~ into b.Rm. For K <= 32: CholeskyQR2 (two passes of Gram, K-pivot Cholesky and a
-// warp-parallel triangular solve), checked on the device; when a Cholesky breaks down or the
-// second pass is not near the identity (cond(A1) beyond ~1e8) it falls back to the multi-CTA
-// Householder QR on the same input.
+// b.Mq, R~ into b.Rm. For K <= 32: CholeskyQR2 in one cooperative launch (site1_qr.cu), checked on
+// the device; when a Cholesky breaks down or the second pass is not near the identity (cond(A1)
+// beyond ~1e8) it falls back to the multi-CTA Householder QR on the same input.
 int site1_qr(cudaStream_t s, const double *core0, int64_t I1, int64_t K, int64_t t, Bufs &b) {
-  const int64_t m = I1 * t;
-  if (K <= 32 && m >= K && m * K <= b.cap) {
-    {
-      LaunchScope ls(K_MISC, s);
-      k_site1_rowmajor<<<grid_for(m * K), 256, 0, s>>>(core0, b.US, I1, K, t);
-    }
-    TNR_CK(cudaGetLastError());
-    int *flag = b.ctl + 1;
-    TNR_CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
-    TNR_TRY(cholqr_pass_small(s, b.US, m, (int)K, b.G, b.Rm, b.Sv, flag, K_QR, false));
-    TNR_TRY(cholqr_pass_small(s, b.US, m, (int)K, b.G, b.Vr, b.Sv, flag, K_QR, true));
+  bool launched = false;
+  int *flag = b.ctl + 1;
+  TNR_TRY(site1_cholqr2(s, core0, I1, K, t, b.US, b.cap, b.Vr, b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
+  if (launched) {
     int hflag = 0;
     TNR_CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     TNR_TRY(read_status(s));
-    if (!hflag) {
-      TNR_TRY(gemm_f64(s, false, false, K, K, K, 1.0, b.Vr, K, 0, b.Rm, K, 0, 0.0, b.G, K, 0));  // R2 R1
-      TNR_TRY(copy_matrix_f64(s, b.G, K, b.Rm, K, K, K, false));
-      return copy_matrix_f64(s, b.US, K, b.Mq, m, m, K, true);  // row-major -> column-major
-    }
+    if (!hflag) return TNR_OK;
   }
   TNR_TRY(site1_perm(s, core0, b.Mq, I1, K, t, K, 0));
-  return thin_qr(s, b.Mq, m, K, b.Rm, K, b);
+  return thin_qr(s, b.Mq, I1 * t, K, b.Rm, K, b);
 }
 
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K

@@ -27,8 +27,10 @@ constexpr int kS1MaxK = 32;
 constexpr int kS1MaxRowsPerCta = 384;
 
 struct Site1Args {
-  const double *core0;  // (1, I1, K, t)
-  int I1, K, m, rpc;    // m = I1 t rows; rows per CTA
+  double *core0;          // (1, I1, K, t)
+  const int64_t *t_dev;   // t in device memory (rank left there by the rounding), or null
+  int I1, K, t, rpc;      // t: the rank when t_dev is null; rows per CTA
+  int core_out;           // write Q~ back into core0's layout instead of Qout
   double *Gpart;        // gridDim.x partial Grams, K x K each
   double *S, *rdiag;    // the current pass's factor scaled to unit diagonal, and 1 / its diagonal
   double *Rout;         // K x K: R = R2 R1 (column-major, upper)
@@ -37,6 +39,16 @@ struct Site1Args {
   unsigned *bar;
   int *status;
 };
+
+// 1 / x for finite x > 0 with one Newton step from the FP32 reciprocal (relative error ~2^-46): the
+// pass-1 pivots only have to precondition, since Y = Q1 R1 holds exactly for the R1 the solve uses.
+__device__ __forceinline__ double rcp_f64_1(double x) {
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+  const double xs = x * pow2(-e);
+  double q = (double)(1.0f / (float)xs);
+  q = q * fma(-xs, q, 2.0);
+  return q * pow2(-e);
+}
 
 // Cholesky of the K x K matrix a (shared, column-major, K <= 32) on one CTA of kS1Threads
 // threads: R (upper) to Rs and 1 / diag(R) to rd (both shared; Rs must not alias a). Thread
@@ -83,23 +95,25 @@ __device__ bool cta_chol(double *a, int K, double *Rs, double *rd, bool second, 
     if (!(d0 > 0.0) || !isfinite(d0))
       s_bad = 1;
     else
-      dinv[0] = rcp_f64(d0);
+      dinv[0] = second ? rcp_f64(d0) : rcp_f64_1(d0);
   }
   __syncthreads();
   if (s_bad) return false;
+  const bool own_diag = i < K && (i % kW) == w;  // this thread holds (i, i)
   for (int j = 0; j < K; ++j) {
     if (i > j && i < K) {
       const double f = a[j + K * i] * dinv[j];
+      if (own_diag && i == j + 1) {  // the next pivot first: its reciprocal overlaps the other updates
+        const double v = fma(-f, a[j + K * i], a[i + K * i]);
+        a[i + K * i] = v;
+        if (!(v > 0.0) || !isfinite(v))
+          s_bad = 1;
+        else
+          dinv[j + 1] = second ? rcp_f64(v) : rcp_f64_1(v);
+      }
       for (int l = w; l < K; l += kW) {
-        if (l < i) continue;
-        const double v = fma(-f, a[j + K * l], a[i + K * l]);
-        a[i + K * l] = v;
-        if (l == i && i == j + 1) {
-          if (!(v > 0.0) || !isfinite(v))
-            s_bad = 1;
-          else
-            dinv[j + 1] = rcp_f64(v);
-        }
+        if (l < i || (l == i && i == j + 1)) continue;
+        a[i + K * l] = fma(-f, a[j + K * l], a[i + K * l]);
       }
     }
     __syncthreads();
@@ -123,7 +137,8 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   __shared__ double r2s[kS1MaxK * kS1MaxK];
   __shared__ double rdv[kS1MaxK];
   __shared__ double dinv[kS1MaxK];
-  const int K = a.K, I1 = a.I1, m = a.m, tid = threadIdx.x, nthr = blockDim.x;
+  const int K = a.K, I1 = a.I1, tid = threadIdx.x, nthr = blockDim.x;
+  const int m = I1 * (a.t_dev ? (int)__ldcg(a.t_dev) : a.t);  // rows; the grid covers the bound
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const int ld = K + 1;
   const int r0 = blockIdx.x * a.rpc;
@@ -161,19 +176,28 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
       // fixed-order sum of the partials (deterministic); four loads in flight per step
       const unsigned nb = gridDim.x;
       const size_t KK = (size_t)K * K;
-      for (int e = tid; e < K * K; e += nthr) {
-        double s = 0.0;
-        unsigned b = 0;
-        for (; b + 3 < nb; b += 4) {
-          const double p0 = __ldcg(a.Gpart + b * KK + e), p1 = __ldcg(a.Gpart + (b + 1) * KK + e);
-          const double p2 = __ldcg(a.Gpart + (b + 2) * KK + e), p3 = __ldcg(a.Gpart + (b + 3) * KK + e);
-          s += p0;
-          s += p1;
-          s += p2;
-          s += p3;
-        }
-        for (; b < nb; ++b) s += __ldcg(a.Gpart + b * KK + e);
-        am[e] = s;
+      constexpr int kE = kS1MaxK * kS1MaxK / kS1Threads;  // elements per thread (4)
+      double acc[kE];
+#pragma unroll
+      for (int u = 0; u < kE; ++u) acc[u] = 0.0;
+      for (unsigned b0 = 0; b0 < nb; b0 += 8) {
+        double p[8][kE];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int u = 0; u < kE; ++u) {
+            const int e = tid + u * kS1Threads;
+            p[q][u] = (b0 + q < nb && e < K * K) ? __ldcg(a.Gpart + (b0 + q) * KK + e) : 0.0;
+          }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int u = 0; u < kE; ++u) acc[u] += p[q][u];
+      }
+#pragma unroll
+      for (int u = 0; u < kE; ++u) {
+        const int e = tid + u * kS1Threads;
+        if (e < K * K) am[e] = acc[u];
       }
       __syncthreads();
       double *Rs = pass == 0 ? r1s : r2s;
@@ -218,28 +242,41 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     }
     __syncthreads();
   }
-  // Q~ (column-major, consecutive threads write consecutive rows)
+  // Q~: column-major, or back into the core's layout (each CTA writes only the rows it read)
   for (int x = tid; x < nr * K; x += nthr) {
-    const int rr = x % nr, c = x / nr;
-    a.Qout[(r0 + rr) + (size_t)m * c] = ys[rr * ld + c];
+    const int rr = x % nr, c = x / nr, row = r0 + rr;
+    if (a.core_out)
+      a.core0[row % I1 + I1 * (c + K * (row / I1))] = ys[rr * ld + c];
+    else
+      a.Qout[row + (size_t)m * c] = ys[rr * ld + c];
   }
   if (blockIdx.x == 0)  // R~ = R2 R1 (both upper, in shared memory)
     for (int e = tid; e < K * K; e += nthr) {
       const int i = e % K, l = e / K;
-      double s = 0.0;
-      for (int q = i; q <= l; ++q) s = fma(r2s[i + K * q], r1s[q + K * l], s);
-      a.Rout[e] = i <= l ? s : 0.0;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int q = i;
+      for (; q + 3 <= l; q += 4) {
+        s0 = fma(r2s[i + K * q], r1s[q + K * l], s0);
+        s1 = fma(r2s[i + K * (q + 1)], r1s[q + 1 + K * l], s1);
+        s2 = fma(r2s[i + K * (q + 2)], r1s[q + 2 + K * l], s2);
+        s3 = fma(r2s[i + K * (q + 3)], r1s[q + 3 + K * l], s3);
+      }
+      for (; q <= l; ++q) s0 = fma(r2s[i + K * q], r1s[q + K * l], s0);
+      a.Rout[e] = i <= l ? (s0 + s1) + (s2 + s3) : 0.0;
     }
 }
 
 }  // namespace
 
-// CholeskyQR2 of the site-1 matrix of core0 (1, I1, K, t) in one cooperative launch: Q~ (column-
-// major (I1 t) x K) to Qout, R~ (K x K) to Rout, *flag (device) = 1 when the caller must fall back
-// to Householder. Scratch: Gpart (gcap doubles), S (K x K), rdiag (K). *launched = false (nothing queued) when the sizes are outside the kernel's
-// layout (K > 32, more rows than 64 CTAs hold) or gcap (doubles at Gpart) is too small.
-int site1_cholqr2(cudaStream_t s, const double *core0, int64_t I1, int64_t K, int64_t t, double *Gpart, int64_t gcap,
-                  double *S, double *rdiag, double *Rout, double *Qout, int *flag, unsigned *bar, bool *launched) {
+// CholeskyQR2 of the site-1 matrix of core0 (1, I1, K, t) in one cooperative launch: Q~ to Qout
+// (column-major (I1 t) x K) or, with core_out, back into core0 (1, I1, K, t); R~ (K x K) to Rout;
+// *flag (device) = 1 when the caller must fall back to Householder (core0 is then unchanged).
+// t_dev: when not null the rank is read there on the device and t is only its upper bound.
+// Scratch: Gpart (gcap doubles), S (K x K), rdiag (K). *launched = false (nothing queued) when the
+// sizes are outside the kernel's layout (K > 32, more rows than 64 CTAs hold) or gcap is too small.
+int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
+                  double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout, int *flag,
+                  unsigned *bar, bool *launched) {
   *launched = false;
   const int64_t m = I1 * t;
   if (K < 1 || K > kS1MaxK || m < K || m > (int64_t)64 * kS1MaxRowsPerCta) return TNR_OK;
@@ -253,10 +290,12 @@ int site1_cholqr2(cudaStream_t s, const double *core0, int64_t I1, int64_t K, in
   TNR_TRY(ensure_dynamic_smem((const void *)k_site1_cholqr2, smem));
   Site1Args a;
   a.core0 = core0;
+  a.t_dev = t_dev;
   a.I1 = (int)I1;
   a.K = (int)K;
-  a.m = (int)m;
+  a.t = (int)t;
   a.rpc = (int)rpc;
+  a.core_out = core_out ? 1 : 0;
   a.Gpart = Gpart;
   a.S = S;
   a.rdiag = rdiag;

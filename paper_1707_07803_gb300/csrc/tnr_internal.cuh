@@ -197,10 +197,13 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
                 bool *launched);
 
 // CholeskyQR2 of the site-1 matrix (I1 t) x K of core0 (1, I1, K, t) in one cooperative launch
-// (site1_qr.cu): Q~ to Qout (column-major), R~ to Rout; *flag (device) = 1 when the factorisation
-// must be redone by Householder. *launched = false when the sizes are outside its layout.
-int site1_cholqr2(cudaStream_t s, const double *core0, int64_t I1, int64_t K, int64_t t, double *Gpart, int64_t gcap,
-                  double *S, double *rdiag, double *Rout, double *Qout, int *flag, unsigned *bar, bool *launched);
+// (site1_qr.cu): Q~ to Qout (column-major) or back into core0 (core_out), R~ to Rout; *flag
+// (device) = 1 when the factorisation must be redone by Householder. t_dev (may be null): the
+// rank in device memory, t then being its upper bound. *launched = false when the sizes are
+// outside its layout.
+int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
+                  double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout, int *flag,
+                  unsigned *bar, bool *launched);
 
 // Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
 int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);

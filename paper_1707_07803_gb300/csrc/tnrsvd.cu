@@ -376,17 +376,28 @@ int sweep_rl(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, Bufs &b) 
 // Both rounding sweeps of Section 5.4 (L->R QR, then the R->L truncating loop of Alg. 5.2): one
 // fused one-CTA launch when every core fits shared memory, else one launch sequence per bond.
 // right_orth: cores 1..d-1 are right-orthonormal on entry (see compress_rl).
-int round_sweeps(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, bool right_orth, Bufs &b) {
+// *pending: the fused kernel ran and left the ranks in b.rdev (Y.R keeps the bounds it had on
+// entry until read_ranks); otherwise Y.R is exact on return.
+int round_sweeps(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, bool right_orth, Bufs &b, bool *pending) {
+  *pending = false;
   bool fused = false;
   TNR_TRY(round_small(s, Y, tol, max_rank, right_orth, b.rdev, &fused));
   if (!fused) {
     TNR_TRY(sweep_lr(s, Y, b));
     return sweep_rl(s, Y, tol, max_rank, b);
   }
+  *pending = true;
+  return TNR_OK;
+}
+
+// Reads the ranks the fused rounding left in b.rdev and the site-1 fallback flag (one sync).
+int read_ranks(cudaStream_t s, tnr_mpo &Y, Bufs &b, bool pending, int *hflag) {
   int64_t R[TNR_MAX_SITES + 1];
-  TNR_CK(cudaMemcpyAsync(R, b.rdev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
+  if (pending) TNR_CK(cudaMemcpyAsync(R, b.rdev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
+  TNR_CK(cudaMemcpyAsync(hflag, b.ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   TNR_TRY(read_status(s));
-  for (int k = 0; k <= Y.d; ++k) Y.R[k] = R[k];
+  if (pending)
+    for (int k = 0; k <= Y.d; ++k) Y.R[k] = R[k];
   return TNR_OK;
 }
 
@@ -397,37 +408,44 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
   return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
-// Thin QR of the site-1 matrix A1^T = Q~ R~ ((I1 t) x K, Alg. 5.2/5.3): Q~ (column-major) into
-// b.Mq, R~ into b.Rm. For K <= 32: CholeskyQR2 in one cooperative launch (site1_qr.cu), checked on
-// the device; when a Cholesky breaks down or the second pass is not near the identity (cond(A1)
-// beyond ~1e8) it falls back to the multi-CTA Householder QR on the same input.
-int site1_qr(cudaStream_t s, const double *core0, int64_t I1, int64_t K, int64_t t, Bufs &b) {
+// Thin QR of the site-1 matrix A1^T = Q~ R~ ((I1 t) x K, Alg. 5.2/5.3), R~ into b.Rm, Q~ into b.Mq
+// (column-major) or, with core_out, back into the site-1 core. For K <= 32: CholeskyQR2 in one
+// cooperative launch (site1_qr.cu) that reads the rank left by the fused rounding on the device
+// when `pending`; the ranks and its fallback flag come back in one sync. When a Cholesky breaks
+// down or the second pass is not near the identity (cond(A1) beyond ~1e8) the QR is redone by the
+// multi-CTA Householder kernel on the unchanged core.
+int site1_qr(cudaStream_t s, tnr_mpo &Y, bool pending, bool core_out, Bufs &b) {
+  const int64_t I1 = Y.I[0], K = Y.J[0];
   bool launched = false;
   int *flag = b.ctl + 1;
-  TNR_TRY(site1_cholqr2(s, core0, I1, K, t, b.US, b.cap, b.Vr, b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
+  TNR_TRY(site1_cholqr2(s, Y.core[0], I1, K, Y.R[1], pending ? b.rdev + 1 : nullptr, core_out, b.US, b.cap, b.Vr,
+                        b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
+  int hflag = 1;
   if (launched) {
-    int hflag = 0;
-    TNR_CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TNR_TRY(read_status(s));
-    if (!hflag) return TNR_OK;
+    TNR_TRY(read_ranks(s, Y, b, pending, &hflag));
+  } else if (pending) {
+    int dummy = 0;
+    TNR_TRY(read_ranks(s, Y, b, true, &dummy));
   }
-  TNR_TRY(site1_perm(s, core0, b.Mq, I1, K, t, K, 0));
-  return thin_qr(s, b.Mq, I1 * t, K, b.Rm, K, b);
+  const int64_t t = Y.R[1];
+  if (I1 * t < K) return TNR_EINVAL;
+  if (!hflag) return TNR_OK;
+  TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
+  TNR_TRY(thin_qr(s, b.Mq, I1 * t, K, b.Rm, K, b));
+  if (core_out) TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
+  return TNR_OK;
 }
 
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
                        bool mixed_product = false) {
-  bool right_orth = false;
+  bool right_orth = false, pending = false;
   if (tol > 0.0) TNR_TRY(compress(s, Y, b, compress_cut(tol, mixed_product), &right_orth));
-  TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b));
-  const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
-  const int64_t m = I1 * t;
-  if (m < K) return TNR_EINVAL;
-  TNR_TRY(site1_qr(s, Y.core[0], I1, K, t, b));  // A1^T = Q~ R~
-  if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * K * K, cudaMemcpyDeviceToDevice, s));
-  TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
+  TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b, &pending));
+  if (Y.I[0] * Y.R[1] < Y.J[0] && !pending) return TNR_EINVAL;
+  TNR_TRY(site1_qr(s, Y, pending, true, b));  // A1^T = Q~ R~, Q~ back into the site-1 core
+  if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * Y.J[0] * Y.J[0], cudaMemcpyDeviceToDevice, s));
   return TNR_OK;
 }
 
@@ -436,14 +454,13 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 // kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
-  bool right_orth = false;
+  bool right_orth = false, pending = false;
   if (tol > 0.0) TNR_TRY(compress(s, Z, b, compress_cut(tol, false), &right_orth));
-  TNR_TRY(round_sweeps(s, Z, tol, max_rank, right_orth, b));
+  TNR_TRY(round_sweeps(s, Z, tol, max_rank, right_orth, b, &pending));
+  TNR_TRY(site1_qr(s, Z, pending, false, b));  // M^T ((J1 t) x K) = Q~ R~
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
   const int64_t m = J1 * t;
-  if (m < K) return TNR_EINVAL;
   if (J1 * kout * t > v1cap) return TNR_ENOMEM;
-  TNR_TRY(site1_qr(s, Z.core[0], J1, K, t, b));  // M^T ((J1 t) x K) = Q~ R~
   TNR_TRY(copy_matrix_f64(s, b.Rm, K, Wout, K, K, K, true));  // R~^T
   TNR_TRY(jacobi_svd_f64(s, Wout, K, K, Sout, b.Vr, K, b.jac));  // R~^T = W S Zr^T
   // V = Q~ Zr ((J1 t) x K), then V^(1) columns < kout

@@ -39,7 +39,7 @@ KERNELS = {
 UNIT = "solves/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the named kernel, as recorded in
 # profiles/ (k_compress_c2.md); reported only while that kernel is unchanged.
-TRAFFIC_BYTES = {"qr_piv": 2.74e6}
+TRAFFIC_BYTES = {}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 

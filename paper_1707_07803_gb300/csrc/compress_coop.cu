@@ -17,6 +17,7 @@
 
 #include "grid_sync.cuh"
 #include "qr_tpc.cuh"
+#include "round_small.cuh"
 #include "tnr_internal.cuh"
 
 namespace tnr {
@@ -34,8 +35,14 @@ struct CompressArgs {
   int64_t qr_cap;        // shared-memory bytes available to the QR
   int64_t *R_out;        // ranks on exit (d + 1)
   unsigned *bar;         // [0] arrivals, [1] generation
-  int *ctl;              // [0] first bond left to the host (0: none)
+  int *ctl;              // [0] first bond left to the host (0: none), [2] rounding done here
   int *status;
+  // fused rounding (Section 5.4) after a complete compression, on CTA 0
+  int fuse_round;
+  double tol;
+  int64_t max_rank;
+  int64_t round_cap;     // dynamic shared-memory bytes available to it
+  int64_t *R_round;      // ranks after the rounding (d + 1)
 };
 
 __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
@@ -43,6 +50,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   const int d = a.d;
   const double *cur = a.core[d - 1];  // M_k (t x w, ld t)
   int rk1 = 1;                        // compressed rank of bond k+1
+  // the rounding has not run (yet): a later launch gated on this word must do nothing
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl[2] = 0;
   for (int k = d - 1; k >= 1; --k) {
     const int t = a.R[k], w = a.phys[k] * rk1;
     const bool fits = w <= 64 && qr_tpc_bytes(w, t) <= a.qr_cap;
@@ -119,23 +128,45 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     a.core[0][x] = __ldcg(cur + x);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ctl[0] = 0;
+    a.ctl[2] = 0;
     a.R_out[1] = rk1;
   }
+  if (!a.fuse_round) return;
+  // every bond was compressed, so cores 1..d-1 are right-orthonormal: CTA 0 runs the rounding
+  // sweeps (or their no-truncation certificate) on the compressed cores when they fit its
+  // shared memory, leaving the final ranks in R_out
+  grid_barrier(a.bar, a.status);
+  if (blockIdx.x != 0) return;
+  __shared__ int64_t s_R[TNR_MAX_SITES + 1], s_phys[TNR_MAX_SITES];
+  __shared__ RoundSmallArgs s_args;
+  __shared__ int s_fit;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= d; ++k) s_R[k] = (k == 0 || k == d) ? 1 : __ldcg(a.R_out + k);
+    for (int k = 0; k < d; ++k) s_phys[k] = a.phys[k];
+    RoundSmallLayout lay;
+    const size_t need = round_small_layout(s_R, s_phys, d, &lay);
+    s_fit = need > 0 && (int64_t)need <= a.round_cap;
+    if (s_fit) round_small_args(s_args, lay, d, a.core, s_R, s_phys, true, a.tol, a.max_rank, a.R_round, a.status);
+    a.ctl[2] = s_fit;
+  }
+  __syncthreads();
+  if (s_fit) round_small_body(s_args, sm);
 }
 
 }  // namespace
 
-// Runs the compression of Y's bonds d-1 .. 1 on the device. On return Y.R holds the new ranks of
-// the bonds it finished and *next_bond the first bond left for the host-driven sweep (0: all
-// done). Scratch: L (maxbond x 64), two buffers of cap_buf doubles, ctl (>= 4 ints), bar (2).
-int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
-                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond) {
-  *next_bond = Y.d - 1;
+// Queues the compression of Y's bonds d-1 .. 1 on the device (no host synchronisation). With
+// fuse_round, a complete compression is followed in the same launch by the rounding sweeps on
+// CTA 0 (ctl[2] = 1 when they ran; R_round then holds the final ranks, d + 1 values). ctl[0] is
+// the first bond left for the host-driven sweep (0: none); R_dev[k] the new rank of every bond the
+// device finished. Scratch: L (maxbond x 64), two buffers of cap_buf doubles, ctl (>= 4 ints),
+// bar (2). *launched = false when the shapes are outside the kernel's layout (nothing queued).
+int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1,
+                    int64_t cap_buf, unsigned *bar, int *ctl, int64_t *R_dev, bool fuse_round, double tol,
+                    int64_t max_rank, int64_t *R_round, bool *launched) {
+  *launched = false;
   const int d = Y.d;
-  if (d < 2) {
-    *next_bond = 0;
-    return TNR_OK;
-  }
+  if (d < 2) return TNR_OK;
   CompressArgs a;
   a.d = d;
   int64_t qr_need = 0;
@@ -148,6 +179,7 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
   }
   for (int k = 0; k <= d; ++k) a.R[k] = (int)Y.R[k];
   const int64_t qr_cap = std::min<int64_t>(qr_need, 200 * 1024);
+  const int64_t smem = fuse_round ? std::max<int64_t>(qr_cap, (int64_t)kRoundSmallMaxSmem) : qr_cap;
   a.cut = cut;
   a.L = L;
   a.buf[0] = buf0;
@@ -158,11 +190,16 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
   a.bar = bar;
   a.ctl = ctl;
   a.status = status_ptr();
+  a.fuse_round = fuse_round ? 1 : 0;
+  a.tol = tol;
+  a.max_rank = max_rank;
+  a.round_cap = smem;
+  a.R_round = R_round;
   int dev = 0, sms = 0, per_sm = 0;
   TNR_CK(cudaGetDevice(&dev));
   TNR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)qr_cap));
-  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)qr_cap));
+  TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)smem));
+  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)smem));
   if (per_sm < 1) return TNR_OK;
   const int blocks = std::min(64, sms * per_sm);
   TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
@@ -170,19 +207,18 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
     LaunchScope ls(K_QR_PIV, s);
     void *args[] = {&a};
     TNR_CK(cudaLaunchCooperativeKernel((const void *)k_compress, dim3(blocks), dim3(kSmallThreads), args,
-                                       (size_t)qr_cap, s));
+                                       (size_t)smem, s));
   }
-  int64_t h[TNR_MAX_SITES + 2];
-  int hctl = 0;
-  TNR_CK(cudaMemcpyAsync(h, R_dev, sizeof(int64_t) * (d + 1), cudaMemcpyDeviceToHost, s));
-  TNR_CK(cudaMemcpyAsync(&hctl, ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TNR_TRY(read_status(s));
-  *next_bond = hctl;
-  // algorithmic work of the bonds done: r reflectors on w x t plus the explicit w x r Q, and the
-  // absorb 2 rows t r
+  *launched = true;
+  return TNR_OK;
+}
+
+// Algorithmic flops of the bonds the device compressed (recorded once the ranks are known):
+// r reflectors on w x t plus the explicit w x r Q, and the absorb 2 rows t r.
+void compress_record_work(const tnr_mpo &Y, const int64_t *h, int first_host_bond) {
   double work = 0.0;
   int64_t rk1 = 1;
-  for (int k = d - 1; k > hctl; --k) {
+  for (int k = Y.d - 1; k > first_host_bond; --k) {
     const double t = (double)Y.R[k], w = (double)(Y.I[k] * Y.J[k] * rk1), r = (double)h[k];
     const double rows = (double)(Y.R[k - 1] * Y.I[k - 1] * Y.J[k - 1]);
     work += 4 * w * t * r - 2 * (w + t) * r * r + 4 * r * r * r / 3 + 2 * w * r * r - 2 * r * r * r / 3;
@@ -190,7 +226,29 @@ int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *b
     rk1 = h[k];
   }
   stats_work(K_QR_PIV, work);
-  for (int k = hctl + 1; k < d; ++k) Y.R[k] = h[k];
+}
+
+// Runs the compression on the device and reads the ranks back: on return Y.R holds the new ranks
+// of the bonds it finished and *next_bond the first bond left for the host-driven sweep (0: all
+// done).
+int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
+                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond) {
+  *next_bond = Y.d - 1;
+  if (Y.d < 2) {
+    *next_bond = 0;
+    return TNR_OK;
+  }
+  bool launched = false;
+  TNR_TRY(compress_launch(s, Y, cut, L, buf0, buf1, cap_buf, bar, ctl, R_dev, false, 0.0, 0, nullptr, &launched));
+  if (!launched) return TNR_OK;
+  int64_t h[TNR_MAX_SITES + 2];
+  int hctl = 0;
+  TNR_CK(cudaMemcpyAsync(h, R_dev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
+  TNR_CK(cudaMemcpyAsync(&hctl, ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TNR_TRY(read_status(s));
+  *next_bond = hctl;
+  compress_record_work(Y, h, hctl);
+  for (int k = hctl + 1; k < Y.d; ++k) Y.R[k] = h[k];
   return TNR_OK;
 }
 

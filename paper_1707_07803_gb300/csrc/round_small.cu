@@ -8,171 +8,14 @@
 // ranks stay on the device, and each step's small dense factorisation is a device function run
 // by the whole CTA, so there is no launch, host round trip or global-memory staging per bond.
 // The site-1 step of Alg. 5.2/5.3 follows separately.
-#include "cta_linalg.cuh"
+#include "round_small.cuh"
 
 namespace tnr {
 namespace {
 
-struct RoundSmallArgs {
-  int d;
-  double *core[TNR_MAX_SITES];
-  int phys[TNR_MAX_SITES];   // I_k J_k (row multiplicity of core k)
-  int R[TNR_MAX_SITES + 1];  // ranks on entry
-  int off[TNR_MAX_SITES];    // shared-memory offset of core k (doubles)
-  int tmp_off, tmp_cap, rbuf_off, work_off, gram_off;
-  int certify;  // cores 1..d-1 are right-orthonormal on entry: try the no-truncation certificate
-  double tol;
-  int64_t max_rank;
-  int64_t *R_out;  // device, d + 1 ranks on exit
-  int *status;
-};
-
-// No-truncation certificate for the rounding (Section 5.4), valid when cores 1..d-1 are
-// right-orthonormal (as the exact right-to-left compression leaves them). Then the singular
-// values at bond k are those of the left part Y_{<k}, whose Gram matrix follows the recurrence
-// G_1 = C_0^T C_0, G_{k+1} = sum_{a, a', x} C_k(a, x, .) G_k(a, a') C_k(a', x, .), and
-// ||Y||_F^2 = trace(G_1). If every bond keeps sigma_min^2 >= 1 / trace(G_k^{-1}) > delta^2 and
-// no rank exceeds max_rank, both sweeps would keep every singular value and only change the
-// gauge: the rounded tensor is Y itself. A bound that is off by rounding can only keep a
-// component smaller than delta, the truncation error the rounding allows anyway.
-// Returns 1 (uniform over the CTA) when certified.
-__device__ int bonds_certified(const RoundSmallArgs &a, const double *sm, const int *Rs, double *tmp, double *gram,
-                               double *sc) {
-  __shared__ int goff[TNR_MAX_SITES];
-  __shared__ int s_ok;
-  const int d = a.d;
-  if (threadIdx.x == 0) {
-    int off = 0;
-    int ok = 1;
-    for (int k = 1; k < d; ++k) {
-      goff[k] = off;
-      off += Rs[k] * Rs[k];
-      if (Rs[k] > 32 || (a.max_rank > 0 && Rs[k] > a.max_rank)) ok = 0;
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (!s_ok) return 0;
-  // Gram chain
-  cta_tn_sym(gram + goff[1], sm + a.off[0], sm + a.off[0], Rs[0] * a.phys[0], Rs[1]);
-  for (int k = 1; k + 1 < d; ++k) {
-    const int r = Rs[k], w = a.phys[k] * Rs[k + 1];
-    cta_gemm(tmp, gram + goff[k], r, sm + a.off[k], r, r, w, r);  // T = G_k C_k (r x phys r')
-    cta_tn_sym(gram + goff[k + 1], sm + a.off[k], tmp, r * a.phys[k], Rs[k + 1]);
-  }
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < Rs[1]; ++b) t += gram[goff[1] + b + Rs[1] * b];
-    sc[0] = a.tol * a.tol * t / (double)(d - 1);  // delta^2
-  }
-  __syncthreads();
-  const double delta2 = sc[0];
-  // one warp per bond
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 1 + warp; k < d; k += kStepWarps) {
-    const double lb = warp_lambda_min_bound(gram + goff[k], Rs[k]);
-    if (lane == 0 && !(lb > delta2 * (1.0 + 1e-6))) atomicExch(&s_ok, 0);
-  }
-  __syncthreads();
-  return s_ok;
-}
-
 __global__ void __launch_bounds__(kStepThreads) k_round_small(RoundSmallArgs a) {
   extern __shared__ double sm[];
-  __shared__ int Rs[TNR_MAX_SITES + 1];
-  __shared__ double red[8 * kStepWarps];
-  __shared__ double sc[8];
-  const int d = a.d;
-  for (int k = threadIdx.x; k <= d; k += kStepThreads) Rs[k] = a.R[k];
-  for (int k = 0; k < d; ++k) {
-    const int n = a.R[k] * a.phys[k] * a.R[k + 1];
-    const double *src = a.core[k];
-    double *dst = sm + a.off[k];
-    for (int i = threadIdx.x; i < n; i += kStepThreads) dst[i] = src[i];
-  }
-  __syncthreads();
-  double *tmp = sm + a.tmp_off, *rbuf = sm + a.rbuf_off, *work = sm + a.work_off;
-  if (a.certify && bonds_certified(a, sm, Rs, tmp, sm + a.gram_off, sc)) {
-    for (int k = threadIdx.x; k <= d; k += kStepThreads) a.R_out[k] = Rs[k];  // cores unchanged
-    return;
-  }
-  // left-to-right QR sweep: core k = Q R, R absorbed into core k+1
-  for (int k = 0; k + 1 < d; ++k) {
-    const int rows = Rs[k] * a.phys[k], cols = Rs[k + 1];
-    const int nq = rows < cols ? rows : cols;
-    cta_qr(sm + a.off[k], rows, cols, rbuf, work, red, sc);
-    const int w = a.phys[k + 1] * Rs[k + 2];
-    cta_gemm(tmp, rbuf, nq, sm + a.off[k + 1], cols, nq, w, cols);
-    for (int i = threadIdx.x; i < nq * w; i += kStepThreads) sm[a.off[k + 1] + i] = tmp[i];
-    if (threadIdx.x == 0) Rs[k + 1] = nq;
-    __syncthreads();
-  }
-  // ||Y||_F^2 = ||last core||_F^2 (all other cores are left-orthogonal now)
-  double nrm2;
-  {
-    const int n = Rs[d - 1] * a.phys[d - 1] * Rs[d];
-    const double *c = sm + a.off[d - 1];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += kStepThreads) s = fma(c[i], c[i], s);
-    nrm2 = cta_sum(s, n, red, sc);
-  }
-  const double delta2 = a.tol * a.tol * nrm2 / (double)(d - 1);
-  // right-to-left truncating sweep: core k = (U S) V^T, V^T kept, U S absorbed into core k-1
-  for (int k = d - 1; k >= 1; --k) {
-    const int t = Rs[k], w = a.phys[k] * Rs[k + 1];
-    const int r = svd_step_cta(sm + a.off[k], t, w, delta2, a.max_rank, sm + a.off[k], rbuf, work, a.status);
-    cta_absorb_right(sm + a.off[k - 1], Rs[k - 1] * a.phys[k - 1], t, rbuf, r, tmp, a.tmp_cap);
-    if (threadIdx.x == 0) Rs[k] = r;
-    __syncthreads();
-  }
-  for (int k = 0; k < d; ++k) {
-    const int n = Rs[k] * a.phys[k] * Rs[k + 1];
-    const double *src = sm + a.off[k];
-    double *dst = a.core[k];
-    for (int i = threadIdx.x; i < n; i += kStepThreads) dst[i] = src[i];
-  }
-  for (int k = threadIdx.x; k <= d; k += kStepThreads) a.R_out[k] = Rs[k];
-}
-
-struct RoundSmallLayout {
-  int off[TNR_MAX_SITES];
-  int tmp_off, tmp_cap, rbuf_off, work_off, gram_off;
-};
-
-// Shared-memory bytes for the fused sweeps on Y (0 when some dimension is out of range).
-size_t round_small_layout(const tnr_mpo &Y, RoundSmallLayout *lay) {
-  const int d = Y.d;
-  if (d < 2 || d > TNR_MAX_SITES) return 0;
-  int64_t off = 0, maxcore_tail = 1, maxbond = 1, maxwork = 1, gram = 0;
-  for (int k = 0; k < d; ++k) {
-    const int64_t phys = Y.I[k] * Y.J[k];
-    if (phys <= 0 || phys > (1 << 20) || Y.R[k] > kStepMaxN || Y.R[k + 1] > kStepMaxN) return 0;
-    const int64_t n = Y.R[k] * phys * Y.R[k + 1];
-    if (n > (1 << 22)) return 0;
-    lay->off[k] = (int)off;
-    off += (n + 3) & ~int64_t(3);  // 32-byte aligned regions
-    if (k >= 1) {
-      maxcore_tail = std::max(maxcore_tail, n);
-      const int64_t t = Y.R[k], w = phys * Y.R[k + 1];
-      if (std::min(t, w) > kStepMaxN) return 0;
-      maxwork = std::max(maxwork, svd_step_work(t, w));
-    }
-    maxbond = std::max(maxbond, std::max(Y.R[k], Y.R[k + 1]));
-    if (k >= 1) gram += Y.R[k] * Y.R[k];
-  }
-  // tmp: output of the L->R absorb (at most a core of site >= 1) and the row blocks of the
-  // R->L absorb (at least one row of maxbond values)
-  const int64_t tmp_cap = std::max(maxcore_tail, 32 * maxbond);
-  lay->tmp_off = (int)off;
-  lay->tmp_cap = (int)tmp_cap;
-  off += (tmp_cap + 3) & ~int64_t(3);
-  lay->rbuf_off = (int)off;  // R factors (nq x cols) and U S (t x r): at most maxbond^2
-  off += (maxbond * maxbond + 3) & ~int64_t(3);
-  lay->work_off = (int)off;  // SVD-step workspace, or the QR's tau (at most maxbond)
-  off += (std::max(maxwork, maxbond) + 3) & ~int64_t(3);
-  lay->gram_off = (int)off;  // Gram matrices of bonds 1..d-1 for the certificate
-  off += gram;
-  return sizeof(double) * (size_t)off;
+  round_small_body(a, sm);
 }
 
 }  // namespace
@@ -184,26 +27,12 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
                 bool *launched) {
   *launched = false;
   RoundSmallLayout lay;
-  const size_t smem = round_small_layout(Y, &lay);
+  int64_t phys[TNR_MAX_SITES];
+  for (int k = 0; k < Y.d; ++k) phys[k] = Y.I[k] * Y.J[k];
+  const size_t smem = round_small_layout(Y.R, phys, Y.d, &lay);
   if (smem == 0 || smem > kRoundSmallMaxSmem) return TNR_OK;
   RoundSmallArgs a;
-  a.d = Y.d;
-  for (int k = 0; k < Y.d; ++k) {
-    a.core[k] = Y.core[k];
-    a.phys[k] = (int)(Y.I[k] * Y.J[k]);
-    a.off[k] = lay.off[k];
-  }
-  for (int k = 0; k <= Y.d; ++k) a.R[k] = (int)Y.R[k];
-  a.tmp_off = lay.tmp_off;
-  a.tmp_cap = lay.tmp_cap;
-  a.rbuf_off = lay.rbuf_off;
-  a.work_off = lay.work_off;
-  a.gram_off = lay.gram_off;
-  a.certify = certify ? 1 : 0;
-  a.tol = tol;
-  a.max_rank = max_rank;
-  a.R_out = R_dev;
-  a.status = status_ptr();
+  round_small_args(a, lay, Y.d, Y.core, Y.R, phys, certify, tol, max_rank, R_dev, status_ptr());
   TNR_TRY(ensure_dynamic_smem((const void *)k_round_small, smem));
   {
     LaunchScope ls(K_ROUND, s);

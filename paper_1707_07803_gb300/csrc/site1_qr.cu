@@ -29,8 +29,9 @@ constexpr int kS1MaxRowsPerCta = 384;
 struct Site1Args {
   double *core0;          // (1, I1, K, t)
   const int64_t *t_dev;   // t in device memory (rank left there by the rounding), or null
-  int I1, K, t, rpc;      // t: the rank when t_dev is null; rows per CTA
+  int I1, K, t;           // t: the rank when t_dev is null, else its upper bound
   int core_out;           // write Q~ back into core0's layout instead of Qout
+  const int *gate;        // when not null and 0 on the device: do nothing (an earlier step declined)
   double *Gpart;        // gridDim.x partial Grams, K x K each
   double *S, *rdiag;    // the current pass's factor scaled to unit diagonal, and 1 / its diagonal
   double *Rout;         // K x K: R = R2 R1 (column-major, upper)
@@ -137,12 +138,21 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   __shared__ double r2s[kS1MaxK * kS1MaxK];
   __shared__ double rdv[kS1MaxK];
   __shared__ double dinv[kS1MaxK];
+  if (a.gate && __ldcg(a.gate) == 0) return;  // uniform: written by an earlier launch
   const int K = a.K, I1 = a.I1, tid = threadIdx.x, nthr = blockDim.x;
-  const int m = I1 * (a.t_dev ? (int)__ldcg(a.t_dev) : a.t);  // rows; the grid covers the bound
+  const int64_t td = a.t_dev ? __ldcg(a.t_dev) : a.t;
+  if (td < 1 || td > a.t) {  // outside the bound the launch was sized for: leave it to the fallback
+    if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
+    return;
+  }
+  const int m = I1 * (int)td;  // rows; the grid covers the bound
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const int ld = K + 1;
-  const int r0 = blockIdx.x * a.rpc;
-  const int nr = max(0, min(a.rpc, m - r0));
+  // about 16 rows per CTA on the first nb CTAs (the others only take part in the barriers)
+  const int nb = min((int)gridDim.x, max(1, (m + 15) / 16));
+  const int rpc = (m + nb - 1) / nb;
+  const int r0 = blockIdx.x * rpc;
+  const int nr = (int)blockIdx.x < nb ? max(0, min(rpc, m - r0)) : 0;
   if (blockIdx.x == 0 && tid == 0) *a.flag = 0;  // read only after the next grid barrier
   // own rows of A1^T: row i + I1 r, column c <- core (i, c, r); consecutive threads, consecutive rows
   for (int x = tid; x < nr * K; x += nthr) {
@@ -153,8 +163,9 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   const int npair = K * (K + 1) / 2;
   double *Gp = a.Gpart + (size_t)blockIdx.x * K * K;
   for (int pass = 0; pass < 2; ++pass) {
-    // symmetric partial Gram of the own rows
-    for (int e = tid; e < npair; e += nthr) {
+    // symmetric partial Gram of the own rows (CTAs without rows write nothing: only the first nb
+    // partials are summed)
+    for (int e = tid; e < npair && (int)blockIdx.x < nb; e += nthr) {
       int j = 0, base = 0;
       while (base + j + 1 <= e) {
         base += j + 1;
@@ -174,20 +185,19 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     grid_barrier(a.bar, a.status);
     if (blockIdx.x == 0) {
       // fixed-order sum of the partials (deterministic); four loads in flight per step
-      const unsigned nb = gridDim.x;
       const size_t KK = (size_t)K * K;
       constexpr int kE = kS1MaxK * kS1MaxK / kS1Threads;  // elements per thread (4)
       double acc[kE];
 #pragma unroll
       for (int u = 0; u < kE; ++u) acc[u] = 0.0;
-      for (unsigned b0 = 0; b0 < nb; b0 += 8) {
+      for (unsigned b0 = 0; (int)b0 < nb; b0 += 8) {
         double p[8][kE];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
 #pragma unroll
           for (int u = 0; u < kE; ++u) {
             const int e = tid + u * kS1Threads;
-            p[q][u] = (b0 + q < nb && e < K * K) ? __ldcg(a.Gpart + (b0 + q) * KK + e) : 0.0;
+            p[q][u] = ((int)(b0 + q) < nb && e < K * K) ? __ldcg(a.Gpart + (b0 + q) * KK + e) : 0.0;
           }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -272,11 +282,12 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
 // (column-major (I1 t) x K) or, with core_out, back into core0 (1, I1, K, t); R~ (K x K) to Rout;
 // *flag (device) = 1 when the caller must fall back to Householder (core0 is then unchanged).
 // t_dev: when not null the rank is read there on the device and t is only its upper bound.
+// gate: when not null, the kernel does nothing unless *gate != 0 on the device.
 // Scratch: Gpart (gcap doubles), S (K x K), rdiag (K). *launched = false (nothing queued) when the
 // sizes are outside the kernel's layout (K > 32, more rows than 64 CTAs hold) or gcap is too small.
 int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
-                  double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout, int *flag,
-                  unsigned *bar, bool *launched) {
+                  const int *gate, double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout,
+                  int *flag, unsigned *bar, bool *launched) {
   *launched = false;
   const int64_t m = I1 * t;
   if (K < 1 || K > kS1MaxK || m < K || m > (int64_t)64 * kS1MaxRowsPerCta) return TNR_OK;
@@ -284,7 +295,7 @@ int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t 
   TNR_CK(cudaGetDevice(&dev));
   TNR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t nblk = std::min<int64_t>(std::min<int64_t>(64, sms), std::max<int64_t>(1, cdiv(m, 16)));
-  const int64_t rpc = cdiv(m, nblk);
+  const int64_t rpc = std::max<int64_t>(16, cdiv(m, nblk));  // the device's rows per CTA never exceed this
   if (rpc > kS1MaxRowsPerCta || nblk * K * K > gcap) return TNR_OK;
   const size_t smem = sizeof(double) * (size_t)(rpc * (K + 1));
   TNR_TRY(ensure_dynamic_smem((const void *)k_site1_cholqr2, smem));
@@ -294,8 +305,8 @@ int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t 
   a.I1 = (int)I1;
   a.K = (int)K;
   a.t = (int)t;
-  a.rpc = (int)rpc;
   a.core_out = core_out ? 1 : 0;
+  a.gate = gate;
   a.Gpart = Gpart;
   a.S = S;
   a.rdiag = rdiag;

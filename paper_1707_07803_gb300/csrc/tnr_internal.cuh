@@ -199,11 +199,11 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
 // CholeskyQR2 of the site-1 matrix (I1 t) x K of core0 (1, I1, K, t) in one cooperative launch
 // (site1_qr.cu): Q~ to Qout (column-major) or back into core0 (core_out), R~ to Rout; *flag
 // (device) = 1 when the factorisation must be redone by Householder. t_dev (may be null): the
-// rank in device memory, t then being its upper bound. *launched = false when the sizes are
-// outside its layout.
+// rank in device memory, t then being its upper bound; gate (may be null): run only when *gate
+// != 0 on the device. *launched = false when the sizes are outside its layout.
 int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
-                  double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout, int *flag,
-                  unsigned *bar, bool *launched);
+                  const int *gate, double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout,
+                  int *flag, unsigned *bar, bool *launched);
 
 // Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
 int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
@@ -213,6 +213,13 @@ int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
 // host-driven sweep (0: none).
 int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
                     unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond);
+// The same launch without the read-back; with fuse_round a complete compression is followed by the
+// fused rounding sweeps in the same launch (ctl[2] = 1 when they ran). See compress_coop.cu.
+int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1,
+                    int64_t cap_buf, unsigned *bar, int *ctl, int64_t *R_dev, bool fuse_round, double tol,
+                    int64_t max_rank, int64_t *R_round, bool *launched);
+// Records the algorithmic work of the bonds the device compressed, from the ranks h read back.
+void compress_record_work(const tnr_mpo &Y, const int64_t *h, int first_host_bond);
 
 // Small element-wise kernels.
 int copy_matrix_f64(cudaStream_t s, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,

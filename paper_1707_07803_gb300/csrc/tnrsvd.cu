@@ -196,7 +196,7 @@ struct Bufs {
   void *qr = nullptr;       // QR scratch
   void *jac = nullptr;      // Jacobi scratch
   double *norm2 = nullptr;  // device scalar
-  int64_t *rdev = nullptr;  // device rank(s): one per bond for the fused sweeps
+  int64_t *rdev = nullptr;  // device ranks: 2 x (TNR_MAX_SITES + 1) (compression, then rounding)
   unsigned *bar = nullptr;  // grid-barrier state of the cooperative compression
   int *ctl = nullptr;       // its control word
   int64_t cap = 0;          // doubles in tmp, Mq and US
@@ -216,7 +216,7 @@ void carve(Arena &ar, const Limits &L, Bufs &b) {
                                  qrcp_scratch_bound(L.maxcore, std::max(L.maxbond, L.maxsq))));
   b.jac = ar.take<char>(std::max<size_t>(jacobi_scratch(L.maxsq), 256));
   b.norm2 = ar.take<double>(1);
-  b.rdev = ar.take<int64_t>(TNR_MAX_SITES + 1);
+  b.rdev = ar.take<int64_t>(2 * (TNR_MAX_SITES + 1));  // compression ranks, then rounded ranks
   b.bar = ar.take<unsigned>(4);
   b.ctl = ar.take<int>(4);
   b.cap = L.maxcore;
@@ -271,14 +271,6 @@ int compress_rl(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds
     Y.R[k] = r;
   }
   return TNR_OK;
-}
-
-// The compression: the cooperative device-side sweep for every bond it can take, the host-driven
-// sweep for the rest.
-int compress(cudaStream_t s, tnr_mpo &Y, Bufs &b, double cut, bool *all_bonds) {
-  int next = Y.d - 1;
-  TNR_TRY(compress_device(s, Y, cut, b.Rbuf, b.tmp, b.Mq, b.cap, b.bar, b.ctl, b.rdev, &next));
-  return compress_rl(s, Y, b, cut, all_bonds, next);
 }
 
 
@@ -414,12 +406,22 @@ int site1_perm(cudaStream_t s, const double *src, double *dst, int64_t I1, int64
 // when `pending`; the ranks and its fallback flag come back in one sync. When a Cholesky breaks
 // down or the second pass is not near the identity (cond(A1) beyond ~1e8) the QR is redone by the
 // multi-CTA Householder kernel on the unchanged core.
+// Householder QR of the site-1 matrix (the CholeskyQR2 fallback), Y.R exact.
+int site1_householder(cudaStream_t s, tnr_mpo &Y, bool core_out, Bufs &b) {
+  const int64_t I1 = Y.I[0], K = Y.J[0], t = Y.R[1];
+  if (I1 * t < K) return TNR_EINVAL;
+  TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
+  TNR_TRY(thin_qr(s, b.Mq, I1 * t, K, b.Rm, K, b));
+  if (core_out) TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
+  return TNR_OK;
+}
+
 int site1_qr(cudaStream_t s, tnr_mpo &Y, bool pending, bool core_out, Bufs &b) {
   const int64_t I1 = Y.I[0], K = Y.J[0];
   bool launched = false;
   int *flag = b.ctl + 1;
-  TNR_TRY(site1_cholqr2(s, Y.core[0], I1, K, Y.R[1], pending ? b.rdev + 1 : nullptr, core_out, b.US, b.cap, b.Vr,
-                        b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
+  TNR_TRY(site1_cholqr2(s, Y.core[0], I1, K, Y.R[1], pending ? b.rdev + 1 : nullptr, core_out, nullptr, b.US, b.cap,
+                        b.Vr, b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
   int hflag = 1;
   if (launched) {
     TNR_TRY(read_ranks(s, Y, b, pending, &hflag));
@@ -427,24 +429,66 @@ int site1_qr(cudaStream_t s, tnr_mpo &Y, bool pending, bool core_out, Bufs &b) {
     int dummy = 0;
     TNR_TRY(read_ranks(s, Y, b, true, &dummy));
   }
-  const int64_t t = Y.R[1];
-  if (I1 * t < K) return TNR_EINVAL;
+  if (I1 * Y.R[1] < K) return TNR_EINVAL;
   if (!hflag) return TNR_OK;
-  TNR_TRY(site1_perm(s, Y.core[0], b.Mq, I1, K, t, K, 0));
-  TNR_TRY(thin_qr(s, b.Mq, I1 * t, K, b.Rm, K, b));
-  if (core_out) TNR_TRY(site1_perm(s, b.Mq, Y.core[0], I1, K, t, K, 1));
-  return TNR_OK;
+  return site1_householder(s, Y, core_out, b);
+}
+
+// Compression, rounding and the site-1 QR of a product MPO (Section 5.4 and the site-1 step of
+// Algs. 5.2/5.3) with one host round trip when the shapes allow: the cooperative compression runs
+// the rounding sweeps at its end (fused), the CholeskyQR2 of the site-1 matrix follows at once
+// (reading the rounded rank on the device, run only if the rounding ran), and the ranks, the
+// control words and the QR's fallback flag come back together. Whatever a fused stage declined
+// (a bond too wide for the one-CTA QR, cores beyond the rounding's shared memory, a CholeskyQR2
+// that must be redone) continues on the host-driven path from that point.
+int reduce_and_site1(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, double cut, bool core_out, Bufs &b) {
+  bool right_orth = false, pending = false;
+  if (tol > 0.0 && Y.d >= 2) {
+    bool launched = false;
+    int64_t *Rround = b.rdev + (TNR_MAX_SITES + 1);
+    TNR_TRY(compress_launch(s, Y, cut, b.Rbuf, b.tmp, b.Mq, b.cap, b.bar, b.ctl, b.rdev, true, tol, max_rank,
+                            Rround, &launched));
+    if (launched) {
+      bool s1 = false;
+      TNR_TRY(site1_cholqr2(s, Y.core[0], Y.I[0], Y.J[0], Y.R[1], Rround + 1, core_out, b.ctl + 2, b.US, b.cap, b.Vr,
+                            b.Sv, b.Rm, b.Mq, b.ctl + 1, b.bar, &s1));
+      int64_t h[2 * (TNR_MAX_SITES + 1)];
+      int hctl[3] = {0, 0, 0};
+      TNR_CK(cudaMemcpyAsync(h, b.rdev, sizeof(int64_t) * 2 * (TNR_MAX_SITES + 1), cudaMemcpyDeviceToHost, s));
+      TNR_CK(cudaMemcpyAsync(hctl, b.ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
+      TNR_TRY(read_status(s));
+      const int next = hctl[0];
+      compress_record_work(Y, h, next);
+      for (int k = next + 1; k < Y.d; ++k) Y.R[k] = h[k];
+      if (next != 0) {  // a bond too wide for the one-CTA QR: the host-driven sweep continues
+        TNR_TRY(compress_rl(s, Y, b, cut, &right_orth, next));
+        TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b, &pending));
+        return site1_qr(s, Y, pending, core_out, b);
+      }
+      if (hctl[2] == 0) {  // compressed cores beyond the fused rounding's shared memory
+        TNR_TRY(round_sweeps(s, Y, tol, max_rank, true, b, &pending));
+        return site1_qr(s, Y, pending, core_out, b);
+      }
+      const int64_t *hr = h + (TNR_MAX_SITES + 1);
+      for (int k = 0; k <= Y.d; ++k) Y.R[k] = hr[k];
+      if (Y.I[0] * Y.R[1] < Y.J[0]) return TNR_EINVAL;
+      if (!s1) return site1_qr(s, Y, false, core_out, b);
+      if (hctl[1]) return site1_householder(s, Y, core_out, b);
+      return TNR_OK;
+    }
+    TNR_TRY(compress_rl(s, Y, b, cut, &right_orth, Y.d - 1));
+  }
+  TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b, &pending));
+  if (Y.I[0] * Y.R[1] < Y.J[0] && !pending) return TNR_EINVAL;
+  return site1_qr(s, Y, pending, core_out, b);
 }
 
 // MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4). Y is a tall matrix MPO with K
 // columns on site 1 (Y.J[0] = K, Y.J[k>0] = 1). Rout (K x K) may be null.
 int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int64_t max_rank, Bufs &b,
                        bool mixed_product = false) {
-  bool right_orth = false, pending = false;
-  if (tol > 0.0) TNR_TRY(compress(s, Y, b, compress_cut(tol, mixed_product), &right_orth));
-  TNR_TRY(round_sweeps(s, Y, tol, max_rank, right_orth, b, &pending));
-  if (Y.I[0] * Y.R[1] < Y.J[0] && !pending) return TNR_EINVAL;
-  TNR_TRY(site1_qr(s, Y, pending, true, b));  // A1^T = Q~ R~, Q~ back into the site-1 core
+  // A1^T = Q~ R~ with Q~ back into the site-1 core
+  TNR_TRY(reduce_and_site1(s, Y, tol, max_rank, compress_cut(tol, mixed_product), true, b));
   if (Rout) TNR_CK(cudaMemcpyAsync(Rout, b.Rm, sizeof(double) * Y.J[0] * Y.J[0], cudaMemcpyDeviceToDevice, s));
   return TNR_OK;
 }
@@ -454,10 +498,7 @@ int orthogonalize_impl(cudaStream_t s, tnr_mpo &Y, double *Rout, double tol, int
 // kout columns into V1 (core (1, J1, kout, t2)). Z's other cores become V's cores.
 int mpo_svd_impl(cudaStream_t s, tnr_mpo &Z, double tol, int64_t max_rank, Bufs &b, double *Wout, double *Sout,
                  double *V1, int64_t kout, int64_t v1cap) {
-  bool right_orth = false, pending = false;
-  if (tol > 0.0) TNR_TRY(compress(s, Z, b, compress_cut(tol, false), &right_orth));
-  TNR_TRY(round_sweeps(s, Z, tol, max_rank, right_orth, b, &pending));
-  TNR_TRY(site1_qr(s, Z, pending, false, b));  // M^T ((J1 t) x K) = Q~ R~
+  TNR_TRY(reduce_and_site1(s, Z, tol, max_rank, compress_cut(tol, false), false, b));  // M^T = Q~ R~
   const int64_t J1 = Z.I[0], K = Z.J[0], t = Z.R[1];
   const int64_t m = J1 * t;
   if (J1 * kout * t > v1cap) return TNR_ENOMEM;

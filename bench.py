@@ -29,17 +29,18 @@ import workloads as W  # noqa: E402
 METRIC = "TNrSVD solves/s (2^20 x 2^20 MPO, sigma_j = 0.7^j, k=16 p=16 q=2)"
 DTYPES = {"mixed": "bf16x3/f64", "fp64": "f64"}
 KERNELS = {
-    "qr": "k_gram_rm + k_chol_small + k_trsm_warp (site-1 CholeskyQR2) / k_qr_coop (Householder fallback)",
+    "qr": "k_site1_cholqr2 (site-1 CholeskyQR2, one cooperative launch) / k_qr_coop (Householder fallback)",
     "qr_small": "k_qr_small / k_qr_small_tpc (one-CTA FP64 Householder QR, explicit Q)",
-    "qr_piv": "k_compress (cooperative exact compression sweep: one-CTA pivoted FP64 QR per bond + grid-wide absorb)",
+    "qr_piv": "k_compress (cooperative exact compression sweep: one-CTA pivoted FP64 QR per bond + grid-wide "
+              "absorb, then the fused rounding sweeps / certificate on CTA 0)",
     "svd": "k_svd_step / k_jacobi (FP64 truncated SVD step, one-sided Jacobi)",
     "gemm": "k_gemm / k_gemm_tiny (FP64 GEMM)",
     "contract": "k_contract (per-site MPO product)",
 }
 UNIT = "solves/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the named kernel, as recorded in
-# profiles/ (k_compress_c2.md); reported only while that kernel is unchanged.
-TRAFFIC_BYTES = {}
+# profiles/; reported only while that kernel is unchanged (empty: not yet re-captured).
+TRAFFIC_BYTES = {"qr_piv": 2.79e6}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 

@@ -449,21 +449,25 @@ def adjoint_main(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default per workload: prescribed 200, sparse 20, batched 20, adjoint 2)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--workload", default="prescribed", choices=["prescribed", "batched", "adjoint", "sparse"],
                     help="prescribed: one 2^20 x 2^20 solve per step (default); batched: a batch of "
-                         "independent Gaussian-core MPOs per step (tnr_solve_batched); adjoint: forward "
-                         "and backward of the differentiable solve per step")
+                         "independent Gaussian-core MPOs per step (persistent kernel); adjoint: forward "
+                         "and backward of the differentiable solve per step; sparse: Alg. 4.1 conversion "
+                         "and the block-sparse TNrSVD per step")
     ap.add_argument("--fd-entries", type=int, default=16)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--batch-impl", default="persistent", choices=["persistent", "pool"],
                     help="batched workload: persistent kernel (default) or the host worker pool")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {"prescribed": 200, "sparse": 20, "batched": 20, "adjoint": 2}[args.workload]
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batched":

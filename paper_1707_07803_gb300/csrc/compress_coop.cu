@@ -228,28 +228,4 @@ void compress_record_work(const tnr_mpo &Y, const int64_t *h, int first_host_bon
   stats_work(K_QR_PIV, work);
 }
 
-// Runs the compression on the device and reads the ranks back: on return Y.R holds the new ranks
-// of the bonds it finished and *next_bond the first bond left for the host-driven sweep (0: all
-// done).
-int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
-                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond) {
-  *next_bond = Y.d - 1;
-  if (Y.d < 2) {
-    *next_bond = 0;
-    return TNR_OK;
-  }
-  bool launched = false;
-  TNR_TRY(compress_launch(s, Y, cut, L, buf0, buf1, cap_buf, bar, ctl, R_dev, false, 0.0, 0, nullptr, &launched));
-  if (!launched) return TNR_OK;
-  int64_t h[TNR_MAX_SITES + 2];
-  int hctl = 0;
-  TNR_CK(cudaMemcpyAsync(h, R_dev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
-  TNR_CK(cudaMemcpyAsync(&hctl, ctl, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TNR_TRY(read_status(s));
-  *next_bond = hctl;
-  compress_record_work(Y, h, hctl);
-  for (int k = hctl + 1; k < Y.d; ++k) Y.R[k] = h[k];
-  return TNR_OK;
-}
-
 }  // namespace tnr

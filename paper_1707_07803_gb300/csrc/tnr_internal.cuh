@@ -208,13 +208,10 @@ int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t 
 // Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
 int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
 
-// Exact right-to-left compression of a product MPO as one cooperative kernel (compress_coop.cu).
-// Y.R gets the ranks of the bonds it finished; *next_bond is the first bond left for the
-// host-driven sweep (0: none).
-int compress_device(cudaStream_t s, tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1, int64_t cap_buf,
-                    unsigned *bar, int *ctl, int64_t *R_dev, int *next_bond);
-// The same launch without the read-back; with fuse_round a complete compression is followed by the
-// fused rounding sweeps in the same launch (ctl[2] = 1 when they ran). See compress_coop.cu.
+// Exact right-to-left compression of a product MPO as one cooperative kernel (compress_coop.cu),
+// queued without a read-back; with fuse_round a complete compression is followed by the fused
+// rounding sweeps in the same launch (ctl[2] = 1 when they ran). ctl[0]: the first bond left to the
+// host-driven sweep (0: none); R_dev: the ranks of the bonds the device finished.
 int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1,
                     int64_t cap_buf, unsigned *bar, int *ctl, int64_t *R_dev, bool fuse_round, double tol,
                     int64_t max_rank, int64_t *R_round, bool *launched);

@@ -105,16 +105,6 @@ __global__ void k_site1_perm(const double *__restrict__ src, double *__restrict_
   }
 }
 
-// Site-1 core (1, I1, K, t) -> row-major A1^T ((I1 t) x K): element (i, c, r) -> c + K (i + I1 r).
-__global__ void k_site1_rowmajor(const double *__restrict__ src, double *__restrict__ dst, int64_t I1, int64_t K,
-                                 int64_t t) {
-  const unsigned total = (unsigned)(I1 * K * t), kk = (unsigned)K, uI1 = (unsigned)I1;
-  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const unsigned i = idx % uI1, c = (idx / uI1) % kk, r = idx / (uI1 * kk);
-    dst[c + kk * (i + uI1 * r)] = src[idx];
-  }
-}
-
 __global__ void __launch_bounds__(1024) k_norm2(const double *__restrict__ x, int64_t n, double *out, int *status) {
   __shared__ double red[32];
   double s = 0.0;

@@ -118,3 +118,32 @@ def test_solve_c2_prescribed_fp64():
     c = W.c2_prescribed()
     S, So, err = _check_solve(c["A"], c["k"], c["p"], c["q"], c["seed"], c["tol"], c["max_rank"])
     assert sv_rel_err(S, c["sigma"][:16]) <= 1e-10
+
+
+def test_rank_deficient_site1_falls_back_to_householder():
+    # A of exact rank 3 with K = 8 columns: the site-1 matrices of Y = A Omega and of the later
+    # products have rank 3, so their CholeskyQR2 must hand over to the Householder QR
+    K = 8
+    sigma = np.array([1.0, 0.5, 0.25, 0, 0, 0, 0, 0])
+    A, _, _ = W.prescribed_mpo(3, 4, 16, [2, 2, 2], K, 3, sigma)
+    T.stats_reset()
+    U, S, V = T.tnr_solve(dev_mpo(A), 4, 4, 1, 5, tol=1e-13, max_rank=0)
+    torch.cuda.synchronize()
+    classes = T.stats_classes()
+    householder = T.stats(classes.index("qr_small"))[0] + max(0, T.stats(classes.index("qr"))[0] - 4)
+    assert householder >= 1
+    S = S.cpu().numpy()
+    Uo, So, Vo = ot.tnrsvd(A, 4, 4, 1, 5, tol=1e-13, max_rank=0)
+    assert sv_rel_err(S, So) <= FP64_SV_TOL
+    np.testing.assert_allclose(S[:3], sigma[:3], rtol=1e-12)
+    # the rank-3 part of the singular vectors (the rest spans an arbitrary null direction)
+    Uh, Vh = host_cores(U), host_cores(V)
+    np.testing.assert_allclose(np.abs(np.diag(om.inner(Uh, Uo)))[:3], 1.0, atol=1e-9)
+    np.testing.assert_allclose(np.abs(np.diag(om.inner(Vh, Vo)))[:3], 1.0, atol=1e-9)
+
+
+def test_wide_bonds_continue_on_the_host_path():
+    # product bonds wider than the one-CTA pivoted QR takes (w > 64): the cooperative compression
+    # hands the rest of the sweep to the host-driven kernels, and the rounding runs per bond
+    A = W.gaussian_mpo(12, [4] * 6, [4] * 6, [1, 8, 8, 8, 8, 8, 1], scale=lambda k, sh: 1.0 / np.sqrt(sh[1] * sh[0]))
+    _check_solve(A, 8, 8, 1, seed=7, tol=1e-13, max_rank=16)

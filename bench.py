@@ -160,13 +160,16 @@ def reference_arm(args):
     return 0
 
 
-BATCH_METRIC = "TNrSVD solves/s, batch of independent Gaussian-core MPOs (d 8-12, I=J in {2,4}, k in {4,8}, p=k, q=1)"
+def batched_metric(d, ranks, ks):
+    return (f"TNrSVD solves/s, batch of independent Gaussian-core MPOs (d {d[0]}-{d[1]}, I=J in {{2,4}}, "
+            f"ranks {ranks[0]}-{ranks[1]}, k in {set(ks)}, p=k, q=1)")
 
 
-def batched_config(n):
-    probs = W.batched_gaussian(0, n, d_range=BATCH_D, rank_range=BATCH_RANKS, ks=BATCH_KS)
-    cfg = {"workload": f"{n} independent Gaussian-core MPOs, d uniform {BATCH_D[0]}-{BATCH_D[1]}, I=J in {{2,4}}, "
-                       f"ranks uniform {BATCH_RANKS[0]}-{BATCH_RANKS[1]}, k in {set(BATCH_KS)}, p=k, q=1, "
+def batched_config(n, d=None, ranks=None, ks=None):
+    d, ranks, ks = d or BATCH_D, ranks or BATCH_RANKS, ks or BATCH_KS
+    probs = W.batched_gaussian(0, n, d_range=d, rank_range=ranks, ks=ks)
+    cfg = {"workload": f"{n} independent Gaussian-core MPOs, d uniform {d[0]}-{d[1]}, I=J in {{2,4}}, "
+                       f"ranks uniform {ranks[0]}-{ranks[1]}, k in {set(ks)}, p=k, q=1, "
                        "max_rank=K, seed 0",
            "precision": "products BF16 x3 on tcgen05 / FP32 accumulate, sweeps + SVD + B in FP64",
            "global_batch": n, "seq_len": 0, "l2": "flushed between timed steps (256 MiB write)",
@@ -192,7 +195,8 @@ def batched_main(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    probs, cfg = batched_config(args.batch)
+    bd, br, bk = tuple(args.batch_d), tuple(args.batch_ranks), tuple(args.batch_ks)
+    probs, cfg = batched_config(args.batch, bd, br, bk)
     dprobs = [dict(pr, A=T.Mpo.from_numpy(pr["A"], device=dev)) for pr in probs]
     persistent = args.batch_impl == "persistent"
     if persistent:
@@ -276,7 +280,7 @@ def batched_main(args):
     ms_step = total_ms / args.steps
     achieved = fp64_flops_per_batch / (ms_step * 1e-3) / 1e9
     line = {
-        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": batched_metric(bd, br, bk), "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES["mixed"], "data": "synthetic", "config": cfg,
         "e2e": {"value": n * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -328,7 +332,7 @@ def sparse_main(args):
         step()
     torch.cuda.synchronize()
     T.stats_reset()
-    T.stats_enable(1 << classes.index("contract"))
+    T.stats_enable(sum(1 << classes.index(c) for c in ("contract", "gemm", "qr")))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sampler = ClockSampler(local)
     sampler.start()
@@ -345,10 +349,29 @@ def sparse_main(args):
     clocks = sampler.stop()
     sp_launches, sp_ms = T.stats(classes.index("contract"))
     sp_bytes = T.stats_work(classes.index("contract"))
+    fp64 = {c: (T.stats(classes.index(c)), T.stats_work(classes.index(c))) for c in ("gemm", "qr")}
     T.stats_enable(0)
     peaks = read_peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
     achieved = (sp_bytes / max(sp_launches, 1)) / (sp_ms / max(sp_launches, 1) * 1e-3) / 1e9 if sp_launches else 0.0
+    spmm = {"kernel": "k_spmm_rows (products over the compact lists of the block form)", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "launches_per_step": sp_launches / args.steps, "avg_launch_us": 1000 * sp_ms / max(sp_launches, 1),
+            "share_of_step": sp_ms / max(total_ms, 1e-9),
+            "note": "algorithmic bytes per product: 12 B per nonzero (index + value) + 4 B per row "
+                    "pointer + 8 B per right-hand-side element read once + 8 B per output element written"}
+    # the dominant class: the FP64 symmetric Grams of the tall CholeskyQR2 (GEMM class)
+    (g_launches, g_ms), g_flops = fp64["gemm"]
+    g_rate = g_flops / (g_ms * 1e-3) / 1e9 if g_ms > 0 else 0.0
+    gram = {"kernel": "k_gram_rm + k_gemm (symmetric Grams of the 2^20 x K CholeskyQR2, FP64 GEMMs)", "class": "gemm",
+            "bound": "alu", "achieved": g_rate, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+            "frac": g_rate / FP64_NOMINAL_GFLOPS, "traffic": None,
+            "launches_per_step": g_launches / args.steps, "avg_launch_us": 1000 * g_ms / max(g_launches, 1),
+            "share_of_step": g_ms / max(total_ms, 1e-9),
+            "note": "algorithmic FP64 flops recorded per launch (n K (K+1) per symmetric Gram, 2mnk per GEMM)"}
     line = {
         "metric": SPARSE_METRIC, "value": args.steps / (total_ms / 1000.0), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -358,14 +381,8 @@ def sparse_main(args):
                                f"conversion (Alg. 4.1) + TNrSVD k={k} p={p} q={q} via the block form",
                    "global_batch": 1, "seq_len": 0, "l2": "flushed between timed steps (256 MiB write)"},
         "clocks": clocks,
-        "roofline": {"kernel": "k_spmm_rows (products over the compact lists of the block form)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "peak_source": "hbm_gbs of MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "launches_per_step": sp_launches / args.steps, "avg_launch_us": 1000 * sp_ms / max(sp_launches, 1),
-                     "share_of_step": sp_ms / max(total_ms, 1e-9),
-                     "note": "algorithmic bytes per product: 12 B per nonzero (index + value) + 4 B per row "
-                             "pointer + 8 B per right-hand-side element read once + 8 B per output element written"},
+        "roofline": gram if g_ms >= sp_ms else spmm,
+        "spmm": spmm,
     }
     print(json.dumps(line))
     return 0
@@ -465,6 +482,9 @@ def main():
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--batch-impl", default="persistent", choices=["persistent", "pool"],
                     help="batched workload: persistent kernel (default) or the host worker pool")
+    ap.add_argument("--batch-d", type=int, nargs=2, default=list(BATCH_D), help="batched: range of d")
+    ap.add_argument("--batch-ranks", type=int, nargs=2, default=list(BATCH_RANKS), help="batched: range of ranks")
+    ap.add_argument("--batch-ks", type=int, nargs="+", default=list(BATCH_KS), help="batched: set of k")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"prescribed": 200, "sparse": 20, "batched": 20, "adjoint": 2}[args.workload]

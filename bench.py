@@ -613,7 +613,7 @@ def main():
                      "launches_per_step": qr_launches / args.steps, "avg_launch_us": 1000 * qr_avg_ms,
                      "share_of_step": qr_ms / max(total_ms, 1e-9),
                      "class_ms_one_solve": {k: round(v, 4) for k, v in per_class.items() if v > 0}},
-        "contraction": ({"kernel": "k_tc_gemm (tcgen05 BF16 x3, FP32 accumulate)", "bound": "tensor",
+        "contraction": ({"kernel": "k_tc_gemm_tma (TMA-staged FP64 boxes via cp.async.bulk.tensor, tcgen05 BF16 x3, FP32 accumulate in TMEM)", "bound": "tensor",
                          "launches_per_step": tc_launches / args.steps,
                          "avg_launch_us": 1000 * tc_ms / max(tc_launches, 1),
                          "achieved": (tc_flops / max(tc_launches, 1)) / (tc_ms / max(tc_launches, 1) * 1e-3) / 1e12

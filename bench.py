@@ -134,6 +134,18 @@ def run_oracle_sample(c, budget_s):
     return n / el, n, el, S
 
 
+def replicas_rate(total_ms, steps, world, dev, dist=None):
+    """Whole-job rate of `world` independent replicas, each having run `steps` steps in its own
+    `total_ms`: the slowest rank (all_reduce MAX) bounds the job. Returns (steps/s, max ms)."""
+    import torch
+
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return world * steps / (max_ms / 1000.0), max_ms
+
+
 def reference_arm(args):
     """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -559,10 +571,7 @@ def main():
     tc_launches, tc_ms = T.stats(tc_cls)
     tc_flops = T.stats_work(tc_cls)
     T.stats_enable(0)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    value, max_ms = replicas_rate(total_ms, args.steps, world, dev, dist)
 
     # accuracy of this run against the exact singular values
     S = plan.S.cpu().numpy()
@@ -590,21 +599,15 @@ def main():
         e1.synchronize()
         d2h = sum(o.numel() * 8 for o in outs)
         e2e_ms += e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_value, e2e_ms = replicas_rate(e2e_ms, args.steps, world, dev, dist)
     del host
-
-    value = world * args.steps / (max_ms / 1000.0)
     qr_avg_ms = qr_ms / max(qr_launches, 1)
     achieved_gflops = (qr_flops / max(qr_launches, 1)) / (qr_avg_ms * 1e-3) / 1e9 if qr_launches else 0.0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic", "config": cfg,
-        "e2e": {"value": world * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"kernel": KERNELS.get(dom, dom), "class": dom, "bound": "alu",
                      "achieved": achieved_gflops, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",

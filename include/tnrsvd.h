@@ -239,6 +239,17 @@ int tnr_batch_config(void *handle, int32_t *grid, int32_t *ctas_per_sm, int64_t 
 int tnr_batch_destroy(void *handle);
 
 /* ---------------------------------------------------------------------------------------
+ * Self-test of the bounded device waits (no counterpart in the paper). Every spin-wait of the
+ * library's kernels on work of another CTA (grid barriers, mbarriers) is capped and reports
+ * TNR_ETIMEOUT instead of waiting forever. This entry makes such a wait run out on purpose: two
+ * CTAs enter a grid barrier, one returns without arriving, the other gives up after spin_cap
+ * polls (1 <= spin_cap <= the library's cap). Returns TNR_ETIMEOUT (the expected outcome; the
+ * device status word is cleared again and the context stays usable), TNR_OK if the wait somehow
+ * completed, TNR_EINVAL for a bad cap. Synchronises `stream`.
+ * ------------------------------------------------------------------------------------- */
+int tnr_selftest_wait_timeout(int64_t spin_cap, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * TNrSVD of a sparse matrix given in the block form of Alg. 4.1 (R, X, digits as produced by
  * tnr_sparse_fill; any block order). The MPO of Alg. 4.1 has rank R
  * at every bond (Lemma 4.2), so the products of Section 5.2 are applied straight from the

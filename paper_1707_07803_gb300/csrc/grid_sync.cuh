@@ -1,7 +1,7 @@
 // Bounded grid-wide barrier for cooperative launches (all CTAs co-resident by construction).
 // bar[0] counts arrivals, bar[1] is the generation; the last CTA to arrive resets the count and
-// advances the generation. A waiter gives up after kSpinCap polls and records TNR_ETIMEOUT
-// instead of waiting forever. bar must be zeroed before the launch.
+// advances the generation. A waiter gives up after spin_cap polls (kSpinCap by default) and
+// records TNR_ETIMEOUT instead of waiting forever. bar must be zeroed before the launch.
 #pragma once
 
 #include <cuda/atomic>
@@ -10,7 +10,7 @@
 
 namespace tnr {
 
-static __device__ void grid_barrier(unsigned *bar, int *status) {
+static __device__ void grid_barrier(unsigned *bar, int *status, long long spin_cap = kSpinCap) {
   __syncthreads();
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned, cuda::thread_scope_device> count(bar[0]), gen(bar[1]);
@@ -22,7 +22,7 @@ static __device__ void grid_barrier(unsigned *bar, int *status) {
     } else {
       long long spins = 0;
       while (gen.load(cuda::memory_order_acquire) == my) {
-        if (++spins > kSpinCap) {
+        if (++spins > spin_cap) {
           set_status(status, TNR_ETIMEOUT);
           break;
         }

@@ -101,6 +101,7 @@ _SIGS = {
     "tnr_batch_collect": (ctypes.c_int, [_P, _P]),
     "tnr_batch_config": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _I64P]),
     "tnr_batch_destroy": (ctypes.c_int, [_P]),
+    "tnr_selftest_wait_timeout": (ctypes.c_int, [_I64, _P]),
     "tnr_sparse_solve_workspace": (ctypes.c_int, [_I64, _I64, _I64, _I32, _I64P, _I64P, _I32, _I32, _SZP]),
     "tnr_sparse_solve": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _I32, _I64P, _I64P, _I32, _I32, _I32,
                                         ctypes.c_uint64, _I32, _P, _P, _P, _P, ctypes.c_size_t, _P]),

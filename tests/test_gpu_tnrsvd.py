@@ -147,3 +147,13 @@ def test_wide_bonds_continue_on_the_host_path():
     # hands the rest of the sweep to the host-driven kernels, and the rounding runs per bond
     A = W.gaussian_mpo(12, [4] * 6, [4] * 6, [1, 8, 8, 8, 8, 8, 1], scale=lambda k, sh: 1.0 / np.sqrt(sh[1] * sh[0]))
     _check_solve(A, 8, 8, 1, seed=7, tol=1e-13, max_rank=16)
+
+
+def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
+    # a grid-barrier wait that nothing satisfies gives up after its poll cap with TNR_ETIMEOUT
+    lib = T.load()
+    assert lib.tnr_selftest_wait_timeout(1000, T._stream()) == -7
+    assert lib.tnr_selftest_wait_timeout(0, T._stream()) == -1
+    # the status word is clear again and the next solve is unaffected
+    A = W.gaussian_mpo(4, [4, 4, 4, 4], [4, 4, 4, 4], [1, 3, 3, 3, 1], scale=1 / np.sqrt(12))
+    _check_solve(A, 4, 4, 1, seed=2, tol=1e-14, max_rank=0)

@@ -62,3 +62,58 @@ def test_host_side_argument_errors(lib):
     assert lib.tnr_solve_batched(1, P, 64, ctypes.c_void_p(256), 256, None) == -1  # more workers than status slots
     assert lib.tnr_solve_batched(1, P, 1, ctypes.c_void_p(256), 100, None) == -1  # stride not a multiple of 256
     assert lib.tnr_solve_batched(0, None, 0, None, 0, None) == 0  # empty batch
+
+
+def _host_problem(T, d, x, r, k, p):
+    """A tnr_problem whose pointers are placeholders: only host-side planning may look at it."""
+    A = T.tnr_mpo()
+    A.d = d
+    for i in range(d):
+        A.I[i] = A.J[i] = x
+        A.core[i] = 4096 * (i + 1)
+    for i in range(d + 1):
+        A.R[i] = 1 if i in (0, d) else r
+    K, m, prod = k + p, 0, 1
+    while prod < K:  # leading sites merged until prod I >= K (Section 6.3)
+        prod *= x
+        m += 1
+    dm = d - max(m, 1) + 1
+    U, V = T.tnr_mpo(), T.tnr_mpo()
+    for M in (U, V):
+        M.d = dm
+        for i in range(dm):
+            M.core[i] = 1 << 20
+            M.cap[i] = 1 << 20
+    return A, U, V
+
+
+def test_persistent_batch_planning_on_the_host(lib):
+    """tnr_batch_workspace plans every problem on the host (no device memory is touched), and
+    tnr_batch_create refuses bad batch arguments before any device work."""
+    import ctypes
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    keep = []
+    probs = (T.tnr_problem * 2)()
+    for i, (d, x, r, k) in enumerate([(4, 2, 2, 2), (5, 4, 3, 4)]):
+        A, U, V = _host_problem(T, d, x, r, k, k)
+        keep += [A, U, V]
+        P = probs[i]
+        P.A, P.U, P.V = ctypes.pointer(A), ctypes.pointer(U), ctypes.pointer(V)
+        P.k, P.p, P.q, P.seed = k, k, 1, i
+        P.S = 1 << 20
+        P.opts = T._opts(1e-12, 2 * k, T.TNR_MIXED)
+    b1, b2 = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.tnr_batch_workspace(1, probs, ctypes.byref(b1)) == 0 and b1.value > 0
+    assert lib.tnr_batch_workspace(2, probs, ctypes.byref(b2)) == 0 and b2.value > b1.value
+    probs[1].k = 1 << 20  # K = k + p beyond prod I: refused by the plan
+    assert lib.tnr_batch_workspace(2, probs, ctypes.byref(b2)) == -1
+    h = ctypes.c_void_p(0)
+    ws = ctypes.c_void_p(1 << 30)
+    assert lib.tnr_batch_create(0, probs, 0, ws, 1 << 20, None, ctypes.byref(h)) == -1  # empty batch
+    assert lib.tnr_batch_create(1, probs, 1 << 3, ws, 1 << 20, None, ctypes.byref(h)) == -1  # unknown flag bit
+    assert lib.tnr_batch_create(1, probs, 0, None, 1 << 20, None, ctypes.byref(h)) == -1  # no workspace
+    assert not h.value
+    assert lib.tnr_batch_launch(None, None) == -1 and lib.tnr_batch_collect(None, None) == -1
+    assert lib.tnr_batch_destroy(None) == 0

@@ -57,12 +57,18 @@ enum tnr_precision {
                     tol, the QR sweeps and the SVDs in float64 */
 };
 
-/* MPO descriptor (host memory). For inputs only d, I, J, R and core are read. For outputs
- * the caller sets d, I, J, core and cap (capacity of each core buffer in elements); the
+/* Element type of an MPO's cores. Outputs are always TNR_F64. TNR_F32 inputs are accepted by
+ * tnr_solve / tnr_solve_query (A) and tnr_diff_forward / tnr_diff_backward (A, dA): the cores
+ * are widened to float64 on the device (exactly) before the method runs; every other entry point
+ * requires TNR_F64 (TNR_EINVAL otherwise). */
+enum tnr_dtype { TNR_F64 = 0, TNR_F32 = 1 };
+
+/* MPO descriptor (host memory). For inputs only d, dtype, I, J, R and core are read. For
+ * outputs the caller sets d, I, J, core and cap (capacity of each core buffer in elements); the
  * library writes the achieved ranks into R. */
 typedef struct tnr_mpo {
   int32_t d;
-  int32_t reserved;
+  int32_t dtype; /* enum tnr_dtype; 0 (TNR_F64) for every buffer the library writes */
   int64_t I[TNR_MAX_SITES];
   int64_t J[TNR_MAX_SITES];
   int64_t R[TNR_MAX_SITES + 1];

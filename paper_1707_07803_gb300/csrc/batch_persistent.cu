@@ -589,6 +589,7 @@ int64_t pow2_ceil(int64_t v) {
 // descriptor. cost: an estimate of its FP64 work, for the queue order.
 int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cost, int64_t *bucket) {
   if (!pr.A || !pr.U || !pr.V || !pr.S || pr.k < 1 || pr.p < 0 || pr.q < 0) return TNR_EINVAL;
+  if (pr.A->dtype != TNR_F64) return TNR_EINVAL;  // the kernel reads float64 cores
   if (pr.opts.precision != TNR_FP64 && pr.opts.precision != TNR_MIXED) return TNR_EINVAL;
   const int64_t K = (int64_t)pr.k + pr.p;
   Plan P;

@@ -815,6 +815,7 @@ extern "C" int tnr_diff_forward(const tnr_mpo *A, int32_t k, int32_t p, int32_t 
   if (!A || !S || !tape || k < 1 || p < 0 || q < 0) return TNR_EINVAL;
   *tape = nullptr;
   if (A->d < 1 || A->d > TNR_MAX_SITES || A->R[0] != 1 || A->R[A->d] != 1) return TNR_EINVAL;
+  if (A->dtype != TNR_F64 && A->dtype != TNR_F32) return TNR_EINVAL;
   for (int i = 0; i < A->d; ++i)
     if (A->I[i] < 1 || A->J[i] < 1 || A->R[i + 1] < 1 || !A->core[i]) return TNR_EINVAL;
   const int64_t K = (int64_t)k + p;
@@ -836,6 +837,24 @@ extern "C" int tnr_diff_forward(const tnr_mpo *A, int32_t k, int32_t p, int32_t 
   if (!T) return TNR_ENOMEM;
   T->mem.s = s;
   T->A = *A;
+  if (A->dtype == TNR_F32) {  // the tape keeps float64 copies of the cores (exact widening)
+    double *dst[TNR_MAX_SITES];
+    for (int i = 0; i < A->d; ++i) {
+      dst[i] = T->mem.take(A->R[i] * A->I[i] * A->J[i] * A->R[i + 1]);
+      if (!dst[i]) {
+        T->mem.release();
+        delete T;
+        return TNR_ENOMEM;
+      }
+    }
+    const int rc = widen_cores(s, *A, dst, &T->A);
+    if (rc != TNR_OK) {
+      T->mem.release();
+      cudaStreamSynchronize(s);
+      delete T;
+      return rc;
+    }
+  }
   T->m = m;
   T->d = A->d - m + 1;
   T->K = K;
@@ -868,10 +887,30 @@ extern "C" int tnr_diff_forward(const tnr_mpo *A, int32_t k, int32_t p, int32_t 
 extern "C" int tnr_diff_backward(void *tape, const double *dS, tnr_mpo *dA, void *stream) {
   if (!tape || !dS || !dA) return TNR_EINVAL;
   DiffTape *T = static_cast<DiffTape *>(tape);
-  if (dA->d != T->A.d) return TNR_EINVAL;
+  if (dA->d != T->A.d || (dA->dtype != TNR_F64 && dA->dtype != TNR_F32)) return TNR_EINVAL;
   for (int i = 0; i < T->A.d; ++i)
     if (!dA->core[i]) return TNR_EINVAL;
-  return diff_backward(static_cast<cudaStream_t>(stream), *T, dS, dA);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dA->dtype == TNR_F64) return diff_backward(s, *T, dS, dA);
+  // float32 gradients: computed in float64 scratch, then rounded into the caller's cores
+  tnr::Pool scratch;
+  scratch.s = s;
+  tnr_mpo g = *dA;
+  g.dtype = TNR_F64;
+  for (int i = 0; i < T->A.d; ++i) {
+    g.core[i] = scratch.take(T->A.R[i] * T->A.I[i] * T->A.J[i] * T->A.R[i + 1]);
+    if (!g.core[i]) {
+      scratch.release();
+      return TNR_ENOMEM;
+    }
+  }
+  int rc = diff_backward(s, *T, dS, &g);
+  for (int i = 0; i < T->A.d && rc == TNR_OK; ++i)
+    rc = tnr::narrow_to_f32(s, g.core[i], reinterpret_cast<float *>(dA->core[i]),
+                            T->A.R[i] * T->A.I[i] * T->A.J[i] * T->A.R[i + 1]);
+  scratch.release();
+  const cudaError_t e = cudaStreamSynchronize(s);
+  return rc != TNR_OK ? rc : tnr::check_cuda(e);
 }
 
 extern "C" void tnr_diff_free(void *tape, void *stream) {

@@ -133,7 +133,14 @@ struct Plan {
   Limits L;
 };
 
-int validate_input(const tnr_mpo *A);
+// Dims, ranks and core pointers of an input MPO; allow_f32: TNR_F32 cores are accepted.
+int validate_input(const tnr_mpo *A, bool allow_f32 = false);
+// Element count of every core of A (for the float64 copies of TNR_F32 inputs).
+int64_t mpo_elems(const tnr_mpo &A);
+// Widens A's float32 cores into float64 buffers (dst[k] holds core k); *out = A with those cores.
+int widen_cores(cudaStream_t s, const tnr_mpo &A, double *const *dst, tnr_mpo *out);
+// y (float32) <- x (float64), n elements (round to nearest).
+int narrow_to_f32(cudaStream_t s, const double *x, float *y, int64_t n);
 // Merge count, merged dimensions, bond caps (Thm 3.2 bounds and max_rank) and buffer bounds of
 // a solve with K = k + p columns.
 int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P);

@@ -105,6 +105,16 @@ __global__ void k_site1_perm(const double *__restrict__ src, double *__restrict_
   }
 }
 
+__global__ void k_widen(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+__global__ void k_narrow(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 __global__ void __launch_bounds__(1024) k_norm2(const double *__restrict__ x, int64_t n, double *out, int *status) {
   __shared__ double red[32];
   double s = 0.0;
@@ -163,8 +173,9 @@ int64_t core_elems(const tnr_mpo &M, int k) { return M.R[k] * M.I[k] * M.J[k] * 
 
 }  // namespace
 
-int validate_input(const tnr_mpo *A) {
+int validate_input(const tnr_mpo *A, bool allow_f32) {
   if (!A || A->d < 1 || A->d > TNR_MAX_SITES) return TNR_EINVAL;
+  if (A->dtype != TNR_F64 && !(allow_f32 && A->dtype == TNR_F32)) return TNR_EINVAL;
   if (A->R[0] != 1 || A->R[A->d] != 1) return TNR_EINVAL;
   for (int k = 0; k < A->d; ++k) {
     if (A->I[k] < 1 || A->J[k] < 1 || A->R[k + 1] < 1 || !A->core[k]) return TNR_EINVAL;
@@ -563,7 +574,7 @@ int64_t tall_bound(const int64_t *dims, int d, int64_t K, int b) {
 }  // namespace
 
 int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
-  TNR_TRY(validate_input(A));
+  TNR_TRY(validate_input(A, true));
   if (K < 1) return TNR_EINVAL;
   double pi = 1, pj = 1;
   int m = 0;
@@ -634,9 +645,38 @@ int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
   return TNR_OK;
 }
 
+int64_t mpo_elems(const tnr_mpo &A) {
+  int64_t n = 0;
+  for (int k = 0; k < A.d; ++k) n += A.R[k] * A.I[k] * A.J[k] * A.R[k + 1];
+  return n;
+}
+
+int widen_cores(cudaStream_t s, const tnr_mpo &A, double *const *dst, tnr_mpo *out) {
+  *out = A;
+  out->dtype = TNR_F64;
+  for (int k = 0; k < A.d; ++k) {
+    const int64_t n = A.R[k] * A.I[k] * A.J[k] * A.R[k + 1];
+    {
+      LaunchScope ls(K_MISC, s);
+      k_widen<<<grid_for(n), 256, 0, s>>>(reinterpret_cast<const float *>(A.core[k]), dst[k], n);
+    }
+    TNR_CK(cudaGetLastError());
+    out->core[k] = dst[k];
+  }
+  return TNR_OK;
+}
+
+int narrow_to_f32(cudaStream_t s, const double *x, float *y, int64_t n) {
+  if (n <= 0) return TNR_OK;
+  LaunchScope ls(K_MISC, s);
+  k_narrow<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
+}
+
 namespace {
 
 struct SolveBufs {
+  double *widened[TNR_MAX_SITES] = {nullptr};  // float64 copies of TNR_F32 input cores
   double *merged = nullptr, *merge_tmp = nullptr;
   double *omega = nullptr;
   double *P0[TNR_MAX_SITES], *P1[TNR_MAX_SITES];
@@ -644,7 +684,9 @@ struct SolveBufs {
   Bufs b;
 };
 
-void carve_solve(Arena &ar, const Plan &P, int64_t K, SolveBufs &sb) {
+void carve_solve(Arena &ar, const Plan &P, int64_t K, SolveBufs &sb, const tnr_mpo *A) {
+  if (A->dtype == TNR_F32)
+    for (int k = 0; k < A->d; ++k) sb.widened[k] = ar.take<double>(A->R[k] * A->I[k] * A->J[k] * A->R[k + 1]);
   if (P.m > 1) {
     sb.merged = ar.take<double>(P.merged_elems);
     sb.merge_tmp = ar.take<double>(P.merged_elems);
@@ -693,11 +735,16 @@ int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q
   ar.base = static_cast<char *>(ws);
   ar.size = ws_bytes;
   SolveBufs sb;
-  carve_solve(ar, P, K, sb);
+  carve_solve(ar, P, K, sb, A);
   if (!ar.ok || !ws) return TNR_ENOMEM;
   // output capacities
-  if (U->d != P.d || V->d != P.d) return TNR_EINVAL;
+  if (U->d != P.d || V->d != P.d || U->dtype != TNR_F64 || V->dtype != TNR_F64) return TNR_EINVAL;
   TNR_TRY(reset_status(s));
+  tnr_mpo A64;
+  if (A->dtype == TNR_F32) {  // widened to float64 on the device, exactly
+    TNR_TRY(widen_cores(s, *A, sb.widened, &A64));
+    A = &A64;
+  }
 
   // A' : merged operator
   tnr_mpo Am;
@@ -876,7 +923,7 @@ extern "C" int tnr_solve_query(const tnr_mpo *A, int32_t k, int32_t p, const tnr
   TNR_TRY(make_plan(A, K, opts, P));
   Arena ar;
   SolveBufs sb;
-  carve_solve(ar, P, K, sb);
+  carve_solve(ar, P, K, sb, A);
   if (ws_bytes) *ws_bytes = ar.off;
   for (tnr_mpo *M : {U_shape, V_shape}) {
     if (!M) continue;

@@ -35,7 +35,7 @@ class TnrError(RuntimeError):
 class tnr_mpo(ctypes.Structure):
     _fields_ = [
         ("d", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
         ("I", ctypes.c_int64 * MAX_SITES),
         ("J", ctypes.c_int64 * MAX_SITES),
         ("R", ctypes.c_int64 * (MAX_SITES + 1)),
@@ -165,8 +165,12 @@ def _need_cuda(*ts):
 # ----------------------------------------------------------------------------------------
 # MPO container
 # ----------------------------------------------------------------------------------------
+TNR_F64, TNR_F32 = 0, 1
+
+
 class Mpo:
-    """Dims, ranks and flat float64 CUDA core buffers of an MPO (layout of include/tnrsvd.h)."""
+    """Dims, ranks and flat CUDA core buffers of an MPO (layout of include/tnrsvd.h): float64, or
+    float32 for the inputs that accept it (tnr_solve, the differentiable solve)."""
 
     def __init__(self, I, J, R, cores):
         self.I = [int(x) for x in I]
@@ -184,6 +188,10 @@ class Mpo:
     def to_struct(self, caps=None):
         m = tnr_mpo()
         m.d = self.d
+        dts = {c.dtype for c in self.cores if c is not None}
+        if dts - {torch.float64, torch.float32} or len(dts) > 1:
+            raise ValueError("cores must all be float64 or all float32")
+        m.dtype = TNR_F32 if dts == {torch.float32} else TNR_F64
         for k in range(self.d):
             m.I[k], m.J[k] = self.I[k], self.J[k]
             m.core[k] = self.cores[k].data_ptr() if self.cores[k] is not None else 0
@@ -193,11 +201,13 @@ class Mpo:
         return m
 
     @staticmethod
-    def from_numpy(cores, device="cuda"):
-        """Logical numpy cores (R, I, J, R') -> flat device buffers in memory order."""
+    def from_numpy(cores, device="cuda", dtype=None):
+        """Logical numpy cores (R, I, J, R') -> flat device buffers in memory order (float64, or
+        dtype=numpy.float32 for float32 input cores)."""
         import numpy as np
 
-        flat = [torch.from_numpy(np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1, order="F")))
+        dt = np.float64 if dtype is None else dtype
+        flat = [torch.from_numpy(np.ascontiguousarray(np.asarray(c, dtype=dt).reshape(-1, order="F")))
                 .to(device) for c in cores]
         I = [c.shape[1] for c in cores]
         J = [c.shape[2] for c in cores]

@@ -80,3 +80,22 @@ def test_backward_twice_and_free():
     g2 = torch.autograd.grad(S.sum(), A.cores)
     for a, b in zip(g1, g2):
         assert torch.equal(a, b)
+
+
+def test_float32_cores_give_the_float64_values_and_rounded_gradients():
+    # FP32 Gaussian cores (the shape of the differentiable workload): the forward widens them
+    # exactly, so S equals the float64 run's; the gradients are the float64 ones rounded to float32
+    A_host = [c.astype(np.float32) for c in W.gaussian_mpo(8, [4] * 4, [4] * 4, [1, 3, 3, 3, 1], scale=0.3)]
+    A32 = T.Mpo.from_numpy(A_host, dtype=np.float32)
+    A64 = T.Mpo.from_numpy([c.astype(np.float64) for c in A_host])
+    for A in (A32, A64):
+        for c in A.cores:
+            c.requires_grad_(True)
+    S32 = T.tnrsvd_values(A32, 4, 4, 1, 5)
+    S64 = T.tnrsvd_values(A64, 4, 4, 1, 5)
+    assert torch.equal(S32, S64)
+    g32 = torch.autograd.grad(S32.sum(), A32.cores)
+    g64 = torch.autograd.grad(S64.sum(), A64.cores)
+    for a, b in zip(g32, g64):
+        assert a.dtype == torch.float32
+        torch.testing.assert_close(a, b.to(torch.float32), rtol=1e-6, atol=1e-30)

@@ -157,3 +157,21 @@ def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
     # the status word is clear again and the next solve is unaffected
     A = W.gaussian_mpo(4, [4, 4, 4, 4], [4, 4, 4, 4], [1, 3, 3, 3, 1], scale=1 / np.sqrt(12))
     _check_solve(A, 4, 4, 1, seed=2, tol=1e-14, max_rank=0)
+
+
+def test_float32_input_cores_are_widened_exactly():
+    # TNR_F32 cores: the solve widens them to float64 on the device, so it equals the solve of the
+    # same values held in float64, bit for bit
+    A = W.gaussian_mpo(5, [4] * 5, [4] * 5, [1, 4, 4, 4, 4, 1], scale=0.25)
+    A32 = [c.astype(np.float32) for c in A]
+    for precision in (T.TNR_FP64, T.TNR_MIXED):
+        U1, S1, V1 = T.tnr_solve(T.Mpo.from_numpy(A32, dtype=np.float32), 4, 4, 1, 3, tol=1e-13, precision=precision)
+        U2, S2, V2 = T.tnr_solve(T.Mpo.from_numpy([c.astype(np.float64) for c in A32]), 4, 4, 1, 3, tol=1e-13,
+                                 precision=precision)
+        torch.cuda.synchronize()
+        assert torch.equal(S1, S2)
+        assert all(np.array_equal(a, b) for a, b in zip(host_cores(U1), host_cores(U2)))
+    # the persistent batch reads float64 cores only
+    pr = dict(A=T.Mpo.from_numpy(A32, dtype=np.float32), k=4, p=4, q=1, seed=3, tol=1e-13, max_rank=8)
+    with pytest.raises(T.TnrError):
+        T.PersistentBatch([pr], precision=T.TNR_FP64)

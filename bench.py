@@ -417,8 +417,8 @@ def adjoint_main(args):
     d, rank, k, p, q, seed, n_sv = 12, 16, 16, 16, 2, 3, 16
     A_host = W.gaussian_mpo(0, [4] * d, [4] * d, [1] + [rank] * (d - 1) + [1],
                             scale=lambda kk, sh: 1.0 / np.sqrt(sh[1] * sh[0]))
-    A_host = [c.astype(np.float32).astype(np.float64) for c in A_host]  # FP32 Gaussian cores
-    A = T.Mpo.from_numpy(A_host, device=dev)
+    A_host = [c.astype(np.float32).astype(np.float64) for c in A_host]  # FP32 Gaussian cores (values)
+    A = T.Mpo.from_numpy(A_host, device=dev, dtype=np.float32)  # passed as float32 (TNR_F32)
     for c in A.cores:
         c.requires_grad_(True)
 

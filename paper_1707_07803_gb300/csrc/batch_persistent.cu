@@ -28,7 +28,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <tuple>
 #include <vector>
 
 #include <cuda_bf16.h>

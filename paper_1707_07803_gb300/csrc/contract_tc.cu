@@ -330,7 +330,6 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm_tma(const __grid_constan
   for (int i = threadIdx.x; i < a.BN; i += kTcThreads) s_ccol[i] = i < a.N ? a.ccol(i) : -1;
   // box coordinates of this CTA's 128 rows: (row within the group, group)
   const int r0c = (int)(m0 % a.rows0), g0c = (int)(m0 / a.rows0);
-  const int bg = kTcM / a.box_r0;
   __syncthreads();
 
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.BN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
@@ -405,7 +404,6 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm_tma(const __grid_constan
     __syncthreads();
     if (s_abort) break;
   }
-  (void)bg;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!s_abort) {
     const int64_t rowoff = s_crow[warp * 32 + lane];

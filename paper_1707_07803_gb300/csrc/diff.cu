@@ -644,7 +644,7 @@ const double *site_core(const DiffTape &T, int k) { return k == 0 ? T.merged[T.m
 tnr::Site site_dims(const DiffTape &T, int k) { return {T.RA[k], T.Im[k], T.Jm[k], T.RA[k + 1]}; }
 
 // product op(A') (x) X where X has ranks XR, K columns on site 1; output into a new record's inputs
-int run_product(cudaStream_t s, DiffTape &T, int trans, const double *const *X, const int64_t *XR, bool x_is_omega,
+int run_product(cudaStream_t s, DiffTape &T, int trans, const double *const *X, const int64_t *XR,
                 tnr::OrthRec &rec) {
   const int d = T.d;
   rec.d = d;
@@ -664,7 +664,6 @@ int run_product(cudaStream_t s, DiffTape &T, int trans, const double *const *X, 
     rec.phys[k] = Nx * Kx;
   }
   rec.Rin[d] = 1;
-  (void)x_is_omega;
   T.prods.push_back(cores);
   return TNR_OK;
 }
@@ -707,7 +706,7 @@ int diff_forward(cudaStream_t s, DiffTape &T, uint64_t seed, double *S_out) {
   T.recs.assign(nrec, OrthRec());
   auto fwd = [&](int i, int trans, const double *const *X, const int64_t *XR, bool svd) -> int {
     OrthRec &rec = T.recs[i];
-    TNR_TRY(run_product(s, T, trans, X, XR, i == 0, rec));
+    TNR_TRY(run_product(s, T, trans, X, XR, rec));
     rec.svd = svd;
     int rc = orth_fwd(s, rec, T.mem, tmp);
     tmp.release();

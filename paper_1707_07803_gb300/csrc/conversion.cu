@@ -387,8 +387,8 @@ extern "C" int tnr_sparse_count(int64_t nrows, int64_t ncols, int64_t nnz, const
   }
   TNR_CK(cudaGetLastError());
   int32_t total = 0;
-  TNR_CK(cudaMemcpyAsync(&total, tile_off + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  int st = read_status(s);  // synchronises
+  const ReadBack rb[1] = {{&total, tile_off + ntiles, sizeof(int32_t)}};
+  int st = read_back(s, rb, 1);  // synchronises once
   if (st != TNR_OK) return st;
   *R_out = total;
   return TNR_OK;
@@ -492,8 +492,8 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   }
   TNR_CK(cudaGetLastError());
   int32_t total = 0;
-  TNR_CK(cudaMemcpyAsync(&total, tile_off + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  int st = read_status(s);  // synchronises
+  const ReadBack rb[1] = {{&total, tile_off + ntiles, sizeof(int32_t)}};
+  int st = read_back(s, rb, 1);  // synchronises once
   if (st != TNR_OK) return st;
   *R_out = total;
   if (total > max_blocks) return TNR_ENOMEM;  // X and digits untouched

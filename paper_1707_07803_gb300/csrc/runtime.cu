@@ -69,19 +69,67 @@ int check_cuda(cudaError_t e) {
   return TNR_ECUDA;
 }
 
-int read_status(cudaStream_t s) {
-  int *p = status_ptr();
-  if (!p) return TNR_ECUDA;
-  int h = 0;
-  TNR_CK(cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+// Per host thread pinned staging for read-backs: copies into pinned memory stay asynchronous, so
+// several read-backs and the status word cost one synchronisation instead of one each.
+namespace {
+struct PinnedStage {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+  void *get(size_t need) {
+    if (need > bytes) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      bytes = 0;
+      const size_t want = need < 4096 ? 4096 : need;
+      if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+      bytes = want;
+    }
+    return p;
+  }
+};
+thread_local PinnedStage t_stage;
+}  // namespace
+
+int read_back(cudaStream_t s, const ReadBack *items, int n) {
+  int *st = status_ptr();
+  if (!st) return TNR_ECUDA;
+  size_t total = sizeof(int);
+  for (int i = 0; i < n; ++i) total += (items[i].bytes + 15) & ~size_t(15);
+  char *stage = static_cast<char *>(t_stage.get(total));
+  if (!stage) {  // no pinned memory: the plain path, one synchronising copy each
+    for (int i = 0; i < n; ++i)
+      TNR_CK(cudaMemcpyAsync(items[i].dst, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));
+    int h = 0;
+    TNR_CK(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TNR_CK(cudaStreamSynchronize(s));
+    if (h != 0) TNR_CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+    return h;
+  }
+  size_t off = sizeof(int);
+  for (int i = 0; i < n; ++i) {
+    TNR_CK(cudaMemcpyAsync(stage + off, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));
+    off += (items[i].bytes + 15) & ~size_t(15);
+  }
+  TNR_CK(cudaMemcpyAsync(stage, st, sizeof(int), cudaMemcpyDeviceToHost, s));
   TNR_CK(cudaStreamSynchronize(s));
-  if (h != 0) {
-    int zero = 0;
-    TNR_CK(cudaMemcpyAsync(p, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  off = sizeof(int);
+  for (int i = 0; i < n; ++i) {
+    memcpy(items[i].dst, stage + off, items[i].bytes);
+    off += (items[i].bytes + 15) & ~size_t(15);
+  }
+  int h = 0;
+  memcpy(&h, stage, sizeof(int));
+  if (h != 0) {  // clear the word for the next call (rare path)
+    TNR_CK(cudaMemsetAsync(st, 0, sizeof(int), s));
     TNR_CK(cudaStreamSynchronize(s));
   }
   return h;
 }
+
+int read_status(cudaStream_t s) { return read_back(s, nullptr, 0); }
 
 int reset_status(cudaStream_t s) {
   int *p = status_ptr();

@@ -85,6 +85,14 @@ int check_cuda_at(cudaError_t e, const char *file, int line);  // same, naming t
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current device.
 int ensure_dynamic_smem(const void *func, size_t bytes);
 int read_status(cudaStream_t s);  // synchronises s, returns and clears the device status word
+// Copies device regions to host memory and reads (and clears) the status word with one
+// synchronisation of s (pinned staging); returns the status.
+struct ReadBack {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+int read_back(cudaStream_t s, const ReadBack *items, int n);
 int reset_status(cudaStream_t s);
 
 #define TNR_CK(expr)                                           \

@@ -224,8 +224,8 @@ void carve(Arena &ar, const Limits &L, Bufs &b) {
 }
 
 int d2h_rank(cudaStream_t s, const int64_t *rdev, int64_t *r) {
-  TNR_CK(cudaMemcpyAsync(r, rdev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  int st = read_status(s);
+  const ReadBack rb[1] = {{r, rdev, sizeof(int64_t)}};
+  int st = read_back(s, rb, 1);
   return st;
 }
 
@@ -386,9 +386,8 @@ int round_sweeps(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, bool 
 // Reads the ranks the fused rounding left in b.rdev and the site-1 fallback flag (one sync).
 int read_ranks(cudaStream_t s, tnr_mpo &Y, Bufs &b, bool pending, int *hflag) {
   int64_t R[TNR_MAX_SITES + 1];
-  if (pending) TNR_CK(cudaMemcpyAsync(R, b.rdev, sizeof(int64_t) * (Y.d + 1), cudaMemcpyDeviceToHost, s));
-  TNR_CK(cudaMemcpyAsync(hflag, b.ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TNR_TRY(read_status(s));
+  const ReadBack rb[2] = {{hflag, b.ctl + 1, sizeof(int)}, {R, b.rdev, sizeof(int64_t) * (Y.d + 1)}};
+  TNR_TRY(read_back(s, rb, pending ? 2 : 1));
   if (pending)
     for (int k = 0; k <= Y.d; ++k) Y.R[k] = R[k];
   return TNR_OK;
@@ -455,9 +454,8 @@ int reduce_and_site1(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, d
                             b.Sv, b.Rm, b.Mq, b.ctl + 1, b.bar, &s1));
       int64_t h[2 * (TNR_MAX_SITES + 1)];
       int hctl[3] = {0, 0, 0};
-      TNR_CK(cudaMemcpyAsync(h, b.rdev, sizeof(int64_t) * 2 * (TNR_MAX_SITES + 1), cudaMemcpyDeviceToHost, s));
-      TNR_CK(cudaMemcpyAsync(hctl, b.ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
-      TNR_TRY(read_status(s));
+      const ReadBack rb[2] = {{h, b.rdev, sizeof(int64_t) * 2 * (TNR_MAX_SITES + 1)}, {hctl, b.ctl, sizeof(hctl)}};
+      TNR_TRY(read_back(s, rb, 2));
       const int next = hctl[0];
       compress_record_work(Y, h, next);
       for (int k = next + 1; k < Y.d; ++k) Y.R[k] = h[k];

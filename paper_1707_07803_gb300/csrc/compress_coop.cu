@@ -5,17 +5,22 @@
 // bond) as L Q_k by a column-pivoted QR of M_k^T that stops at the rounding-level cutoff; Q_k
 // (orthonormal rows) becomes core k and L is absorbed into core k-1. Each bond needs the rank of
 // the previous one, so the host-driven version reads a rank back and launches again for every
-// bond. Here the whole sweep runs on the device: CTA 0 factors M_k in shared memory (the
-// thread-per-column pivoted QR of qr_tpc.cuh) while the other CTAs wait at a grid barrier, then
-// every CTA takes part in the absorb C_{k-1} L, and the next bond starts after a second barrier.
+// bond. Here the whole sweep runs on the device: the first thread-block cluster factors M_k in
+// shared memory (the cluster-distributed pivoted QR of qr_cluster.cuh: each of its CTAs owns a
+// block of columns; without clusters, CTA 0 runs the thread-per-column QR of qr_tpc.cuh) while
+// the other CTAs wait at a grid barrier; then the other CTAs absorb L into core k-1 while the
+// cluster forms Q_k (only L is on the sweep's critical path), and the next bond starts after a
+// second barrier.
 // Ranks stay in device memory and are read back once at the end. A bond whose matrix does not
 // fit the one-CTA QR (more than 64 rows, or beyond the shared-memory capacity) ends the kernel
 // with the state of the host-driven sweep just before that bond, which the host then continues.
 // The barriers spin with a bound (kSpinCap polls) and report TNR_ETIMEOUT instead of waiting
 // forever; co-residency of all CTAs is guaranteed by the cooperative launch.
 #include <algorithm>
+#include <atomic>
 
 #include "grid_sync.cuh"
+#include "qr_cluster.cuh"
 #include "qr_tpc.cuh"
 #include "round_small.cuh"
 #include "tnr_internal.cuh"
@@ -32,7 +37,7 @@ struct CompressArgs {
   double *L;             // t x r factor of the current bond (ld t)
   double *buf[2];        // absorbed cores (ping-pong), cap_buf doubles each
   int64_t cap_buf;
-  int64_t qr_cap;        // shared-memory bytes available to the QR
+  int64_t qr_cap;        // shared-memory bytes available to the QR (per CTA)
   int64_t *R_out;        // ranks on exit (d + 1)
   unsigned *bar;         // [0] arrivals, [1] generation
   int *ctl;              // [0] first bond left to the host (0: none), [2] rounding done here
@@ -41,7 +46,7 @@ struct CompressArgs {
   int fuse_round;
   double tol;
   int64_t max_rank;
-  int64_t round_cap;     // dynamic shared-memory bytes available to it
+  int64_t round_cap;     // dynamic shared-memory bytes of the launch (the rounding may use all)
   int64_t *R_round;      // ranks after the rounding (d + 1)
 };
 
@@ -50,11 +55,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   const int d = a.d;
   const double *cur = a.core[d - 1];  // M_k (t x w, ld t)
   int rk1 = 1;                        // compressed rank of bond k+1
+  const unsigned C = cluster_nctarank();  // CTAs of the factoring cluster (1: launched without)
   // the rounding has not run (yet): a later launch gated on this word must do nothing
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl[2] = 0;
   for (int k = d - 1; k >= 1; --k) {
     const int t = a.R[k], w = a.phys[k] * rk1;
-    const bool fits = w <= 64 && qr_tpc_bytes(w, t) <= a.qr_cap;
+    const bool fits = w <= 64 && (C > 1 ? qr_cluster_bytes(w, t, C) : qr_tpc_bytes(w, t)) <= a.qr_cap;
     if (!fits) {  // leave M_k in core k and bonds <= k to the host-driven sweep
       double *dst = a.core[k];
       if (cur != dst)
@@ -64,8 +70,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl[0] = k;  // ranks of bonds > k are in R_out
       return;
     }
-    if (blockIdx.x == 0) {  // M_k^T (w x t) = Q~ R~ P^T: core k <- Q~^T (r x w), L <- R~^T (t x r)
-      QrSmallArgs q;
+    int r_qr = 0;
+    QrSmallArgs q;
+    if (blockIdx.x < C) {  // M_k^T (w x t) = Q~ R~ P^T: core k <- Q~^T (r x w), L <- R~^T (t x r)
       q.src = cur;
       q.lds = t;
       q.m = w;
@@ -80,43 +87,63 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
       q.R = a.L;
       q.ldr = t;
       q.r_out = a.R_out + k;
-      qr_tpc_cta(q, sm);
+      if (C > 1)
+        r_qr = qr_cluster_cta(q, sm);
+      else
+        qr_tpc_cta(q, sm);
     }
     grid_barrier(a.bar, a.status);
-    // data written by other CTAs is read through L2 (__ldcg), never from a possibly stale L1 line
-    const int r = (int)__ldcg(a.R_out + k);
-    // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r); L staged in shared memory (the
-    // QR's buffer is free now), the core streamed from global memory
-    const int rows = a.R[k - 1] * a.phys[k - 1];
-    const double *C = a.core[k - 1];
+    // data written by other CTAs is read through L2 (__ldcg), never from a possibly stale L1 line;
+    // the factoring cluster keeps its own rank, so its CTAs always agree on the next bond's shape
+    // (and execute the same cluster barriers)
+    const int r = (C > 1 && blockIdx.x < C) ? r_qr : (int)__ldcg(a.R_out + k);
+    const double *Cc = a.core[k - 1];
     double *out = a.buf[k & 1];
-    double *Ls = sm;
-    const bool staged = (int64_t)t * r * (int64_t)sizeof(double) <= a.qr_cap;
-    if (staged)
-      for (int x = threadIdx.x; x < t * r; x += blockDim.x) Ls[x] = __ldcg(a.L + x);
-    __syncthreads();
-    // four lanes per output, each summing every fourth term, combined by shuffles (fixed order:
-    // deterministic); eight outputs per warp, consecutive rows (coalesced core reads)
-    const int lane = threadIdx.x & 31, part = lane & 3;
-    const int64_t nout = (int64_t)rows * r;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 8 < nout; g += warps) {
-      const int64_t x = g * 8 + (lane >> 2);
-      double acc = 0.0;
-      if (x < nout) {
-        const int i = (int)(x % rows), c = (int)(x / rows);
-        const double *Ci = C + i;
-        if (staged) {
-          const double *l = Ls + t * c;
-          for (int j = part; j < t; j += 4) acc = fma(Ci[(int64_t)rows * j], l[j], acc);
-        } else {
-          const double *l = a.L + (int64_t)t * c;
-          for (int j = part; j < t; j += 4) acc = fma(Ci[(int64_t)rows * j], __ldcg(l + j), acc);
+    const unsigned first = C > 1 ? C : 0;  // CTAs that absorb: [first, gridDim.x)
+    if (blockIdx.x < first) {
+      qr_cluster_form_q(q, sm, r);  // core k <- Q~^T, beside the absorb
+    } else {
+      // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r); L staged in shared memory (the
+      // QR's buffer is free now), the core streamed from global memory
+      const int rows = a.R[k - 1] * a.phys[k - 1];
+      double *Ls = sm;
+      const bool staged = (int64_t)t * r * (int64_t)sizeof(double) <= a.round_cap;
+      if (staged)
+        for (int x = threadIdx.x; x < t * r; x += blockDim.x) Ls[x] = __ldcg(a.L + x);
+      __syncthreads();
+      // four lanes per output, lane `part` summing terms j = part mod 4 in four interleaved
+      // chains (16 terms apart, so eight core loads are in flight per lane), combined in a fixed
+      // order (deterministic); eight outputs per warp, consecutive rows (coalesced core reads)
+      const int lane = threadIdx.x & 31, part = lane & 3;
+      const int64_t nout = (int64_t)rows * r;
+      const int64_t warps = ((int64_t)(gridDim.x - first) * blockDim.x) >> 5;
+      for (int64_t g = ((int64_t)(blockIdx.x - first) * blockDim.x + threadIdx.x) >> 5; g * 8 < nout; g += warps) {
+        const int64_t x = g * 8 + (lane >> 2);
+        double acc = 0.0;
+        if (x < nout) {
+          const int i = (int)(x % rows), c = (int)(x / rows);
+          const double *Ci = Cc + i;
+          const double *l = staged ? Ls + t * c : a.L + (int64_t)t * c;
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+          int j = part;
+#pragma unroll 2
+          for (; j + 12 < t; j += 16) {
+            const double c0 = Ci[(int64_t)rows * j], c1 = Ci[(int64_t)rows * (j + 4)];
+            const double c2 = Ci[(int64_t)rows * (j + 8)], c3 = Ci[(int64_t)rows * (j + 12)];
+            const double l0 = staged ? l[j] : __ldcg(l + j), l1 = staged ? l[j + 4] : __ldcg(l + j + 4);
+            const double l2 = staged ? l[j + 8] : __ldcg(l + j + 8), l3 = staged ? l[j + 12] : __ldcg(l + j + 12);
+            a0 = fma(c0, l0, a0);
+            a1 = fma(c1, l1, a1);
+            a2 = fma(c2, l2, a2);
+            a3 = fma(c3, l3, a3);
+          }
+          for (; j < t; j += 4) a0 = fma(Ci[(int64_t)rows * j], staged ? l[j] : __ldcg(l + j), a0);
+          acc = (a0 + a1) + (a2 + a3);
         }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (x < nout && part == 0) out[x] = acc;
       }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (x < nout && part == 0) out[x] = acc;
     }
     grid_barrier(a.bar, a.status);
     cur = out;
@@ -161,6 +188,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
 // the first bond left for the host-driven sweep (0: none); R_dev[k] the new rank of every bond the
 // device finished. Scratch: L (maxbond x 64), two buffers of cap_buf doubles, ctl (>= 4 ints),
 // bar (2). *launched = false when the shapes are outside the kernel's layout (nothing queued).
+// Cluster size of the factoring cluster; whether the cooperative launch with clusters is
+// available is decided at the first launch of the process (kept: -1 unknown, 0 refused, else C).
+constexpr int kCompressCluster = 4;
+static_assert(kCompressCluster * kQrWarps <= 32 && kCompressCluster <= kClusterMaxCtas,
+              "one warp reads every candidate of the cluster; portable cluster size");
+static std::atomic<int> g_cluster_mode{-1};
+
+int compress_cluster_size() { return g_cluster_mode.load() > 0 ? g_cluster_mode.load() : 1; }
+
 int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1,
                     int64_t cap_buf, unsigned *bar, int *ctl, int64_t *R_dev, bool fuse_round, double tol,
                     int64_t max_rank, int64_t *R_round, bool *launched) {
@@ -169,23 +205,18 @@ int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, dou
   if (d < 2) return TNR_OK;
   CompressArgs a;
   a.d = d;
-  int64_t qr_need = 0;
   for (int k = 0; k < d; ++k) {
     const int64_t phys = Y.I[k] * Y.J[k];
     if (phys > (1 << 20) || Y.R[k] > (1 << 20) || Y.R[k] * phys * Y.R[k + 1] > cap_buf) return TNR_OK;
     a.core[k] = Y.core[k];
     a.phys[k] = (int)phys;
-    if (k >= 1) qr_need = std::max(qr_need, qr_tpc_bytes(std::min<int64_t>(64, phys * Y.R[k + 1]), Y.R[k]));
   }
   for (int k = 0; k <= d; ++k) a.R[k] = (int)Y.R[k];
-  const int64_t qr_cap = std::min<int64_t>(qr_need, 200 * 1024);
-  const int64_t smem = fuse_round ? std::max<int64_t>(qr_cap, (int64_t)kRoundSmallMaxSmem) : qr_cap;
   a.cut = cut;
   a.L = L;
   a.buf[0] = buf0;
   a.buf[1] = buf1;
   a.cap_buf = cap_buf;
-  a.qr_cap = qr_cap;
   a.R_out = R_dev;
   a.bar = bar;
   a.ctl = ctl;
@@ -193,24 +224,75 @@ int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, dou
   a.fuse_round = fuse_round ? 1 : 0;
   a.tol = tol;
   a.max_rank = max_rank;
-  a.round_cap = smem;
   a.R_round = R_round;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   TNR_CK(cudaGetDevice(&dev));
   TNR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)smem));
-  TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)smem));
-  if (per_sm < 1) return TNR_OK;
-  const int blocks = std::min(64, sms * per_sm);
-  TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-  {
-    LaunchScope ls(K_QR_PIV, s);
-    void *args[] = {&a};
-    TNR_CK(cudaLaunchCooperativeKernel((const void *)k_compress, dim3(blocks), dim3(kSmallThreads), args,
-                                       (size_t)smem, s));
+  // clusters of kCompressCluster CTAs when available, else the one-CTA factorisation
+  for (int C = g_cluster_mode.load() != 0 ? kCompressCluster : 1;; C = 1) {
+    int64_t qr_need = 0;
+    for (int k = 1; k < d; ++k) {
+      const int64_t w = std::min<int64_t>(64, Y.I[k] * Y.J[k] * Y.R[k + 1]);
+      qr_need = std::max(qr_need, C > 1 ? qr_cluster_bytes(w, Y.R[k], C) : qr_tpc_bytes(w, Y.R[k]));
+    }
+    const int64_t qr_cap = std::min<int64_t>(qr_need, 200 * 1024);
+    const int64_t smem = fuse_round ? std::max<int64_t>(qr_cap, (int64_t)kRoundSmallMaxSmem) : qr_cap;
+    a.qr_cap = qr_cap;
+    a.round_cap = smem;
+    TNR_TRY(ensure_dynamic_smem((const void *)k_compress, (size_t)smem));
+    if (C > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[2];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeCooperative;
+      at[1].val.cooperative = 1;
+      cfg.gridDim = dim3(64);
+      cfg.blockDim = dim3(kSmallThreads);
+      cfg.dynamicSmemBytes = (size_t)smem;
+      cfg.stream = s;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      // at least one cluster besides the factoring one: the other clusters' CTAs do the absorbs
+      if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)k_compress, &cfg) != cudaSuccess || clusters < 2) {
+        (void)cudaGetLastError();
+        g_cluster_mode.store(0);
+        continue;
+      }
+      cfg.gridDim = dim3((unsigned)(C * std::min(64 / C, clusters)));
+      cfg.numAttrs = 2;
+      TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+      cudaError_t e;
+      {
+        LaunchScope ls(K_QR_PIV, s);
+        e = cudaLaunchKernelEx(&cfg, k_compress, a);
+      }
+      if (e != cudaSuccess) {  // the cooperative launch with clusters was refused: one-CTA QR
+        (void)cudaGetLastError();
+        g_cluster_mode.store(0);
+        continue;
+      }
+      g_cluster_mode.store(C);
+      *launched = true;
+      return TNR_OK;
+    }
+    int per_sm = 0;
+    TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)smem));
+    if (per_sm < 1) return TNR_OK;
+    const int blocks = std::min(64, sms * per_sm);
+    TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    {
+      LaunchScope ls(K_QR_PIV, s);
+      void *args[] = {&a};
+      TNR_CK(cudaLaunchCooperativeKernel((const void *)k_compress, dim3(blocks), dim3(kSmallThreads), args,
+                                         (size_t)smem, s));
+    }
+    *launched = true;
+    return TNR_OK;
   }
-  *launched = true;
-  return TNR_OK;
 }
 
 // Algorithmic flops of the bonds the device compressed (recorded once the ranks are known):
@@ -229,3 +311,5 @@ void compress_record_work(const tnr_mpo &Y, const int64_t *h, int first_host_bon
 }
 
 }  // namespace tnr
+
+extern "C" int tnr_compress_cluster_size(void) { return tnr::compress_cluster_size(); }

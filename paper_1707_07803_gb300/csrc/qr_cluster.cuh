@@ -1,0 +1,350 @@
+// Column-pivoted Householder QR of a short wide matrix (m <= 64 rows, n columns) spread over the
+// CTAs of one thread-block cluster: the rank-revealing factorisation of the exact compression
+// (M_k^T = Q R P^T, stopped at the cutoff), with the same outputs as qr_tpc_cta.
+//
+// On one SM every pivot step is bound by the trailing update (about 2 m n FP64 FMAs through the
+// SM's four FP64 pipes) plus the argmax -> reflector -> apply chain. Here CTA c of C owns the
+// contiguous column block [c nl, (c + 1) nl), nl = ceil(n / C), so the update runs on C SMs. A
+// pivot step needs one cluster barrier and two distributed-shared-memory reads:
+//   1. barrier.cluster: every CTA's per-warp argmax candidates of this step are visible;
+//   2. every warp reads all C x 4 candidates (DSMEM) and picks the same pivot p (largest
+//      remaining norm, ties to the lowest column), so the cutoff test is decided identically
+//      in every CTA;
+//   3. each of the four factorisation warps (one per SM sub-partition) reads column p from its
+//      owner's shared memory and forms the Householder reflector itself (no CTA-wide sync);
+//   4. each warp applies it to its columns (g lanes per column, a group-local shuffle sum),
+//      downdates the column norms (LAPACK dgeqp3 safeguard: recompute once the downdate has lost
+//      half the digits) and posts its best remaining column for the next step.
+// The chosen column is never written again, so owners keep updating while others read it; the
+// candidate slots alternate between two buffers by step parity. The cluster's control flow
+// depends only on data every CTA holds identically, so all CTAs execute the same barriers.
+// Outputs of qr_cluster_cta: L = R^T in the original column order (each CTA writes its own
+// columns), the rank r to *r_out (CTA 0) and as the return value (every thread). Every CTA keeps
+// the reflectors in its shared memory, so Q = H_0 .. H_{r-1} [I_r; 0] can be formed afterwards by
+// qr_cluster_form_q (columns split over the cluster's warps) while other CTAs already use L. All
+// threads of every CTA of the cluster call both.
+#pragma once
+
+#include <climits>
+
+#include "dev_common.cuh"
+#include "qr_tpc.cuh"
+
+namespace tnr {
+
+constexpr int kQrWarps = 4;        // factorisation warps per CTA: one per SM sub-partition
+constexpr int kClusterMaxCtas = 8;  // portable cluster size limit
+
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// barrier.cluster with release/acquire: shared-memory writes before it are visible to every CTA
+// of the cluster after it. Executed by all threads, warp-converged.
+__device__ __forceinline__ void cluster_sync_all() {
+  __syncwarp();
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::
+          : "memory");
+}
+
+// Address of `local` (a shared variable of this CTA) in the shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t dsmem_addr(const void *local, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ double dsmem_ld_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ long long dsmem_ld_s64(uint32_t a) {
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int dsmem_ld_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+
+// Dynamic shared-memory bytes of qr_cluster_cta per CTA for an m x n matrix over C CTAs.
+__host__ __device__ inline int64_t qr_cluster_bytes(int64_t m, int64_t n, int64_t C) {
+  const int64_t nl = (n + C - 1) / C, nref = m < n ? m : n;
+  return (int64_t)sizeof(double) * (m * nl + 2 * nl + m * nref + 2 * nref + kQrWarps * 64) +
+         (int64_t)sizeof(int) * nl;
+}
+
+// Lanes per column of the trailing update: the g minimising the FP64 warp instructions one
+// sub-partition issues per step (column rounds per warp x (2 ceil(m / g) + log2 g + 4)).
+__device__ __forceinline__ int qr_cluster_lg(int m, int nl) {
+  int best = 0;
+  long long best_cost = LLONG_MAX;
+  for (int lg = 0; lg <= 5; ++lg) {
+    const int g = 1 << lg, cpw = 32 >> lg;
+    const int rounds = (nl + cpw - 1) / cpw;
+    const long long per_warp = (rounds + kQrWarps - 1) / kQrWarps;
+    const long long cost = per_warp * (2 * ((m + g - 1) / g) + lg + 4);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = lg;
+    }
+  }
+  return best;
+}
+
+// The shared-memory carve-up of one CTA (m x n over C CTAs).
+struct QrClusterLayout {
+  int nl, nref;
+  double *A;     // m x nl row-major: A(t, jl) at t * nl + jl
+  double *nrm;   // nl: squared norms below the active row
+  double *thr;   // nl: 2^-26 x the squared norm at the last recompute
+  double *V;     // m x nref: reflector i in column i (rows >= i)
+  double *tau;   // nref
+  double *bet;   // nref: R(i, p_i)
+  double *vb;    // kQrWarps x 64: each warp's copy of the current reflector
+  int *step_of;  // nl: step a column was chosen
+  __device__ QrClusterLayout(double *sm, int m, int n, int C) {
+    nl = (n + C - 1) / C;
+    nref = m < n ? m : n;
+    A = sm;
+    nrm = A + m * nl;
+    thr = nrm + nl;
+    V = thr + nl;
+    tau = V + m * nref;
+    bet = tau + nref;
+    vb = bet + nref;
+    step_of = reinterpret_cast<int *>(vb + kQrWarps * 64);
+  }
+};
+
+static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *sm) {
+  const int m = (int)a.m, n = (int)a.n;
+  const unsigned C = cluster_nctarank(), me = cluster_ctarank();
+  const QrClusterLayout lay(sm, m, n, (int)C);
+  const int nl = lay.nl, nref = lay.nref, c0 = (int)me * nl;
+  double *A = lay.A, *nrm = lay.nrm, *thr = lay.thr, *V = lay.V, *tau = lay.tau, *bet = lay.bet, *vb = lay.vb;
+  int *step_of = lay.step_of;
+  __shared__ long long s_key[2][kQrWarps];
+  __shared__ int s_idx[2][kQrWarps];
+  __shared__ double s_fro[kQrWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lg = qr_cluster_lg(m, nl), g = 1 << lg, cpw = 32 >> lg, sub = lane & (g - 1);
+  const int rounds = (nl + cpw - 1) / cpw;
+  const unsigned gmask = g == 32 ? 0xffffffffu : ((1u << g) - 1u) << (lane & ~(g - 1));
+  const int ncand = (int)C * kQrWarps;  // <= 32
+
+  for (int idx = threadIdx.x; idx < m * nl; idx += blockDim.x) {
+    const int t = idx / nl, jl = idx - t * nl, j = c0 + jl;
+    // read through L2: the source may have been written by other CTAs of a cooperative kernel
+    A[idx] = j < n ? __ldcg(a.trans_src ? a.src + (j + a.lds * t) : a.src + (t + a.lds * j)) : 0.0;
+  }
+  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) step_of[jl] = c0 + jl < n ? -1 : INT_MAX;
+  __syncthreads();
+  if (warp < kQrWarps) {  // initial norms, the Frobenius norm and the first candidates
+    long long bk = -1;
+    int bi = INT_MAX;
+    double fro = 0.0;
+    for (int rho = warp; rho < rounds; rho += kQrWarps) {
+      const int jl = rho * cpw + (lane >> lg), j = c0 + jl;
+      if (jl >= nl || j >= n) continue;  // uniform over the lane group
+      double q = 0.0;
+      for (int t = sub; t < m; t += g) q = fma(A[t * nl + jl], A[t * nl + jl], q);
+      for (int o = 1; o < g; o <<= 1) q += __shfl_xor_sync(gmask, q, o);
+      if (sub == 0) {
+        nrm[jl] = q;
+        thr[jl] = 0x1p-26 * q;
+        fro += q;
+        const long long key = __double_as_longlong(q);
+        if (key > bk || (key == bk && j < bi)) {
+          bk = key;
+          bi = j;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ok > bk || (ok == bk && oi < bi)) {
+        bk = ok;
+        bi = oi;
+      }
+    }
+    fro = dwarp_sum(fro);
+    if (lane == 0) {
+      s_key[0][warp] = bk;
+      s_idx[0][warp] = bi;
+      s_fro[warp] = fro;
+    }
+  }
+
+  double cut2 = 0.0;
+  int r = nref;
+  for (int i = 0; i < nref; ++i) {
+    cluster_sync_all();
+    // every warp: the step's pivot from all candidates of the cluster (identical everywhere)
+    long long ck = -1;
+    int ci = INT_MAX;
+    if (lane < ncand) {
+      const unsigned rk = (unsigned)lane / kQrWarps, wl = (unsigned)lane % kQrWarps;
+      ck = dsmem_ld_s64(dsmem_addr(&s_key[i & 1][wl], rk));
+      ci = dsmem_ld_s32(dsmem_addr(&s_idx[i & 1][wl], rk));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(0xffffffffu, ck, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+      if (ok > ck || (ok == ck && oi < ci)) {
+        ck = ok;
+        ci = oi;
+      }
+    }
+    if (i == 0) {  // cutoff from the squared Frobenius norm, summed in a fixed lane order
+      const unsigned rk = (unsigned)lane / kQrWarps, wl = (unsigned)lane % kQrWarps;
+      const double f = lane < ncand ? dsmem_ld_f64(dsmem_addr(&s_fro[wl], rk)) : 0.0;
+      cut2 = a.cut_rel * a.cut_rel * dwarp_sum(f);
+    }
+    if (i > 0 && __longlong_as_double(ck) <= cut2) {
+      r = i;
+      break;
+    }
+    if (warp >= kQrWarps) continue;
+    const int p = ci;
+    const unsigned own = (unsigned)(p / nl);
+    const int pl = p - (int)own * nl;
+    // reflector from column p, rows i .. m-1, read from its owner's shared memory
+    const uint32_t col = dsmem_addr(A + pl, own);
+    const int t0 = i + lane, t1 = i + lane + 32;
+    const double x0 = t0 < m ? dsmem_ld_f64(col + 8u * (uint32_t)(t0 * nl)) : 0.0;
+    const double x1 = t1 < m ? dsmem_ld_f64(col + 8u * (uint32_t)(t1 * nl)) : 0.0;
+    const double alpha = __shfl_sync(0xffffffffu, x0, 0);
+    const double sig = dwarp_sum(fma(x1, x1, lane > 0 ? x0 * x0 : 0.0));
+    double tv = 0.0, beta = alpha, scal = 0.0;
+    if (sig > 0.0) householder_params(alpha, sig, beta, tv, scal);
+    double *v = vb + warp * 64;
+    const double v0 = lane == 0 ? 1.0 : x0 * scal, v1 = x1 * scal;
+    if (t0 < m) v[t0] = v0;
+    if (t1 < m) v[t1] = v1;
+    if (warp == 0) {
+      if (t0 < m) V[i * m + t0] = v0;
+      if (t1 < m) V[i * m + t1] = v1;
+      if (lane == 0) {
+        tau[i] = tv;
+        bet[i] = beta;
+        if (own == me) step_of[pl] = i;
+      }
+    }
+    __syncwarp();
+    // apply to this warp's remaining columns; post the best remaining column for step i + 1
+    long long bk = -1;
+    int bi = INT_MAX;
+    for (int rho = warp; rho < rounds; rho += kQrWarps) {
+      const int jl = rho * cpw + (lane >> lg), j = c0 + jl;
+      if (jl >= nl || j == p || step_of[jl] >= 0) continue;  // uniform over the lane group
+      double *cj = A + jl;
+      const double aij = cj[i * nl];
+      double rij = aij;
+      if (tv != 0.0) {
+        double dot = 0.0;
+        for (int t = i + sub; t < m; t += g) dot = fma(v[t], cj[t * nl], dot);
+        for (int o = 1; o < g; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
+        const double w = dot * tv;
+        for (int t = i + sub; t < m; t += g) cj[t * nl] = fma(-w, v[t], cj[t * nl]);
+        rij = fma(-w, 1.0, aij);  // the value the lane owning row i stored (v_i = 1)
+      }
+      double nn = fma(-rij, rij, nrm[jl]);
+      if (nn <= thr[jl]) {  // cancelled (or negative): recompute from rows i+1 .. m-1
+        double q = 0.0;
+        for (int t = i + sub; t < m; t += g)
+          if (t > i) q = fma(cj[t * nl], cj[t * nl], q);
+        for (int o = 1; o < g; o <<= 1) q += __shfl_xor_sync(gmask, q, o);
+        nn = q;
+        if (sub == 0) thr[jl] = 0x1p-26 * q;
+      }
+      if (sub == 0) {
+        nrm[jl] = nn;
+        const long long key = __double_as_longlong(nn);
+        if (key > bk || (key == bk && j < bi)) {
+          bk = key;
+          bi = j;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ok > bk || (ok == bk && oi < bi)) {
+        bk = ok;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_key[(i + 1) & 1][warp] = bk;
+      s_idx[(i + 1) & 1][warp] = bi;
+    }
+  }
+  // no CTA reuses its shared memory while another may still read its pivot column or slots
+  cluster_sync_all();
+  if (me == 0 && threadIdx.x == 0 && a.r_out) *a.r_out = r;
+  // R^T (n x r, original column order) for this CTA's columns: a column chosen at step s keeps
+  // rows < s, R(s, j) = beta_s and zeros below; the others hold row s after reflector s
+  for (int idx = threadIdx.x; idx < r * nl; idx += blockDim.x) {
+    const int s = idx / nl, jl = idx - s * nl, j = c0 + jl;
+    if (j >= n) continue;
+    const int so = step_of[jl];
+    const double x = (so < 0 || s < so) ? A[s * nl + jl] : (s == so ? bet[so] : 0.0);
+    if (a.trans_r)
+      a.R[j + a.ldr * s] = x;
+    else
+      a.R[s + a.ldr * j] = x;
+  }
+  return r;
+}
+
+// Q (m x r) = H_0 .. H_{r-1} [I_r; 0] from the reflectors qr_cluster_cta left in every CTA's
+// shared memory: column l by global warp l mod (C x warps), backward accumulation.
+static __device__ __noinline__ void qr_cluster_form_q(const QrSmallArgs &a, double *sm, int r) {
+  const int m = (int)a.m, n = (int)a.n;
+  const unsigned C = cluster_nctarank(), me = cluster_ctarank();
+  const QrClusterLayout lay(sm, m, n, (int)C);
+  const double *V = lay.V, *tau = lay.tau;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ldq = a.ldq > 0 ? (int)a.ldq : r;
+  const int nwarps = (int)(blockDim.x >> 5);
+  for (int l = (int)me * nwarps + warp; l < r; l += (int)C * nwarps) {
+    const int u0 = lane, u1 = lane + 32;
+    double q0 = u0 == l ? 1.0 : 0.0, q1 = u1 == l ? 1.0 : 0.0;
+    for (int j = l; j >= 0; --j) {
+      const double tj = tau[j];
+      if (tj == 0.0) continue;
+      const double w0 = u0 < j || u0 >= m ? 0.0 : V[j * m + u0];
+      const double w1 = u1 < j || u1 >= m ? 0.0 : V[j * m + u1];
+      const double w = dwarp_sum(fma(w0, q0, w1 * q1)) * tj;
+      q0 = fma(-w, w0, q0);
+      q1 = fma(-w, w1, q1);
+    }
+    if (a.trans_q) {
+      if (u0 < m) a.Q[l + ldq * u0] = q0;
+      if (u1 < m) a.Q[l + ldq * u1] = q1;
+    } else {
+      if (u0 < m) a.Q[u0 + ldq * l] = q0;
+      if (u1 < m) a.Q[u1 + ldq * l] = q1;
+    }
+  }
+}
+
+}  // namespace tnr

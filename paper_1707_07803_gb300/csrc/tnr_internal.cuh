@@ -230,6 +230,8 @@ int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);
 int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, double *buf0, double *buf1,
                     int64_t cap_buf, unsigned *bar, int *ctl, int64_t *R_dev, bool fuse_round, double tol,
                     int64_t max_rank, int64_t *R_round, bool *launched);
+// CTAs per factoring cluster of the compression (1: one-CTA QR, or before the first launch).
+int compress_cluster_size();
 // Records the algorithmic work of the bonds the device compressed, from the ranks h read back.
 void compress_record_work(const tnr_mpo &Y, const int64_t *h, int first_host_bond);
 

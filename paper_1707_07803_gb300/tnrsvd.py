@@ -116,6 +116,7 @@ _SIGS = {
     "tnr_stats_class_name": (ctypes.c_char_p, [_I32]),
     "tnr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "tnr_version": (ctypes.c_int, []),
+    "tnr_compress_cluster_size": (ctypes.c_int, []),
 }
 
 

@@ -30,7 +30,7 @@ def test_contract_elementwise(trans):
         np.testing.assert_allclose(g, w, rtol=0, atol=1e-13 * max(1.0, np.abs(w).max()))
 
 
-@pytest.mark.parametrize("case", ["plain", "wide_sites", "rank_deficient", "single_site"])
+@pytest.mark.parametrize("case", ["plain", "wide_sites", "rank_deficient", "single_site", "hundred_wide"])
 def test_orthogonalize_invariants_and_ranks(case):
     if case == "plain":
         Y = W.gaussian_mpo(3, [12, 3, 2, 2], [5, 1, 1, 1], [1, 4, 3, 2, 1])
@@ -38,6 +38,10 @@ def test_orthogonalize_invariants_and_ranks(case):
         Y = W.gaussian_mpo(4, [8, 4, 4], [6, 1, 1], [1, 9, 7, 1])
     elif case == "rank_deficient":
         Y = W.gaussian_mpo(5, [10, 2, 2, 2], [4, 1, 1, 1], [1, 6, 6, 6, 1])  # bonds above Thm 3.2 bounds
+    elif case == "hundred_wide":
+        # 100-wide bonds: the compression factors 4 x 100, 16 x 100 and 64 x 100 matrices (the
+        # last of rank 48, cut by the pivoting), with columns spread unevenly over a cluster
+        Y = W.gaussian_mpo(7, [8, 4, 4, 4], [6, 1, 1, 1], [1, 100, 100, 100, 1], scale=0.1)
     else:
         Y = W.gaussian_mpo(6, [40], [9], [1, 1])
     Qo, Ro = orr.orthogonalize(Y, tol=1e-13)
@@ -55,6 +59,19 @@ def test_orthogonalize_invariants_and_ranks(case):
     DQo = om.dense(Qo)
     np.testing.assert_allclose(DQ @ DQ.T, DQo @ DQo.T, atol=1e-12)
     np.testing.assert_allclose(np.abs(R), np.abs(Ro), atol=1e-11 * np.abs(Ro).max())
+
+
+def test_compression_factors_each_bond_on_a_thread_block_cluster():
+    # on GB300 the cooperative launch with clusters is available: each bond's pivoted QR runs on a
+    # 4-CTA cluster (distributed shared memory), not the one-CTA fallback
+    Y = W.gaussian_mpo(8, [8, 4, 4, 4], [6, 1, 1, 1], [1, 100, 100, 100, 1], scale=0.1)
+    Qd, Rd = T.tnr_orthogonalize(dev_mpo(Y), tol=1e-13)
+    torch.cuda.synchronize()
+    assert T.load().tnr_compress_cluster_size() == 4
+    Qo, Ro = orr.orthogonalize(Y, tol=1e-13)
+    assert Qd.R == orr.ranks(Qo)
+    DQ, DY = om.dense(host_cores(Qd)), om.dense(Y)
+    np.testing.assert_allclose(DQ @ Rd.cpu().numpy(), DY, atol=1e-11 * np.abs(DY).max())
 
 
 def _check_solve(A, k, p, q, seed, tol, max_rank, sv_tol=FP64_SV_TOL, vec_tol=1e-8):

@@ -42,34 +42,33 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, double ga,
 }
 
 // Householder reflector parameters (LAPACK dlarfg convention) for x = (alpha, x_2..) with
-// sig = ||x_2..||^2 > 0: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta, and
-// scal = 1 / (alpha - beta) (v = x_2.. * scal, v_1 = 1). Written without FP64 division or
-// square root: r = 1/||x|| from an FP32 estimate and two Newton steps, so beta = -sign(alpha)
-// n2 r, tau = 1 + |alpha| r, and 1 / (|alpha| + ||x||) by two Newton steps from an FP32
-// reciprocal. Each Newton step doubles the correct bits: 24 -> 48 -> FP64 rounding.
+// sig = ||x_2..||^2 > 0: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta = 1 + |alpha| r
+// and scal = 1 / (alpha - beta) = sign(alpha) r / tau with r = 1 / ||x|| (v = x_2.. * scal,
+// v_1 = 1). Written without FP64 division or square root, with a short dependent chain (these
+// parameters sit on the critical path of every pivot step): r from an FP32 estimate refined by
+// one third-order step r (1 + e/2 + 3e^2/8), e = 1 - n r^2 (the Taylor series of (1 - e)^(-1/2)),
+// and 1 / tau (tau in [1, 2], no range reduction) from an FP32 reciprocal refined by
+// q (1 + e + e^2), e = 1 - tau q (the geometric series). The FP32 estimates' relative error
+// (< 2^-21) leaves O(2^-63) after the step, below FP64 rounding.
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
 __device__ __forceinline__ void householder_params(double alpha, double sig, double &beta, double &tau,
                                                    double &scal) {
   const double n2 = fma(alpha, alpha, sig);
-  // exact power-of-two range reduction so the FP32 seeds never overflow or underflow
+  // exact power-of-two range reduction so the FP32 seed never overflows or underflows
   const int k = ((int)((__double_as_longlong(n2) >> 52) & 0x7FF) - 1023) >> 1;  // floor(e / 2)
   const double n2s = n2 * pow2(-2 * k);                                            // in [1, 4)
   double r = (double)rsqrtf((float)n2s);
-  r = r * fma(-0.5 * n2s, r * r, 1.5);
-  r = r * fma(-0.5 * n2s, r * r, 1.5);
-  r *= pow2(-k);             // 1 / ||x||
-  const double nx = n2 * r;  // ||x||
+  const double e = fma(-n2s * r, r, 1.0);
+  r = fma(r * e, fma(0.375, e, 0.5), r);
+  r *= pow2(-k);  // 1 / ||x||
   const double sgn = alpha < 0.0 ? -1.0 : 1.0;
-  beta = -sgn * nx;
+  beta = -sgn * (n2 * r);
   tau = fma(fabs(alpha), r, 1.0);
-  const double den = fabs(alpha) + nx;  // |alpha - beta|
-  const int e = (int)((__double_as_longlong(den) >> 52) & 0x7FF) - 1023;
-  const double dens = den * pow2(-e);  // in [1, 2)
-  double q = (double)(1.0f / (float)dens);
-  q = q * fma(-dens, q, 2.0);
-  q = q * fma(-dens, q, 2.0);
-  scal = sgn * q * pow2(-e);
+  double q = (double)(1.0f / (float)tau);
+  const double et = fma(-tau, q, 1.0);
+  q = fma(q, fma(et, et, et), q);
+  scal = (sgn * r) * q;
 }
 
 // 1 / sqrt(x) for finite x > 0 to FP64 accuracy without the FP64 square-root / division

@@ -4,20 +4,20 @@
 //
 // On one SM every pivot step is bound by the trailing update (about 2 m n FP64 FMAs through the
 // SM's four FP64 pipes) plus the argmax -> reflector -> apply chain. Here CTA c of C owns the
-// contiguous column block [c nl, (c + 1) nl), nl = ceil(n / C), so the update runs on C SMs. A
-// pivot step needs one cluster barrier and two distributed-shared-memory reads:
-//   1. barrier.cluster: every CTA's per-warp argmax candidates of this step are visible;
-//   2. every warp reads all C x 4 candidates (DSMEM) and picks the same pivot p (largest
-//      remaining norm, ties to the lowest column), so the cutoff test is decided identically
-//      in every CTA;
-//   3. each of the four factorisation warps (one per SM sub-partition) reads column p from its
-//      owner's shared memory and forms the Householder reflector itself (no CTA-wide sync);
-//   4. each warp applies it to its columns (g lanes per column, a group-local shuffle sum),
+// contiguous column block [c nl, (c + 1) nl), nl = ceil(n / C), so the update runs on C SMs. The
+// exchange is push-only, so a pivot step has one cluster barrier and no remote loads:
+//   1. at the end of step i-1 each of the four factorisation warps (one per SM sub-partition)
+//      stores its best remaining column (norm key, index, and the column's rows i .. m-1) into
+//      every CTA's receive buffers (st.shared::cluster; slots alternate by step parity);
+//   2. barrier.cluster (release/acquire): all C x 4 candidates are in every CTA's shared memory;
+//   3. every warp picks the same pivot p from them (largest remaining norm, ties to the lowest
+//      column), so the cutoff test is decided identically in every CTA, and each factorisation
+//      warp forms the Householder reflector from p's received column itself (no CTA-wide sync);
+//   4. each warp applies it to its columns (g lanes per column, a group-local shuffle sum) and
 //      downdates the column norms (LAPACK dgeqp3 safeguard: recompute once the downdate has lost
-//      half the digits) and posts its best remaining column for the next step.
-// The chosen column is never written again, so owners keep updating while others read it; the
-// candidate slots alternate between two buffers by step parity. The cluster's control flow
-// depends only on data every CTA holds identically, so all CTAs execute the same barriers.
+//      half the digits), then posts its next candidate (1.).
+// The cluster's control flow depends only on data every CTA holds identically, so all CTAs
+// execute the same barriers.
 // Outputs of qr_cluster_cta: L = R^T in the original column order (each CTA writes its own
 // columns), the rank r to *r_out (CTA 0) and as the return value (every thread). Every CTA keeps
 // the reflectors in its shared memory, so Q = H_0 .. H_{r-1} [I_r; 0] can be formed afterwards by
@@ -65,28 +65,22 @@ __device__ __forceinline__ uint32_t dsmem_addr(const void *local, unsigned rank)
   return r;
 }
 
-__device__ __forceinline__ double dsmem_ld_f64(uint32_t a) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
-  return v;
+__device__ __forceinline__ void dsmem_st_f64(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
-__device__ __forceinline__ long long dsmem_ld_s64(uint32_t a) {
-  long long v;
-  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-  return v;
+__device__ __forceinline__ void dsmem_st_s64(uint32_t a, long long v) {
+  asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ int dsmem_ld_s32(uint32_t a) {
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
+__device__ __forceinline__ void dsmem_st_s32(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 // Dynamic shared-memory bytes of qr_cluster_cta per CTA for an m x n matrix over C CTAs.
 __host__ __device__ inline int64_t qr_cluster_bytes(int64_t m, int64_t n, int64_t C) {
   const int64_t nl = (n + C - 1) / C, nref = m < n ? m : n;
-  return (int64_t)sizeof(double) * (m * nl + 2 * nl + m * nref + 2 * nref + kQrWarps * 64) +
+  return (int64_t)sizeof(double) * (m * nl + 2 * nl + m * nref + 2 * nref + kQrWarps * 64 + 2 * C * kQrWarps * 64) +
          (int64_t)sizeof(int) * nl;
 }
 
@@ -118,6 +112,7 @@ struct QrClusterLayout {
   double *tau;   // nref
   double *bet;   // nref: R(i, p_i)
   double *vb;    // kQrWarps x 64: each warp's copy of the current reflector
+  double *rcol;  // 2 x (C kQrWarps) x 64: received candidate columns, by step parity and slot
   int *step_of;  // nl: step a column was chosen
   __device__ QrClusterLayout(double *sm, int m, int n, int C) {
     nl = (n + C - 1) / C;
@@ -129,9 +124,52 @@ struct QrClusterLayout {
     tau = V + m * nref;
     bet = tau + nref;
     vb = bet + nref;
-    step_of = reinterpret_cast<int *>(vb + kQrWarps * 64);
+    rcol = vb + kQrWarps * 64;
+    step_of = reinterpret_cast<int *>(rcol + 2 * C * kQrWarps * 64);
   }
 };
+
+// Received candidates of the cluster (slot = CTA rank x kQrWarps + warp), by step parity.
+struct QrClusterSlots {
+  long long key[2][32];
+  int idx[2][32];
+  double fro[32];
+};
+
+// This warp's candidate for step s (its best remaining column: norm key and index, INT_MAX for
+// none) with the column's rows s .. m-1, stored into every cluster CTA's receive buffers. All
+// lanes call it (warp-converged) after the column's last update is visible to the warp.
+static __device__ __forceinline__ void qr_cluster_post(const QrClusterLayout &lay, QrClusterSlots &sl, int m, int s,
+                                                       long long key, int idx, int c0, unsigned C, unsigned me,
+                                                       int warp, int lane) {
+  const int slot = (int)me * kQrWarps + warp, b = s & 1;
+  if (idx != INT_MAX) {
+    const int jl = idx - c0, t0 = s + lane, t1 = s + lane + 32;
+    const double x0 = t0 < m ? lay.A[t0 * lay.nl + jl] : 0.0;
+    const double x1 = t1 < m ? lay.A[t1 * lay.nl + jl] : 0.0;
+    double *dst = lay.rcol + (b * (int)C * kQrWarps + slot) * 64;
+    for (unsigned rk = 0; rk < C; ++rk) {
+      if (t0 < m) dsmem_st_f64(dsmem_addr(dst + t0, rk), x0);
+      if (t1 < m) dsmem_st_f64(dsmem_addr(dst + t1, rk), x1);
+    }
+  }
+  if (lane < (int)C) {
+    dsmem_st_s64(dsmem_addr(&sl.key[b][slot], (unsigned)lane), key);
+    dsmem_st_s32(dsmem_addr(&sl.idx[b][slot], (unsigned)lane), idx);
+  }
+}
+
+// Warp-wide argmax of (key, column): largest key, ties to the lowest column; every lane gets it.
+static __device__ __forceinline__ void warp_argmax(long long &k, int &j) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (ok > k || (ok == k && oj < j)) {
+      k = ok;
+      j = oj;
+    }
+  }
+}
 
 static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *sm) {
   const int m = (int)a.m, n = (int)a.n;
@@ -140,9 +178,7 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
   const int nl = lay.nl, nref = lay.nref, c0 = (int)me * nl;
   double *A = lay.A, *nrm = lay.nrm, *thr = lay.thr, *V = lay.V, *tau = lay.tau, *bet = lay.bet, *vb = lay.vb;
   int *step_of = lay.step_of;
-  __shared__ long long s_key[2][kQrWarps];
-  __shared__ int s_idx[2][kQrWarps];
-  __shared__ double s_fro[kQrWarps];
+  __shared__ QrClusterSlots sl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lg = qr_cluster_lg(m, nl), g = 1 << lg, cpw = 32 >> lg, sub = lane & (g - 1);
   const int rounds = (nl + cpw - 1) / cpw;
@@ -177,20 +213,10 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
         }
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ok > bk || (ok == bk && oi < bi)) {
-        bk = ok;
-        bi = oi;
-      }
-    }
+    warp_argmax(bk, bi);
     fro = dwarp_sum(fro);
-    if (lane == 0) {
-      s_key[0][warp] = bk;
-      s_idx[0][warp] = bi;
-      s_fro[warp] = fro;
-    }
+    qr_cluster_post(lay, sl, m, 0, bk, bi, c0, C, me, warp, lane);
+    if (lane < (int)C) dsmem_st_f64(dsmem_addr(&sl.fro[(int)me * kQrWarps + warp], (unsigned)lane), fro);
   }
 
   double cut2 = 0.0;
@@ -198,26 +224,12 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
   for (int i = 0; i < nref; ++i) {
     cluster_sync_all();
     // every warp: the step's pivot from all candidates of the cluster (identical everywhere)
-    long long ck = -1;
-    int ci = INT_MAX;
-    if (lane < ncand) {
-      const unsigned rk = (unsigned)lane / kQrWarps, wl = (unsigned)lane % kQrWarps;
-      ck = dsmem_ld_s64(dsmem_addr(&s_key[i & 1][wl], rk));
-      ci = dsmem_ld_s32(dsmem_addr(&s_idx[i & 1][wl], rk));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long ok = __shfl_xor_sync(0xffffffffu, ck, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-      if (ok > ck || (ok == ck && oi < ci)) {
-        ck = ok;
-        ci = oi;
-      }
-    }
-    if (i == 0) {  // cutoff from the squared Frobenius norm, summed in a fixed lane order
-      const unsigned rk = (unsigned)lane / kQrWarps, wl = (unsigned)lane % kQrWarps;
-      const double f = lane < ncand ? dsmem_ld_f64(dsmem_addr(&s_fro[wl], rk)) : 0.0;
-      cut2 = a.cut_rel * a.cut_rel * dwarp_sum(f);
-    }
+    const int b = i & 1;
+    long long ck = lane < ncand ? sl.key[b][lane] : -1;
+    int ci = lane < ncand ? sl.idx[b][lane] : INT_MAX;
+    warp_argmax(ck, ci);
+    if (i == 0)  // cutoff from the squared Frobenius norm, summed in a fixed lane order
+      cut2 = a.cut_rel * a.cut_rel * dwarp_sum(lane < ncand ? sl.fro[lane] : 0.0);
     if (i > 0 && __longlong_as_double(ck) <= cut2) {
       r = i;
       break;
@@ -226,11 +238,12 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
     const int p = ci;
     const unsigned own = (unsigned)(p / nl);
     const int pl = p - (int)own * nl;
-    // reflector from column p, rows i .. m-1, read from its owner's shared memory
-    const uint32_t col = dsmem_addr(A + pl, own);
+    // reflector from p's received column (rows i .. m-1); it was posted by the warp that updates
+    // column pl, slot own x kQrWarps + (pl / cpw) mod kQrWarps
+    const double *col = lay.rcol + (b * ncand + (int)own * kQrWarps + (pl / cpw) % kQrWarps) * 64;
     const int t0 = i + lane, t1 = i + lane + 32;
-    const double x0 = t0 < m ? dsmem_ld_f64(col + 8u * (uint32_t)(t0 * nl)) : 0.0;
-    const double x1 = t1 < m ? dsmem_ld_f64(col + 8u * (uint32_t)(t1 * nl)) : 0.0;
+    const double x0 = t0 < m ? col[t0] : 0.0;
+    const double x1 = t1 < m ? col[t1] : 0.0;
     const double alpha = __shfl_sync(0xffffffffu, x0, 0);
     const double sig = dwarp_sum(fma(x1, x1, lane > 0 ? x0 * x0 : 0.0));
     double tv = 0.0, beta = alpha, scal = 0.0;
@@ -284,21 +297,15 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
         }
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ok > bk || (ok == bk && oi < bi)) {
-        bk = ok;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      s_key[(i + 1) & 1][warp] = bk;
-      s_idx[(i + 1) & 1][warp] = bi;
-    }
+    warp_argmax(bk, bi);
+    __syncwarp();  // the candidate's updated rows, written by its lane group, are read by all lanes
+    if (i + 1 < nref) qr_cluster_post(lay, sl, m, i + 1, bk, bi, c0, C, me, warp, lane);
   }
-  // no CTA reuses its shared memory while another may still read its pivot column or slots
-  cluster_sync_all();
+  // Every posted value was consumed before the loop ended (the last posts are read at the step
+  // that stops), so no remote store is in flight and each CTA may reuse its shared memory. The
+  // outputs read only this CTA's shared memory, but without a cutoff the last step's updates
+  // may still be running in other warps: a CTA barrier orders them.
+  __syncthreads();
   if (me == 0 && threadIdx.x == 0 && a.r_out) *a.r_out = r;
   // R^T (n x r, original column order) for this CTA's columns: a column chosen at step s keeps
   // rows < s, R(s, j) = beta_s and zeros below; the others hold row s after reflector s

@@ -31,8 +31,8 @@ DTYPES = {"mixed": "bf16x3/f64", "fp64": "f64"}
 KERNELS = {
     "qr": "k_site1_cholqr2 (site-1 CholeskyQR2, one cooperative launch) / k_qr_coop (Householder fallback)",
     "qr_small": "k_qr_small / k_qr_small_tpc (one-CTA FP64 Householder QR, explicit Q)",
-    "qr_piv": "k_compress (cooperative exact compression sweep: one-CTA pivoted FP64 QR per bond + grid-wide "
-              "absorb, then the fused rounding sweeps / certificate on CTA 0)",
+    "qr_piv": "k_compress (cooperative exact compression sweep: pivoted FP64 QR per bond on an 8-CTA thread-block "
+              "cluster (DSMEM exchange) + grid-wide absorb, then the fused rounding sweeps / certificate on CTA 0)",
     "svd": "k_svd_step / k_jacobi (FP64 truncated SVD step, one-sided Jacobi)",
     "gemm": "k_gemm / k_gemm_tiny (FP64 GEMM)",
     "contract": "k_contract (per-site MPO product)",
@@ -40,7 +40,7 @@ KERNELS = {
 UNIT = "solves/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the named kernel, as recorded in
 # profiles/; reported only while that kernel is unchanged (empty: not yet re-captured).
-TRAFFIC_BYTES = {"qr_piv": 2.79e6}
+TRAFFIC_BYTES = {"qr_piv": 2.78e6}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 

@@ -316,7 +316,7 @@ int tnr_stats(int32_t cls, int64_t *launches, double *ms);
 int tnr_stats_work(int32_t cls, double *work);
 const char *tnr_stats_class_name(int32_t cls);
 /* CTAs per thread-block cluster that factor each bond of the exact compression (the cluster-
- * distributed column-pivoted QR of Section 5.4's rank-revealing step: 4 when the cooperative
+ * distributed column-pivoted QR of Section 5.4's rank-revealing step: 8 when the cooperative
  * launch with clusters is available, 1 when the one-CTA factorisation is used instead; 1 before
  * the first compression of the process). Instrumentation only. */
 int tnr_compress_cluster_size(void);

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
 // bar (2). *launched = false when the shapes are outside the kernel's layout (nothing queued).
 // Cluster size of the factoring cluster; whether the cooperative launch with clusters is
 // available is decided at the first launch of the process (kept: -1 unknown, 0 refused, else C).
-constexpr int kCompressCluster = 4;
+constexpr int kCompressCluster = 8;
 static_assert(kCompressCluster * kQrWarps <= 32 && kCompressCluster <= kClusterMaxCtas,
               "one warp reads every candidate of the cluster; portable cluster size");
 static std::atomic<int> g_cluster_mode{-1};

@@ -63,11 +63,11 @@ def test_orthogonalize_invariants_and_ranks(case):
 
 def test_compression_factors_each_bond_on_a_thread_block_cluster():
     # on GB300 the cooperative launch with clusters is available: each bond's pivoted QR runs on a
-    # 4-CTA cluster (distributed shared memory), not the one-CTA fallback
+    # 8-CTA cluster (distributed shared memory), not the one-CTA fallback
     Y = W.gaussian_mpo(8, [8, 4, 4, 4], [6, 1, 1, 1], [1, 100, 100, 100, 1], scale=0.1)
     Qd, Rd = T.tnr_orthogonalize(dev_mpo(Y), tol=1e-13)
     torch.cuda.synchronize()
-    assert T.load().tnr_compress_cluster_size() == 4
+    assert T.load().tnr_compress_cluster_size() == 8
     Qo, Ro = orr.orthogonalize(Y, tol=1e-13)
     assert Qd.R == orr.ranks(Qo)
     DQ, DY = om.dense(host_cores(Qd)), om.dense(Y)

@@ -59,9 +59,11 @@ struct JacobiEps<float> {
   static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
 };
 
-// All threads of the CTA call this; nrm: n values of shared memory. Returns the sweep count.
+// All threads of the CTA call this; G and V are n x n with leading dimension ld (n + 1 keeps the
+// columns a warp rotates at once in different shared-memory banks); nrm: n values of shared
+// memory. Returns the sweep count.
 template <typename T>
-static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, T *nrm, int max_sweeps) {
+static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, int ld, T *nrm, int max_sweeps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nthr = blockDim.x, nw = nthr >> 5;
   const int np = (n + 1) & ~1;
@@ -79,10 +81,10 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, T *nrm, in
       T s0 = 0, s1 = 0;
       int i = 0;
       for (; i + 1 < n; i += 2) {
-        s0 = fma(G[i + n * j], G[i + n * j], s0);
-        s1 = fma(G[i + 1 + n * j], G[i + 1 + n * j], s1);
+        s0 = fma(G[i + ld * j], G[i + ld * j], s0);
+        s1 = fma(G[i + 1 + ld * j], G[i + 1 + ld * j], s1);
       }
-      if (i < n) s0 = fma(G[i + n * j], G[i + n * j], s0);
+      if (i < n) s0 = fma(G[i + ld * j], G[i + ld * j], s0);
       nrm[j] = s0 + s1;
     }
     if (threadIdx.x == 0) s_rot2 = 0;
@@ -123,12 +125,12 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, T *nrm, in
         }
         T ga = 0;
         if (act)
-          for (int i = li; i < n; i += g) ga = fma(G[i + n * p], G[i + n * q], ga);
+          for (int i = li; i < n; i += g) ga = fma(G[i + ld * p], G[i + ld * q], ga);
         for (int o = g >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o, g);
         T cs = 1, sn = 0;
         if (act) act = ga != (T)0 && ga * ga > tol2 * al * be && jacobi_rot(al, be, ga, cs, sn);
         if (act) {
-          T *gp = G + n * p, *gq = G + n * q, *vp = V + n * p, *vq = V + n * q;
+          T *gp = G + ld * p, *gq = G + ld * q, *vp = V + ld * p, *vq = V + ld * q;
           for (int i = li; i < n; i += g) {
             const T x = gp[i], y = gq[i];
             gp[i] = fma(-sn, y, cs * x);
@@ -156,11 +158,11 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, T *nrm, in
 
 // Plain FP64 sweeps (G_in V = G_out with V accumulated from its value on entry).
 static __device__ __forceinline__ int jacobi_sweeps(double *G, double *V, int n, double *nrm) {
-  return jacobi_sweeps_t<double>(G, V, n, nrm, 60);
+  return jacobi_sweeps_t<double>(G, V, n, n, nrm, 60);
 }
 
 // Doubles of work area jacobi_sweeps_mixed needs for an n x n matrix.
-__host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 2 * n * n + n; }
+__host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 3 * n * (n + 1); }
 
 // Mixed-precision one-sided Jacobi (the preconditioned scheme of Gao, Ma and Shao, "A mixed
 // precision Jacobi SVD algorithm", 2022): the sweeps run to convergence in FP32 on a copy of G
@@ -175,7 +177,13 @@ __host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 2 * n *
 static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work) {
   const int nthr = blockDim.x;
   const int nn = n * n;
-  float *Gf = reinterpret_cast<float *>(work), *Vf = Gf + nn, *nf = Vf + nn;
+  // padded working copies (leading dimension n + 1): columns i and i + 1 start in different
+  // shared-memory banks, so neither the pairs a warp rotates together nor a column-per-lane
+  // product serialise on one bank. work: Gp, Vp, Tp (n x (n + 1) doubles each); the FP32 copies
+  // live in Tp during the FP32 phase, their norms in nrm.
+  const int ld = n + 1, np = n * ld;
+  double *Gp = work, *Vp = work + np, *Tp = work + 2 * np;
+  float *Gf = reinterpret_cast<float *>(Tp), *Vf = Gf + np, *nf = reinterpret_cast<float *>(nrm);
   __shared__ double s_scale;
   // power-of-two scale bringing ||G||_F near 1 (FP32 range; exact in both directions)
   for (int j = threadIdx.x; j < n; j += nthr) {
@@ -193,19 +201,24 @@ static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int
   __syncthreads();
   const double sc = s_scale;
   for (int idx = threadIdx.x; idx < nn; idx += nthr) {
-    Gf[idx] = (float)(G[idx] * sc);
-    Vf[idx] = (idx % n == idx / n) ? 1.0f : 0.0f;
+    const int i = idx % n, j = idx / n;
+    Gf[i + ld * j] = (float)(G[idx] * sc);
+    Vf[i + ld * j] = i == j ? 1.0f : 0.0f;
   }
   __syncthreads();
-  jacobi_sweeps_t<float>(Gf, Vf, n, nf, 40);
-  for (int idx = threadIdx.x; idx < nn; idx += nthr) V[idx] = (double)Vf[idx];
+  jacobi_sweeps_t<float>(Gf, Vf, n, ld, nf, 40);
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+    const int i = idx % n, j = idx / n;
+    Vp[i + ld * j] = (double)Vf[i + ld * j];
+  }
   __syncthreads();
-  // Newton-Schulz steps; T1 = V^T V, T2 = 1.5 V - 0.5 V T1 (the FP32 copies are dead now)
-  double *T1 = work, *T2 = work + nn;
+  // Newton-Schulz steps: T1 = V^T V (in Gp), V <- 1.5 V - 0.5 V T1 (into Tp; the FP32 copies
+  // are dead now), then the roles of Vp and Tp swap. Lane i reads row l of column i of V (stride
+  // n + 1: conflict-free) or row i of column l; the other operand is a broadcast.
   for (int it = 0; it < 2; ++it) {
     for (int idx = threadIdx.x; idx < nn; idx += nthr) {
       const int i = idx % n, j = idx / n;
-      const double *vi = V + n * i, *vj = V + n * j;
+      const double *vi = Vp + ld * i, *vj = Vp + ld * j;
       double s0 = 0.0, s1 = 0.0;
       int l = 0;
       for (; l + 1 < n; l += 2) {
@@ -213,29 +226,30 @@ static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int
         s1 = fma(vi[l + 1], vj[l + 1], s1);
       }
       if (l < n) s0 = fma(vi[l], vj[l], s0);
-      T1[idx] = s0 + s1;
+      Gp[i + ld * j] = s0 + s1;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nn; idx += nthr) {
       const int i = idx % n, j = idx / n;
-      const double *t = T1 + n * j;
+      const double *t = Gp + ld * j;
       double s0 = 0.0, s1 = 0.0;
       int l = 0;
       for (; l + 1 < n; l += 2) {
-        s0 = fma(V[i + n * l], t[l], s0);
-        s1 = fma(V[i + n * (l + 1)], t[l + 1], s1);
+        s0 = fma(Vp[i + ld * l], t[l], s0);
+        s1 = fma(Vp[i + ld * (l + 1)], t[l + 1], s1);
       }
-      if (l < n) s0 = fma(V[i + n * l], t[l], s0);
-      T2[idx] = fma(-0.5, s0 + s1, 1.5 * V[idx]);
+      if (l < n) s0 = fma(Vp[i + ld * l], t[l], s0);
+      Tp[i + ld * j] = fma(-0.5, s0 + s1, 1.5 * Vp[i + ld * j]);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nn; idx += nthr) V[idx] = T2[idx];
-    __syncthreads();
+    double *x = Vp;
+    Vp = Tp;
+    Tp = x;
   }
-  // G <- G V0
+  // Gp <- G V0
   for (int idx = threadIdx.x; idx < nn; idx += nthr) {
     const int i = idx % n, j = idx / n;
-    const double *v = V + n * j;
+    const double *v = Vp + ld * j;
     double s0 = 0.0, s1 = 0.0;
     int l = 0;
     for (; l + 1 < n; l += 2) {
@@ -243,12 +257,17 @@ static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int
       s1 = fma(G[i + n * (l + 1)], v[l + 1], s1);
     }
     if (l < n) s0 = fma(G[i + n * l], v[l], s0);
-    T2[idx] = s0 + s1;
+    Gp[i + ld * j] = s0 + s1;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nn; idx += nthr) G[idx] = T2[idx];
+  const int sweeps = jacobi_sweeps_t<double>(Gp, Vp, n, ld, nrm, 60);
+  for (int idx = threadIdx.x; idx < nn; idx += nthr) {
+    const int i = idx % n, j = idx / n;
+    G[idx] = Gp[i + ld * j];
+    V[idx] = Vp[i + ld * j];
+  }
   __syncthreads();
-  return jacobi_sweeps_t<double>(G, V, n, nrm, 60);
+  return sweeps;
 }
 
 }  // namespace tnr

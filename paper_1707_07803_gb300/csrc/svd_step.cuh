@@ -28,8 +28,8 @@ constexpr int kStepWarps = kStepThreads / 32;
 constexpr int kStepMaxN = 1024;  // largest min(t, w)
 
 static __host__ __device__ inline int64_t svd_step_work(int64_t t, int64_t w) {
-  const int64_t mm = t >= w ? t : w, n = t >= w ? w : t;
-  return 2 * mm * n + 3 * n * n + 3 * n;
+  const int64_t mm = t >= w ? t : w, n = t >= w ? w : t, jw = jacobi_mixed_work(n);
+  return mm * n + 2 * n * n + 2 * n + (mm * n > jw ? mm * n : jw);
 }
 
 static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, double delta2, int64_t max_rank,
@@ -41,8 +41,8 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
   double *V = G + n * n;     // n x n
   double *tau = V + n * n;   // n
   double *nrm = tau + n;     // n (Jacobi column norms, then singular values)
-  double *W = nrm + n;       // mm x n: reflector application workspace; with the n^2 + n after it,
-                             // the work area of the mixed-precision Jacobi (>= 2 n^2 + n)
+  double *W = nrm + n;       // mm x n: reflector application workspace, then the work area of
+                             // the mixed-precision Jacobi (jacobi_mixed_work(n) doubles)
   __shared__ int s_r;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int idx = threadIdx.x; idx < mm * n; idx += kStepThreads) {

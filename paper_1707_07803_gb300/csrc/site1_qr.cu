@@ -1,18 +1,22 @@
-// Site-1 QR of Algs. 5.2/5.3 (A1^T = Q~ R~, the (I1 t) x K matrix of the site-1 core) by
-// CholeskyQR2 in ONE cooperative launch.
+// Site-1 QR of Algs. 5.2/5.3 (A1^T = Q~ R~, the (I1 t) x K matrix Y of the site-1 core) by
+// CholeskyQR2 in ONE cooperative launch with three grid barriers.
 //
-// Each CTA owns a block of rows of A1^T and keeps it in shared memory for both passes; a pass is
-// a symmetric partial Gram per CTA, a fixed-order sum of the partials and the Cholesky factor on
-// CTA 0, and the triangular solve of every CTA's rows (warp per row). Two bounded grid barriers
-// per pass replace the six launches and the host round trip of the multi-kernel version, and the
-// fixed-order sum makes the result independent of scheduling (no floating-point atomics).
-//
-// Pass 1 factors G1 = Y^T Y in the square-root-free form (one reciprocal per pivot). Pass 2 sees
-// G2 = I + E with |E| ~ cond(Y)^2 eps; it first checks that G2 is within 0.5 / K of the identity
-// (the regime in which CholeskyQR2 is orthogonal to rounding level; otherwise *flag is set and
-// the caller falls back to Householder), and when max |E| <= 1e-9 its factor is taken in closed
-// form, R2 = I + triu(E) - diag(E) / 2, whose error R2^T R2 - G2 = O(|E|^2) is below rounding
-// level: no pivot chain at all. The result is R = R2 R1 and Q = Y R1^{-1} R2^{-1}.
+// Nothing in a pass is serialised on one CTA:
+//   * the Gram G = Y^T Y is computed by column tiles: CTA b takes 4 x 4 tiles of the upper
+//     triangle and sums each entry over all rows (read from L2), so G is written once, with no
+//     partial Grams and no reduction step; the summation order is fixed (deterministic);
+//   * after a grid barrier every CTA reads G and factors it itself: the K-step Cholesky chain is
+//     the same on every SM (identical inputs, identical code: identical factors), so no factor
+//     travels back through L2 and no barrier waits for one CTA;
+//   * every CTA then applies the factor to its own rows (spread over the whole grid).
+// Pass 1 factors G1 in the square-root-free form G1 = U^T D U; it only has to precondition, since
+// Y = Q1 R1 holds exactly for the R1 the solve uses. Pass 2 sees G2 = Q1^T Q1 = I + E with
+// |E| ~ cond(Y)^2 eps. When G2 is not within 0.5 / K of the identity (outside the regime in which
+// CholeskyQR2 is orthogonal to rounding level) *flag is set and the caller falls back to
+// Householder with the core unchanged. When max |E| <= 1e-9 the factor is taken in closed form,
+// R2 = I + F with F = triu(E) - diag(E) / 2 (R2^T R2 - G2 = O(|E|^2), below rounding), and its
+// inverse likewise, R2^{-1} = I - F + O(|E|^2), so Q2 = Q1 - Q1 F is a product, not a solve; in
+// between, G2 is factored like G1. The result is R = R2 R1 and Q = Q2.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -25,6 +29,8 @@ namespace {
 constexpr int kS1Threads = 256;
 constexpr int kS1MaxK = 32;
 constexpr int kS1MaxRowsPerCta = 384;
+constexpr int kS1Tile = 4;     // Gram tiles of 4 x 4 column pairs
+constexpr int kS1Chunk = 256;  // rows of a tile's two column blocks staged per step
 
 struct Site1Args {
   double *core0;          // (1, I1, K, t)
@@ -32,8 +38,8 @@ struct Site1Args {
   int I1, K, t;           // t: the rank when t_dev is null, else its upper bound
   int core_out;           // write Q~ back into core0's layout instead of Qout
   const int *gate;        // when not null and 0 on the device: do nothing (an earlier step declined)
-  double *Gpart;        // gridDim.x partial Grams, K x K each
-  double *S, *rdiag;    // the current pass's factor scaled to unit diagonal, and 1 / its diagonal
+  double *Q1;           // m x K scratch, column-major (ld m): the first pass's Q for the second Gram
+  double *G;            // K x K scratch: the current pass's Gram (column-major, symmetric)
   double *Rout;         // K x K: R = R2 R1 (column-major, upper)
   double *Qout;         // m x K, column-major
   int *flag;            // set when the factorisation cannot be trusted
@@ -41,62 +47,88 @@ struct Site1Args {
   int *status;
 };
 
-// 1 / x for finite x > 0 with one Newton step from the FP32 reciprocal (relative error ~2^-46): the
-// pass-1 pivots only have to precondition, since Y = Q1 R1 holds exactly for the R1 the solve uses.
-__device__ __forceinline__ double rcp_f64_1(double x) {
-  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
-  const double xs = x * pow2(-e);
-  double q = (double)(1.0f / (float)xs);
-  q = q * fma(-xs, q, 2.0);
-  return q * pow2(-e);
+// Element (row, c) of the site-1 matrix: core (row mod I1, c, row div I1).
+__device__ __forceinline__ int64_t ycore(int row, int c, int I1, int K) {
+  return (int64_t)(row % I1) + (int64_t)I1 * (c + (int64_t)K * (row / I1));
 }
 
-// Cholesky of the K x K matrix a (shared, column-major, K <= 32) on one CTA of kS1Threads
-// threads: R (upper) to Rs and 1 / diag(R) to rd (both shared; Rs must not alias a). Thread
-// (lane, warp) owns the elements (i = lane, l = warp + 8 u), so no index division is needed.
-// second: the CholeskyQR2 near-identity check and closed-form factor. Returns false (uniform
-// over the CTA) when the factor cannot be used.
-__device__ bool cta_chol(double *a, int K, double *Rs, double *rd, bool second, double *dinv) {
-  __shared__ int s_bad, s_first;
+struct CoreAt {  // Y read from the core (written by earlier launches)
+  const double *core;
+  int I1, K;
+  __device__ double operator()(int r, int c) const { return core[ycore(r, c, I1, K)]; }
+};
+
+struct ColAt {  // column-major m x K matrix written by other CTAs of this launch (through L2)
+  const double *x;
+  int m;
+  __device__ double operator()(int r, int c) const { return __ldcg(x + r + (int64_t)m * c); }
+};
+
+// Pass-1 pivot reciprocal: the FP64 approximate reciprocal instruction refined by one Newton step
+// (its error is far below what preconditioning needs: Y = Q1 R1 holds for the R1 applied).
+__device__ __forceinline__ double rcp_precondition(double x) {
+  double q;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(q) : "d"(x));
+  return fma(q, fma(-x, q, 1.0), q);
+}
+
+// G (K x K, global) <- X^T X for the m x K matrix X (element (r, c) = x_at(r, c)): CTA b takes
+// tiles b, b + gridDim.x, ... of the 4 x 4-tiled upper triangle; a tile's two column blocks are
+// staged in shared memory kS1Chunk rows at a time, thread (pair, slice) sums rows slice, slice +
+// 16, ..., and the 16 slices of a pair are added in order. cols: 2 kS1Tile kS1Chunk doubles.
+template <typename XAt>
+__device__ void gram_tiles(int m, int K, const XAt &x_at, double *G, double *cols) {
+  __shared__ double red[16][17];
+  const int nt = (K + kS1Tile - 1) / kS1Tile, ntiles = nt * (nt + 1) / 2;
+  const int pr = threadIdx.x & 15, sl = threadIdx.x >> 4;
+  const int pi = pr & 3, pj = pr >> 2;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int bi = 0, rem = tile;  // tile -> (bi, bj), bi <= bj, row by row over the upper triangle
+    while (rem >= nt - bi) {
+      rem -= nt - bi;
+      ++bi;
+    }
+    const int bj = bi + rem;
+    const int ci = bi * kS1Tile + pi, cj = bj * kS1Tile + pj;
+    double acc = 0.0;
+    for (int r0 = 0; r0 < m; r0 += kS1Chunk) {
+      const int nr = min(kS1Chunk, m - r0);
+      for (int x = threadIdx.x; x < 2 * kS1Tile * nr; x += blockDim.x) {
+        const int q = x / nr, rr = x - q * nr;  // column slot q: 0..3 block bi, 4..7 block bj
+        const int c = q < kS1Tile ? bi * kS1Tile + q : bj * kS1Tile + q - kS1Tile;
+        cols[q * kS1Chunk + rr] = c < K ? x_at(r0 + rr, c) : 0.0;
+      }
+      __syncthreads();
+      const double *xa = cols + pi * kS1Chunk, *xb = cols + (kS1Tile + pj) * kS1Chunk;
+      for (int rr = sl; rr < nr; rr += 16) acc = fma(xa[rr], xb[rr], acc);
+      __syncthreads();
+    }
+    red[pr][sl] = acc;
+    __syncthreads();
+    if (threadIdx.x < 16 && ci < K && cj < K) {
+      double s = 0.0;
+      for (int q = 0; q < 16; ++q) s += red[pr][q];
+      G[ci + K * cj] = s;
+      if (bi != bj) G[cj + K * ci] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Square-root-free Cholesky G = U^T D U of the K x K matrix a (shared, column-major, K <= 32)
+// on one CTA: on return a(i, l) = d_i u_il for i <= l and dinv[i] = 1 / d_i. Thread (lane, warp)
+// owns the elements (i = lane, l = warp + 8 u). The owner of the next diagonal element forms
+// its reciprocal right after its own update, so it overlaps the other updates of the step.
+// precond: pass-1 reciprocals (rcp_precondition), else full FP64 ones. Returns false (uniform
+// over the CTA) when a pivot is not positive and finite.
+__device__ bool cta_ldl(double *a, int K, double *dinv, bool precond) {
+  __shared__ int s_bad;
   const int i = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kW = kS1Threads / 32;
   if (threadIdx.x == 0) {
-    s_bad = 0;
-    s_first = 1;
-  }
-  __syncthreads();
-  if (second) {
-    bool bad = false, far = false;
-    if (i < K)
-      for (int l = w; l < K; l += kW) {
-        const double dev = fabs(a[i + K * l] - (i == l ? 1.0 : 0.0));
-        bad |= !(dev <= 0.5 / K);
-        far |= !(dev <= 1e-9);
-      }
-    const bool wbad = __any_sync(0xffffffffu, bad), wfar = __any_sync(0xffffffffu, far);
-    if (i == 0 && wbad) s_bad = 1;  // benign races: every writer stores the same value
-    if (i == 0 && wfar) s_first = 0;
-    __syncthreads();
-    if (s_bad) return false;
-    if (s_first) {  // G = I + E, R = I + triu(E) - diag(E) / 2 up to O(|E|^2)
-      if (i < K)
-        for (int l = w; l < K; l += kW) {
-          const double v = i < l ? a[i + K * l] : (i == l ? 0.5 * (1.0 + a[i + K * l]) : 0.0);
-          Rs[i + K * l] = v;
-          if (i == l) rd[i] = rcp_f64(v);
-        }
-      __syncthreads();
-      return true;
-    }
-  }
-  // square-root-free form G = U^T D U: step j updates a_il -= a_ji a_jl / d_j (j < i <= l); the
-  // owner of the next diagonal element forms its reciprocal right after its own update
-  if (threadIdx.x == 0) {
     const double d0 = a[0];
-    if (!(d0 > 0.0) || !isfinite(d0))
-      s_bad = 1;
-    else
-      dinv[0] = second ? rcp_f64(d0) : rcp_f64_1(d0);
+    s_bad = !(d0 > 0.0) || !isfinite(d0);
+    if (!s_bad) dinv[0] = precond ? rcp_precondition(d0) : rcp_f64(d0);
   }
   __syncthreads();
   if (s_bad) return false;
@@ -104,13 +136,13 @@ __device__ bool cta_chol(double *a, int K, double *Rs, double *rd, bool second, 
   for (int j = 0; j < K; ++j) {
     if (i > j && i < K) {
       const double f = a[j + K * i] * dinv[j];
-      if (own_diag && i == j + 1) {  // the next pivot first: its reciprocal overlaps the other updates
+      if (own_diag && i == j + 1) {
         const double v = fma(-f, a[j + K * i], a[i + K * i]);
         a[i + K * i] = v;
         if (!(v > 0.0) || !isfinite(v))
           s_bad = 1;
         else
-          dinv[j + 1] = second ? rcp_f64(v) : rcp_f64_1(v);
+          dinv[j + 1] = precond ? rcp_precondition(v) : rcp_f64(v);
       }
       for (int l = w; l < K; l += kW) {
         if (l < i || (l == i && i == j + 1)) continue;
@@ -120,24 +152,55 @@ __device__ bool cta_chol(double *a, int K, double *Rs, double *rd, bool second, 
     __syncthreads();
     if (s_bad) return false;
   }
-  // R(i, l) = a_il / sqrt(d_i)
-  if (i < K)
-    for (int l = w; l < K; l += kW) {
-      const double ri = rsqrt_f64(a[i + K * i]);
-      Rs[i + K * l] = i <= l ? a[i + K * l] * ri : 0.0;
-      if (i == l) rd[i] = ri;
-    }
-  __syncthreads();
   return true;
 }
 
+// y <- y R^{-1} for the rows of ys (row-major, leading dimension K + 1), warp per row, lane c
+// owns column c: with R = D^{1/2} U (U unit upper, a(j, c) = d_j u_jc), step j broadcasts the
+// current y_j and lanes c > j subtract y_j u_jc; finally x_c = y_c / sqrt(d_c).
+__device__ void rows_solve(double *ys, int nr, int K, const double *a, const double *dinv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, ld = K + 1;
+  double u[kS1MaxK];
+#pragma unroll
+  for (int j = 0; j < kS1MaxK; ++j) u[j] = (lane < K && j < lane) ? a[j + K * lane] * dinv[j] : 0.0;
+  const double rd = lane < K ? rsqrt_f64(a[lane + K * lane]) : 0.0;
+  for (int rr = warp; rr < nr; rr += nw) {
+    double y = lane < K ? ys[rr * ld + lane] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kS1MaxK; ++j) {
+      if (j >= K) break;
+      const double yj = __shfl_sync(0xffffffffu, y, j);
+      y = fma(-yj, u[j], y);  // u[j] = 0 for j >= lane
+    }
+    if (lane < K) ys[rr * ld + lane] = y * rd;
+  }
+}
+
+// y <- y - y F for the rows of ys with F (K x K, upper, shared) = triu(E) - diag(E) / 2: the
+// closed-form R2^{-1} = I - F applied (two interleaved chains per lane).
+__device__ void rows_apply_closed(double *ys, int nr, int K, const double *F) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, ld = K + 1;
+  double f[kS1MaxK];
+#pragma unroll
+  for (int j = 0; j < kS1MaxK; ++j) f[j] = (lane < K && j < K) ? F[j + K * lane] : 0.0;
+  for (int rr = warp; rr < nr; rr += nw) {
+    const double y = lane < K ? ys[rr * ld + lane] : 0.0;
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < kS1MaxK; j += 2) {
+      s0 = fma(__shfl_sync(0xffffffffu, y, j), f[j], s0);
+      s1 = fma(__shfl_sync(0xffffffffu, y, j + 1), f[j + 1], s1);
+    }
+    if (lane < K) ys[rr * ld + lane] = y - (s0 + s1);
+  }
+}
+
 __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
-  extern __shared__ double ys[];  // own rows, row-major with leading dimension K + 1 (odd: no bank conflicts)
-  __shared__ double am[kS1MaxK * kS1MaxK];  // CTA 0: summed Gram, then the Cholesky workspace
-  __shared__ double r1s[kS1MaxK * kS1MaxK];
-  __shared__ double r2s[kS1MaxK * kS1MaxK];
-  __shared__ double rdv[kS1MaxK];
+  extern __shared__ double dyn[];            // own rows (leading dimension K + 1), then tile staging
+  __shared__ double am[kS1MaxK * kS1MaxK];   // the current Gram, then its factor
+  __shared__ double r1s[kS1MaxK * kS1MaxK];  // CTA 0: R1 (for R = R2 R1)
   __shared__ double dinv[kS1MaxK];
+  __shared__ int s_mode;
   if (a.gate && __ldcg(a.gate) == 0) return;  // uniform: written by an earlier launch
   const int K = a.K, I1 = a.I1, tid = threadIdx.x, nthr = blockDim.x;
   const int64_t td = a.t_dev ? __ldcg(a.t_dev) : a.t;
@@ -145,134 +208,101 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
     return;
   }
-  const int m = I1 * (int)td;  // rows; the grid covers the bound
-  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int m = I1 * (int)td;
   const int ld = K + 1;
-  // about 16 rows per CTA on the first nb CTAs (the others only take part in the barriers)
-  const int nb = min((int)gridDim.x, max(1, (m + 15) / 16));
-  const int rpc = (m + nb - 1) / nb;
+  const int rpc = (m + (int)gridDim.x - 1) / (int)gridDim.x;  // rows per CTA (the host sized for the bound)
   const int r0 = blockIdx.x * rpc;
-  const int nr = (int)blockIdx.x < nb ? max(0, min(rpc, m - r0)) : 0;
-  if (blockIdx.x == 0 && tid == 0) *a.flag = 0;  // read only after the next grid barrier
-  // own rows of A1^T: row i + I1 r, column c <- core (i, c, r); consecutive threads, consecutive rows
+  const int nr = max(0, min(rpc, m - r0));
+  double *ys = dyn, *cols = dyn + (size_t)rpc * ld;
+  if (blockIdx.x == 0 && tid == 0) *a.flag = 0;
+  // own rows of Y: row i + I1 r, column c <- core (i, c, r)
   for (int x = tid; x < nr * K; x += nthr) {
-    const int rr = x % nr, c = x / nr, row = r0 + rr;
-    ys[rr * ld + c] = a.core0[row % I1 + I1 * (c + K * (row / I1))];
+    const int rr = x % nr, c = x / nr;
+    ys[rr * ld + c] = a.core0[ycore(r0 + rr, c, I1, K)];
   }
+  // ---- pass 1: G1 = Y^T Y by tiles, then every CTA factors it and solves its rows
+  gram_tiles(m, K, CoreAt{a.core0, I1, K}, a.G, cols);
+  grid_barrier(a.bar, a.status);
+  for (int e = tid; e < K * K; e += nthr) am[e] = __ldcg(a.G + e);
   __syncthreads();
-  const int npair = K * (K + 1) / 2;
-  double *Gp = a.Gpart + (size_t)blockIdx.x * K * K;
-  for (int pass = 0; pass < 2; ++pass) {
-    // symmetric partial Gram of the own rows (CTAs without rows write nothing: only the first nb
-    // partials are summed)
-    for (int e = tid; e < npair && (int)blockIdx.x < nb; e += nthr) {
-      int j = 0, base = 0;
-      while (base + j + 1 <= e) {
-        base += j + 1;
-        ++j;
-      }
-      const int i = e - base;
-      double s0 = 0.0, s1 = 0.0;
-      int rr = 0;
-      for (; rr + 1 < nr; rr += 2) {
-        s0 = fma(ys[rr * ld + i], ys[rr * ld + j], s0);
-        s1 = fma(ys[(rr + 1) * ld + i], ys[(rr + 1) * ld + j], s1);
-      }
-      if (rr < nr) s0 = fma(ys[rr * ld + i], ys[rr * ld + j], s0);
-      Gp[i + K * j] = s0 + s1;
-      Gp[j + K * i] = s0 + s1;
+  if (!cta_ldl(am, K, dinv, true)) {
+    if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
+    return;  // uniform: every CTA factored the same matrix
+  }
+  if (blockIdx.x == 0)  // R1(i, l) = d_i u_il / sqrt(d_i)
+    for (int e = tid; e < K * K; e += nthr) {
+      const int i = e % K, l = e / K;
+      r1s[e] = i <= l ? am[i + K * l] * rsqrt_f64(am[i + K * i]) : 0.0;
     }
-    grid_barrier(a.bar, a.status);
-    if (blockIdx.x == 0) {
-      // fixed-order sum of the partials (deterministic); four loads in flight per step
-      const size_t KK = (size_t)K * K;
-      constexpr int kE = kS1MaxK * kS1MaxK / kS1Threads;  // elements per thread (4)
-      double acc[kE];
-#pragma unroll
-      for (int u = 0; u < kE; ++u) acc[u] = 0.0;
-      for (unsigned b0 = 0; (int)b0 < nb; b0 += 8) {
-        double p[8][kE];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll
-          for (int u = 0; u < kE; ++u) {
-            const int e = tid + u * kS1Threads;
-            p[q][u] = ((int)(b0 + q) < nb && e < K * K) ? __ldcg(a.Gpart + (b0 + q) * KK + e) : 0.0;
-          }
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll
-          for (int u = 0; u < kE; ++u) acc[u] += p[q][u];
-      }
-#pragma unroll
-      for (int u = 0; u < kE; ++u) {
-        const int e = tid + u * kS1Threads;
-        if (e < K * K) am[e] = acc[u];
-      }
-      __syncthreads();
-      double *Rs = pass == 0 ? r1s : r2s;
-      if (!cta_chol(am, K, Rs, rdv, pass == 1, dinv)) {
-        if (tid == 0) *a.flag = 1;
-      } else {
-        // for the solves: S = diag(1 / R_jj) R (unit upper) to a.S, 1 / R_jj to a.rdiag
-        for (int e = tid; e < K * K; e += nthr) {
-          const int j = e % K;
-          a.S[e] = Rs[e] * rdv[j];
-        }
-        if (tid < K) a.rdiag[tid] = rdv[tid];
-      }
+  rows_solve(ys, nr, K, am, dinv);
+  __syncthreads();
+  for (int x = tid; x < nr * K; x += nthr) {  // Q1 rows for the second Gram
+    const int rr = x % nr, c = x / nr;
+    a.Q1[(r0 + rr) + (int64_t)m * c] = ys[rr * ld + c];
+  }
+  grid_barrier(a.bar, a.status);
+  // ---- pass 2: G2 = Q1^T Q1 by tiles, checked (and factored when needed) by every CTA
+  gram_tiles(m, K, ColAt{a.Q1, m}, a.G, cols);
+  grid_barrier(a.bar, a.status);
+  for (int e = tid; e < K * K; e += nthr) am[e] = __ldcg(a.G + e);
+  if (tid == 0) s_mode = 2;  // 2: closed form, 1: factor G2, 0: not near the identity
+  __syncthreads();
+  {
+    bool bad = false, far = false;
+    for (int e = tid; e < K * K; e += nthr) {
+      const double dev = fabs(am[e] - ((e % K) == (e / K) ? 1.0 : 0.0));
+      bad |= !(dev <= 0.5 / K);
+      far |= !(dev <= 1e-9);
     }
-    grid_barrier(a.bar, a.status);
-    if (__ldcg(a.flag) != 0) return;  // every thread of every CTA reads the same value
-    // Y <- Y R^{-1} row by row (warp per row, lane c owns column c): with S = diag(1/R_jj) R,
-    // step j broadcasts the current y_j and lanes c > j subtract y_j S_jc; finally x_c = y_c / R_cc.
-    // Two rows per warp at a time (independent chains).
-    double sl[kS1MaxK];
-#pragma unroll
-    for (int j = 0; j < kS1MaxK; ++j) sl[j] = (lane < K && j < K) ? __ldcg(a.S + j + K * lane) : 0.0;
-    const double rd = lane < K ? __ldcg(a.rdiag + lane) : 0.0;
-    for (int rr = warp; rr < nr; rr += 2 * nw) {
-      const int rr2 = rr + nw;
-      const bool two = rr2 < nr;
-      double y0 = lane < K ? ys[rr * ld + lane] : 0.0;
-      double y1 = (two && lane < K) ? ys[rr2 * ld + lane] : 0.0;
-#pragma unroll
-      for (int j = 0; j < kS1MaxK; ++j) {
-        if (j >= K) break;
-        const double u0 = __shfl_sync(0xffffffffu, y0, j), u1 = __shfl_sync(0xffffffffu, y1, j);
-        if (lane > j) {
-          y0 = fma(-u0, sl[j], y0);
-          y1 = fma(-u1, sl[j], y1);
-        }
-      }
-      if (lane < K) {
-        ys[rr * ld + lane] = y0 * rd;
-        if (two) ys[rr2 * ld + lane] = y1 * rd;
-      }
-    }
+    const bool wbad = __any_sync(0xffffffffu, bad), wfar = __any_sync(0xffffffffu, far);
+    if ((tid & 31) == 0 && wfar) atomicMin(&s_mode, 1);
+    if ((tid & 31) == 0 && wbad) atomicMin(&s_mode, 0);
     __syncthreads();
   }
+  const int mode = s_mode;
+  if (mode == 0) {
+    if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
+    return;  // uniform; the core is unchanged
+  }
+  if (mode == 2) {
+    // F = triu(E) - diag(E) / 2 in place (E = G2 - I); R2 = I + F
+    __syncthreads();
+    for (int e = tid; e < K * K; e += nthr) {
+      const int i = e % K, l = e / K;
+      am[e] = i < l ? am[e] : (i == l ? 0.5 * (am[e] - 1.0) : 0.0);
+    }
+    __syncthreads();
+    rows_apply_closed(ys, nr, K, am);
+  } else {
+    if (!cta_ldl(am, K, dinv, false)) {
+      if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
+      return;
+    }
+    rows_solve(ys, nr, K, am, dinv);
+  }
+  __syncthreads();
   // Q~: column-major, or back into the core's layout (each CTA writes only the rows it read)
   for (int x = tid; x < nr * K; x += nthr) {
     const int rr = x % nr, c = x / nr, row = r0 + rr;
     if (a.core_out)
-      a.core0[row % I1 + I1 * (c + K * (row / I1))] = ys[rr * ld + c];
+      a.core0[ycore(row, c, I1, K)] = ys[rr * ld + c];
     else
       a.Qout[row + (size_t)m * c] = ys[rr * ld + c];
   }
-  if (blockIdx.x == 0)  // R~ = R2 R1 (both upper, in shared memory)
+  if (blockIdx.x == 0)  // R~ = R2 R1 (both upper); R2 = I + F, or D^{1/2} U from the factor of G2
     for (int e = tid; e < K * K; e += nthr) {
       const int i = e % K, l = e / K;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int q = i;
-      for (; q + 3 <= l; q += 4) {
-        s0 = fma(r2s[i + K * q], r1s[q + K * l], s0);
-        s1 = fma(r2s[i + K * (q + 1)], r1s[q + 1 + K * l], s1);
-        s2 = fma(r2s[i + K * (q + 2)], r1s[q + 2 + K * l], s2);
-        s3 = fma(r2s[i + K * (q + 3)], r1s[q + 3 + K * l], s3);
+      double s0 = 0.0;
+      if (i <= l) {
+        if (mode == 2) {
+          s0 = r1s[i + K * l];
+          for (int q = i; q <= l; ++q) s0 = fma(am[i + K * q], r1s[q + K * l], s0);
+        } else {
+          const double ri = rsqrt_f64(am[i + K * i]);
+          for (int q = i; q <= l; ++q) s0 = fma(am[i + K * q] * ri, r1s[q + K * l], s0);
+        }
       }
-      for (; q <= l; ++q) s0 = fma(r2s[i + K * q], r1s[q + K * l], s0);
-      a.Rout[e] = i <= l ? (s0 + s1) + (s2 + s3) : 0.0;
+      a.Rout[e] = s0;
     }
 }
 
@@ -283,21 +313,22 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
 // *flag (device) = 1 when the caller must fall back to Householder (core0 is then unchanged).
 // t_dev: when not null the rank is read there on the device and t is only its upper bound.
 // gate: when not null, the kernel does nothing unless *gate != 0 on the device.
-// Scratch: Gpart (gcap doubles), S (K x K), rdiag (K). *launched = false (nothing queued) when the
-// sizes are outside the kernel's layout (K > 32, more rows than 64 CTAs hold) or gcap is too small.
+// Scratch: Q1 (q1cap doubles, at least (I1 t) K), G (K x K). *launched = false (nothing queued)
+// when the sizes are outside the kernel's layout (K > 32, more rows than the grid holds) or the
+// scratch is too small.
 int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
-                  const int *gate, double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout,
-                  int *flag, unsigned *bar, bool *launched) {
+                  const int *gate, double *Q1, int64_t q1cap, double *G, double *Rout, double *Qout, int *flag,
+                  unsigned *bar, bool *launched) {
   *launched = false;
   const int64_t m = I1 * t;
-  if (K < 1 || K > kS1MaxK || m < K || m > (int64_t)64 * kS1MaxRowsPerCta) return TNR_OK;
+  if (K < 1 || K > kS1MaxK || m < K || m * K > q1cap) return TNR_OK;
   int dev = 0, sms = 0;
   TNR_CK(cudaGetDevice(&dev));
   TNR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t nblk = std::min<int64_t>(std::min<int64_t>(64, sms), std::max<int64_t>(1, cdiv(m, 16)));
-  const int64_t rpc = std::max<int64_t>(16, cdiv(m, nblk));  // the device's rows per CTA never exceed this
-  if (rpc > kS1MaxRowsPerCta || nblk * K * K > gcap) return TNR_OK;
-  const size_t smem = sizeof(double) * (size_t)(rpc * (K + 1));
+  const int64_t nblk = std::min<int64_t>(64, sms);
+  const int64_t rpc = cdiv(m, nblk);  // the device's rows per CTA never exceed this
+  if (rpc > kS1MaxRowsPerCta) return TNR_OK;
+  const size_t smem = sizeof(double) * (size_t)(rpc * (K + 1) + 2 * kS1Tile * kS1Chunk);
   TNR_TRY(ensure_dynamic_smem((const void *)k_site1_cholqr2, smem));
   Site1Args a;
   a.core0 = core0;
@@ -307,9 +338,8 @@ int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t 
   a.t = (int)t;
   a.core_out = core_out ? 1 : 0;
   a.gate = gate;
-  a.Gpart = Gpart;
-  a.S = S;
-  a.rdiag = rdiag;
+  a.Q1 = Q1;
+  a.G = G;
   a.Rout = Rout;
   a.Qout = Qout;
   a.flag = flag;

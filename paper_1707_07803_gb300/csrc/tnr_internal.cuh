@@ -217,8 +217,8 @@ int round_small(cudaStream_t s, const tnr_mpo &Y, double tol, int64_t max_rank, 
 // rank in device memory, t then being its upper bound; gate (may be null): run only when *gate
 // != 0 on the device. *launched = false when the sizes are outside its layout.
 int site1_cholqr2(cudaStream_t s, double *core0, int64_t I1, int64_t K, int64_t t, const int64_t *t_dev, bool core_out,
-                  const int *gate, double *Gpart, int64_t gcap, double *S, double *rdiag, double *Rout, double *Qout,
-                  int *flag, unsigned *bar, bool *launched);
+                  const int *gate, double *Q1, int64_t q1cap, double *G, double *Rout, double *Qout, int *flag,
+                  unsigned *bar, bool *launched);
 
 // Lemma 5.1 normal draws (SplitMix64 + Box-Muller), `count` values in draw order.
 int omega_fill(cudaStream_t s, uint64_t seed, int64_t count, double *out);

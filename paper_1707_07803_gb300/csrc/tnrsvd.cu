@@ -421,7 +421,7 @@ int site1_qr(cudaStream_t s, tnr_mpo &Y, bool pending, bool core_out, Bufs &b) {
   bool launched = false;
   int *flag = b.ctl + 1;
   TNR_TRY(site1_cholqr2(s, Y.core[0], I1, K, Y.R[1], pending ? b.rdev + 1 : nullptr, core_out, nullptr, b.US, b.cap,
-                        b.Vr, b.Sv, b.Rm, b.Mq, flag, b.bar, &launched));
+                        b.Vr, b.Rm, b.Mq, flag, b.bar, &launched));
   int hflag = 1;
   if (launched) {
     TNR_TRY(read_ranks(s, Y, b, pending, &hflag));
@@ -451,7 +451,7 @@ int reduce_and_site1(cudaStream_t s, tnr_mpo &Y, double tol, int64_t max_rank, d
     if (launched) {
       bool s1 = false;
       TNR_TRY(site1_cholqr2(s, Y.core[0], Y.I[0], Y.J[0], Y.R[1], Rround + 1, core_out, b.ctl + 2, b.US, b.cap, b.Vr,
-                            b.Sv, b.Rm, b.Mq, b.ctl + 1, b.bar, &s1));
+                            b.Rm, b.Mq, b.ctl + 1, b.bar, &s1));
       int64_t h[2 * (TNR_MAX_SITES + 1)];
       int hctl[3] = {0, 0, 0};
       const ReadBack rb[2] = {{h, b.rdev, sizeof(int64_t) * 2 * (TNR_MAX_SITES + 1)}, {hctl, b.ctl, sizeof(hctl)}};

@@ -13,10 +13,12 @@
 // Y = Q1 R1 holds exactly for the R1 the solve uses. Pass 2 sees G2 = Q1^T Q1 = I + E with
 // |E| ~ cond(Y)^2 eps. When G2 is not within 0.5 / K of the identity (outside the regime in which
 // CholeskyQR2 is orthogonal to rounding level) *flag is set and the caller falls back to
-// Householder with the core unchanged. When max |E| <= 1e-9 the factor is taken in closed form,
-// R2 = I + F with F = triu(E) - diag(E) / 2 (R2^T R2 - G2 = O(|E|^2), below rounding), and its
-// inverse likewise, R2^{-1} = I - F + O(|E|^2), so Q2 = Q1 - Q1 F is a product, not a solve; in
-// between, G2 is factored like G1. The result is R = R2 R1 and Q = Q2.
+// Householder with the core unchanged. When K max|E| <= 1e-4 its factor is taken from the series
+// of the Cholesky factor of I + E instead of a K-step pivot chain: with Phi(M) = triu(M) -
+// diag(M) / 2 (so that Phi(M) + Phi(M)^T = M for symmetric M), R2 = I + X solves X + X^T + X^T X
+// = E exactly when X = Phi(E - X^T X); three fixed-point steps from X = 0 leave R2^T R2 - G2 =
+// O(|E|^4) <= (K max|E|)^4 <= 1e-16, below rounding. Otherwise G2 is factored like G1. The
+// result is R = R2 R1 and Q = Y R1^{-1} R2^{-1}.
 #include <algorithm>
 
 #include "dev_common.cuh"
@@ -29,8 +31,9 @@ namespace {
 constexpr int kS1Threads = 256;
 constexpr int kS1MaxK = 32;
 constexpr int kS1MaxRowsPerCta = 384;
-constexpr int kS1Tile = 4;     // Gram tiles of 4 x 4 column pairs
-constexpr int kS1Chunk = 256;  // rows of a tile's two column blocks staged per step
+constexpr int kS1Ld = kS1MaxK + 1;  // leading dimension of the K x K work matrices (no bank conflicts)
+constexpr int kS1Tile = 4;          // Gram tiles of 4 x 4 column pairs
+constexpr int kS1Chunk = 512;       // rows of a tile's two column blocks staged per step
 
 struct Site1Args {
   double *core0;          // (1, I1, K, t)
@@ -115,8 +118,8 @@ __device__ void gram_tiles(int m, int K, const XAt &x_at, double *G, double *col
   }
 }
 
-// Square-root-free Cholesky G = U^T D U of the K x K matrix a (shared, column-major, K <= 32)
-// on one CTA: on return a(i, l) = d_i u_il for i <= l and dinv[i] = 1 / d_i. Thread (lane, warp)
+// Square-root-free Cholesky G = U^T D U of the K x K matrix a (shared, column-major with leading
+// dimension kS1Ld, K <= 32) on one CTA: on return a(i, l) = d_i u_il for i <= l, dinv[i] = 1 / d_i. Thread (lane, warp)
 // owns the elements (i = lane, l = warp + 8 u). The owner of the next diagonal element forms
 // its reciprocal right after its own update, so it overlaps the other updates of the step.
 // precond: pass-1 reciprocals (rcp_precondition), else full FP64 ones. Returns false (uniform
@@ -135,10 +138,10 @@ __device__ bool cta_ldl(double *a, int K, double *dinv, bool precond) {
   const bool own_diag = i < K && (i % kW) == w;  // this thread holds (i, i)
   for (int j = 0; j < K; ++j) {
     if (i > j && i < K) {
-      const double f = a[j + K * i] * dinv[j];
+      const double f = a[j + kS1Ld * i] * dinv[j];
       if (own_diag && i == j + 1) {
-        const double v = fma(-f, a[j + K * i], a[i + K * i]);
-        a[i + K * i] = v;
+        const double v = fma(-f, a[j + kS1Ld * i], a[i + kS1Ld * i]);
+        a[i + kS1Ld * i] = v;
         if (!(v > 0.0) || !isfinite(v))
           s_bad = 1;
         else
@@ -146,7 +149,7 @@ __device__ bool cta_ldl(double *a, int K, double *dinv, bool precond) {
       }
       for (int l = w; l < K; l += kW) {
         if (l < i || (l == i && i == j + 1)) continue;
-        a[i + K * l] = fma(-f, a[j + K * l], a[i + K * l]);
+        a[i + kS1Ld * l] = fma(-f, a[j + kS1Ld * l], a[i + kS1Ld * l]);
       }
     }
     __syncthreads();
@@ -156,14 +159,16 @@ __device__ bool cta_ldl(double *a, int K, double *dinv, bool precond) {
 }
 
 // y <- y R^{-1} for the rows of ys (row-major, leading dimension K + 1), warp per row, lane c
-// owns column c: with R = D^{1/2} U (U unit upper, a(j, c) = d_j u_jc), step j broadcasts the
-// current y_j and lanes c > j subtract y_j u_jc; finally x_c = y_c / sqrt(d_c).
-__device__ void rows_solve(double *ys, int nr, int K, const double *a, const double *dinv) {
+// owns column c. R is given as Ru (upper, leading dimension kS1Ld) with u_jc = Ru(j, c) sc_j the
+// unit upper factor of R = diag(R_jj) U and fin_c = 1 / R_cc: step j broadcasts the current y_j
+// and lanes c > j subtract y_j u_jc; finally x_c = y_c fin_c. (Square-root-free factor: Ru = D U,
+// sc = 1 / d, fin = 1 / sqrt(d); explicit R: Ru = R, sc = fin = 1 / diag(R).)
+__device__ void rows_solve(double *ys, int nr, int K, const double *Ru, const double *sc, const double *fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, ld = K + 1;
   double u[kS1MaxK];
 #pragma unroll
-  for (int j = 0; j < kS1MaxK; ++j) u[j] = (lane < K && j < lane) ? a[j + K * lane] * dinv[j] : 0.0;
-  const double rd = lane < K ? rsqrt_f64(a[lane + K * lane]) : 0.0;
+  for (int j = 0; j < kS1MaxK; ++j) u[j] = (lane < K && j < lane) ? Ru[j + kS1Ld * lane] * sc[j] : 0.0;
+  const double rd = lane < K ? fin[lane] : 0.0;
   for (int rr = warp; rr < nr; rr += nw) {
     double y = lane < K ? ys[rr * ld + lane] : 0.0;
 #pragma unroll
@@ -176,31 +181,40 @@ __device__ void rows_solve(double *ys, int nr, int K, const double *a, const dou
   }
 }
 
-// y <- y - y F for the rows of ys with F (K x K, upper, shared) = triu(E) - diag(E) / 2: the
-// closed-form R2^{-1} = I - F applied (two interleaved chains per lane).
-__device__ void rows_apply_closed(double *ys, int nr, int K, const double *F) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, ld = K + 1;
-  double f[kS1MaxK];
-#pragma unroll
-  for (int j = 0; j < kS1MaxK; ++j) f[j] = (lane < K && j < K) ? F[j + K * lane] : 0.0;
-  for (int rr = warp; rr < nr; rr += nw) {
-    const double y = lane < K ? ys[rr * ld + lane] : 0.0;
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int j = 0; j < kS1MaxK; j += 2) {
-      s0 = fma(__shfl_sync(0xffffffffu, y, j), f[j], s0);
-      s1 = fma(__shfl_sync(0xffffffffu, y, j + 1), f[j + 1], s1);
-    }
-    if (lane < K) ys[rr * ld + lane] = y - (s0 + s1);
+// X <- Phi(E - X^T X) for E = a - I (a: G2 in shared memory), the fixed-point step of the series
+// of the Cholesky factor of I + E; xs, ps: K x K work (leading dimension kS1Ld), xs = X on entry
+// (ignored when first) and on exit. (X^T X)(i, l) = sum_{q <= i} X(q, i) X(q, l) for i <= l: a
+// warp takes whole rows i (lanes over l, so its loop length i + 1 is uniform), rows paired as
+// i and K - 1 - i so that every warp's dependent chain has the same length.
+__device__ void chol_series_step(const double *a, double *xs, double *ps, int K, bool first) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (!first)
+    for (int h = warp; h < (K + 1) / 2; h += nw)
+      for (int side = 0; side < 2; ++side) {
+        const int i = side == 0 ? h : K - 1 - h;
+        if (side == 1 && i == h) break;
+        double p = 0.0;
+        if (lane < K && lane >= i)
+          for (int q = 0; q <= i; ++q) p = fma(xs[q + kS1Ld * i], xs[q + kS1Ld * lane], p);
+        if (lane < K) ps[i + kS1Ld * lane] = p;
+      }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e % K, l = e / K;
+    const double m = a[i + kS1Ld * l] - (i == l ? 1.0 : 0.0) - (first ? 0.0 : ps[i + kS1Ld * l]);
+    xs[i + kS1Ld * l] = i < l ? m : (i == l ? 0.5 * m : 0.0);
   }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
-  extern __shared__ double dyn[];            // own rows (leading dimension K + 1), then tile staging
-  __shared__ double am[kS1MaxK * kS1MaxK];   // the current Gram, then its factor
-  __shared__ double r1s[kS1MaxK * kS1MaxK];  // CTA 0: R1 (for R = R2 R1)
-  __shared__ double dinv[kS1MaxK];
-  __shared__ int s_mode;
+  extern __shared__ double dyn[];         // own rows (leading dimension K + 1), then tile staging
+  __shared__ double am[kS1MaxK * kS1Ld];   // the current Gram, then its factor
+  __shared__ double r1s[kS1MaxK * kS1Ld];  // R1
+  __shared__ double xs[kS1MaxK * kS1Ld];   // R2 (series: X, then I + X)
+  __shared__ double ps[kS1MaxK * kS1Ld];   // series work
+  __shared__ double dinv[kS1MaxK], rd1[kS1MaxK], rd2[kS1MaxK];
+  __shared__ unsigned long long s_emax;
   if (a.gate && __ldcg(a.gate) == 0) return;  // uniform: written by an earlier launch
   const int K = a.K, I1 = a.I1, tid = threadIdx.x, nthr = blockDim.x;
   const int64_t td = a.t_dev ? __ldcg(a.t_dev) : a.t;
@@ -223,62 +237,73 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   // ---- pass 1: G1 = Y^T Y by tiles, then every CTA factors it and solves its rows
   gram_tiles(m, K, CoreAt{a.core0, I1, K}, a.G, cols);
   grid_barrier(a.bar, a.status);
-  for (int e = tid; e < K * K; e += nthr) am[e] = __ldcg(a.G + e);
+  for (int e = tid; e < K * K; e += nthr) am[(e % K) + kS1Ld * (e / K)] = __ldcg(a.G + e);
   __syncthreads();
   if (!cta_ldl(am, K, dinv, true)) {
     if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
     return;  // uniform: every CTA factored the same matrix
   }
-  if (blockIdx.x == 0)  // R1(i, l) = d_i u_il / sqrt(d_i)
-    for (int e = tid; e < K * K; e += nthr) {
-      const int i = e % K, l = e / K;
-      r1s[e] = i <= l ? am[i + K * l] * rsqrt_f64(am[i + K * i]) : 0.0;
-    }
-  rows_solve(ys, nr, K, am, dinv);
+  if (tid < K) rd1[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+  __syncthreads();
+  for (int e = tid; e < K * K; e += nthr) {  // R1(i, l) = d_i u_il / sqrt(d_i)
+    const int i = e % K, l = e / K;
+    r1s[i + kS1Ld * l] = i <= l ? am[i + kS1Ld * l] * rd1[i] : 0.0;
+  }
+  rows_solve(ys, nr, K, am, dinv, rd1);
   __syncthreads();
   for (int x = tid; x < nr * K; x += nthr) {  // Q1 rows for the second Gram
     const int rr = x % nr, c = x / nr;
     a.Q1[(r0 + rr) + (int64_t)m * c] = ys[rr * ld + c];
   }
   grid_barrier(a.bar, a.status);
-  // ---- pass 2: G2 = Q1^T Q1 by tiles, checked (and factored when needed) by every CTA
+  // ---- pass 2: G2 = Q1^T Q1 by tiles, checked and factored by every CTA
   gram_tiles(m, K, ColAt{a.Q1, m}, a.G, cols);
   grid_barrier(a.bar, a.status);
-  for (int e = tid; e < K * K; e += nthr) am[e] = __ldcg(a.G + e);
-  if (tid == 0) s_mode = 2;  // 2: closed form, 1: factor G2, 0: not near the identity
-  __syncthreads();
-  {
-    bool bad = false, far = false;
-    for (int e = tid; e < K * K; e += nthr) {
-      const double dev = fabs(am[e] - ((e % K) == (e / K) ? 1.0 : 0.0));
-      bad |= !(dev <= 0.5 / K);
-      far |= !(dev <= 1e-9);
-    }
-    const bool wbad = __any_sync(0xffffffffu, bad), wfar = __any_sync(0xffffffffu, far);
-    if ((tid & 31) == 0 && wfar) atomicMin(&s_mode, 1);
-    if ((tid & 31) == 0 && wbad) atomicMin(&s_mode, 0);
-    __syncthreads();
+  if (tid == 0) s_emax = 0ull;
+  double dev = 0.0;
+  for (int e = tid; e < K * K; e += nthr) {
+    const int i = e % K, l = e / K;
+    const double g = __ldcg(a.G + e);
+    am[i + kS1Ld * l] = g;
+    const double d = fabs(g - (i == l ? 1.0 : 0.0));
+    dev = (d > dev || d != d) ? d : dev;  // a NaN wins (and fails the checks below)
   }
-  const int mode = s_mode;
-  if (mode == 0) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_xor_sync(0xffffffffu, dev, o);
+    dev = (x > dev || x != x) ? x : dev;
+  }
+  __syncthreads();
+  // non-negative doubles order like their bit patterns (a NaN's is larger than any)
+  if ((tid & 31) == 0) atomicMax(&s_emax, (unsigned long long)__double_as_longlong(dev));
+  __syncthreads();
+  const double emax = __longlong_as_double((long long)s_emax);
+  if (!(emax <= 0.5 / K)) {
     if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
     return;  // uniform; the core is unchanged
   }
-  if (mode == 2) {
-    // F = triu(E) - diag(E) / 2 in place (E = G2 - I); R2 = I + F
-    __syncthreads();
-    for (int e = tid; e < K * K; e += nthr) {
-      const int i = e % K, l = e / K;
-      am[e] = i < l ? am[e] : (i == l ? 0.5 * (am[e] - 1.0) : 0.0);
+  if (K * emax <= 1e-4) {  // R2 = I + X from three steps of the series
+    chol_series_step(am, xs, ps, K, true);
+    chol_series_step(am, xs, ps, K, false);
+    chol_series_step(am, xs, ps, K, false);
+    if (tid < K) {
+      const double r = 1.0 + xs[tid + kS1Ld * tid];
+      xs[tid + kS1Ld * tid] = r;
+      rd2[tid] = rcp_f64(r);
     }
     __syncthreads();
-    rows_apply_closed(ys, nr, K, am);
+    rows_solve(ys, nr, K, xs, rd2, rd2);
   } else {
     if (!cta_ldl(am, K, dinv, false)) {
       if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
       return;
     }
-    rows_solve(ys, nr, K, am, dinv);
+    if (tid < K) rd2[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+    __syncthreads();
+    for (int e = tid; e < K * K; e += nthr) {  // R2 explicitly, for R = R2 R1
+      const int i = e % K, l = e / K;
+      xs[i + kS1Ld * l] = i <= l ? am[i + kS1Ld * l] * rd2[i] : 0.0;
+    }
+    rows_solve(ys, nr, K, am, dinv, rd2);
   }
   __syncthreads();
   // Q~: column-major, or back into the core's layout (each CTA writes only the rows it read)
@@ -289,20 +314,14 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     else
       a.Qout[row + (size_t)m * c] = ys[rr * ld + c];
   }
-  if (blockIdx.x == 0)  // R~ = R2 R1 (both upper); R2 = I + F, or D^{1/2} U from the factor of G2
-    for (int e = tid; e < K * K; e += nthr) {
-      const int i = e % K, l = e / K;
+  // R~ = R2 R1 (both upper): column l by CTA l (every CTA holds both factors)
+  if (tid < 32)
+    for (int l = blockIdx.x; l < K; l += gridDim.x) {
+      const int i = tid;
+      if (i >= K) continue;
       double s0 = 0.0;
-      if (i <= l) {
-        if (mode == 2) {
-          s0 = r1s[i + K * l];
-          for (int q = i; q <= l; ++q) s0 = fma(am[i + K * q], r1s[q + K * l], s0);
-        } else {
-          const double ri = rsqrt_f64(am[i + K * i]);
-          for (int q = i; q <= l; ++q) s0 = fma(am[i + K * q] * ri, r1s[q + K * l], s0);
-        }
-      }
-      a.Rout[e] = s0;
+      for (int q = i; q <= l; ++q) s0 = fma(xs[i + kS1Ld * q], r1s[q + kS1Ld * l], s0);
+      a.Rout[i + K * l] = s0;
     }
 }
 

@@ -228,7 +228,7 @@ static __device__ double warp_lambda_min_bound(double *G, int r) {
       ok = false;
       break;
     }
-    const double inv = 1.0 / dj;  // one division sequence per pivot (lane-uniform)
+    const double inv = rcp_f64(dj);  // Newton-refined reciprocal (no FP64 division sequence)
     double gij = 0.0;
     if (lane > j && lane < r) {
       gij = G[lane + r * j];

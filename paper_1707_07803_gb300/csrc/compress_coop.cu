@@ -39,7 +39,7 @@ struct CompressArgs {
   int64_t cap_buf;
   int64_t qr_cap;        // shared-memory bytes available to the QR (per CTA)
   int64_t *R_out;        // ranks on exit (d + 1)
-  unsigned *bar;         // [0] arrivals, [1] generation
+  unsigned *bar;         // [0] grid-barrier arrivals of the launch (zeroed before it)
   int *ctl;              // [0] first bond left to the host (0: none), [2] rounding done here
   int *status;
   // fused rounding (Section 5.4) after a complete compression, on CTA 0
@@ -52,6 +52,7 @@ struct CompressArgs {
 
 __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   extern __shared__ double sm[];
+  unsigned epoch = 0;  // grid barriers passed by this CTA
   const int d = a.d;
   const double *cur = a.core[d - 1];  // M_k (t x w, ld t)
   int rk1 = 1;                        // compressed rank of bond k+1
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
       else
         qr_tpc_cta(q, sm);
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, epoch);
     // data written by other CTAs is read through L2 (__ldcg), never from a possibly stale L1 line;
     // the factoring cluster keeps its own rank, so its CTAs always agree on the next bond's shape
     // (and execute the same cluster barriers)
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
         if (x < nout && part == 0) out[x] = acc;
       }
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, epoch);
     cur = out;
     rk1 = r;
   }
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
   // every bond was compressed, so cores 1..d-1 are right-orthonormal: CTA 0 runs the rounding
   // sweeps (or their no-truncation certificate) on the compressed cores when they fit its
   // shared memory, leaving the final ranks in R_out
-  grid_barrier(a.bar, a.status);
+  grid_barrier(a.bar, a.status, epoch);
   if (blockIdx.x != 0) return;
   __shared__ int64_t s_R[TNR_MAX_SITES + 1], s_phys[TNR_MAX_SITES];
   __shared__ RoundSmallArgs s_args;

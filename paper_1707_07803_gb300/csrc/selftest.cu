@@ -12,7 +12,8 @@ __device__ unsigned g_selftest_bar[2];
 
 __global__ void k_wait_never_satisfied(unsigned *bar, int *status, long long spin_cap) {
   if (blockIdx.x == 1) return;  // this CTA never arrives
-  grid_barrier(bar, status, spin_cap);
+  unsigned epoch = 0;
+  grid_barrier(bar, status, epoch, spin_cap);
 }
 
 }  // namespace

@@ -208,6 +208,7 @@ __device__ void chol_series_step(const double *a, double *xs, double *ps, int K,
 }
 
 __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
+  unsigned epoch = 0;  // grid barriers passed by this CTA
   extern __shared__ double dyn[];         // own rows (leading dimension K + 1), then tile staging
   __shared__ double am[kS1MaxK * kS1Ld];   // the current Gram, then its factor
   __shared__ double r1s[kS1MaxK * kS1Ld];  // R1
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   }
   // ---- pass 1: G1 = Y^T Y by tiles, then every CTA factors it and solves its rows
   gram_tiles(m, K, CoreAt{a.core0, I1, K}, a.G, cols);
-  grid_barrier(a.bar, a.status);
+  grid_barrier(a.bar, a.status, epoch);
   for (int e = tid; e < K * K; e += nthr) am[(e % K) + kS1Ld * (e / K)] = __ldcg(a.G + e);
   __syncthreads();
   if (!cta_ldl(am, K, dinv, true)) {
@@ -255,10 +256,10 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     const int rr = x % nr, c = x / nr;
     a.Q1[(r0 + rr) + (int64_t)m * c] = ys[rr * ld + c];
   }
-  grid_barrier(a.bar, a.status);
+  grid_barrier(a.bar, a.status, epoch);
   // ---- pass 2: G2 = Q1^T Q1 by tiles, checked and factored by every CTA
   gram_tiles(m, K, ColAt{a.Q1, m}, a.G, cols);
-  grid_barrier(a.bar, a.status);
+  grid_barrier(a.bar, a.status, epoch);
   if (tid == 0) s_emax = 0ull;
   double dev = 0.0;
   for (int e = tid; e < K * K; e += nthr) {

@@ -160,6 +160,34 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     a.R_out[1] = rk1;
   }
   if (!a.fuse_round) return;
+  // the certificate's first Gram G_1 = C_0^T C_0 (C_0: phys_0 x r_1, ld phys_0) spread over the
+  // grid: CTA b sums a block of rows into partial b, in the ping-pong buffer not holding C_0
+  const int p0 = a.phys[0];
+  const int64_t g1_rows = (p0 + (int64_t)gridDim.x - 1) / gridDim.x;  // rows per CTA
+  const bool g1_split = rk1 <= 16 && (int64_t)gridDim.x * rk1 * rk1 <= a.cap_buf &&
+                        g1_rows * rk1 * (int64_t)sizeof(double) <= a.round_cap;
+  double *g1p = a.buf[(cur == a.buf[0]) ? 1 : 0];
+  if (g1_split) {
+    const int rpb = (int)g1_rows, row0 = (int)blockIdx.x * rpb;
+    const int nrow = max(0, min(rpb, p0 - row0));
+    double *cs = sm;  // the block's rows, staged (nrow x rk1, ld nrow)
+    for (int x = threadIdx.x; x < nrow * rk1; x += blockDim.x) {
+      const int rr = x % nrow, c = x / nrow;
+      cs[x] = __ldcg(cur + row0 + rr + (int64_t)p0 * c);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rk1 * rk1; e += blockDim.x) {
+      const int i = e % rk1, j = e / rk1;
+      double s0 = 0.0, s1 = 0.0;
+      int rr = 0;
+      for (; rr + 1 < nrow; rr += 2) {
+        s0 = fma(cs[rr + nrow * i], cs[rr + nrow * j], s0);
+        s1 = fma(cs[rr + 1 + nrow * i], cs[rr + 1 + nrow * j], s1);
+      }
+      if (rr < nrow) s0 = fma(cs[rr + nrow * i], cs[rr + nrow * j], s0);
+      g1p[(int64_t)blockIdx.x * rk1 * rk1 + e] = s0 + s1;
+    }
+  }
   // every bond was compressed, so cores 1..d-1 are right-orthonormal: CTA 0 runs the rounding
   // sweeps (or their no-truncation certificate) on the compressed cores when they fit its
   // shared memory, leaving the final ranks in R_out
@@ -174,7 +202,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     RoundSmallLayout lay;
     const size_t need = round_small_layout(s_R, s_phys, d, &lay);
     s_fit = need > 0 && (int64_t)need <= a.round_cap;
-    if (s_fit) round_small_args(s_args, lay, d, a.core, s_R, s_phys, true, a.tol, a.max_rank, a.R_round, a.status);
+    if (s_fit) {
+      round_small_args(s_args, lay, d, a.core, s_R, s_phys, true, a.tol, a.max_rank, a.R_round, a.status);
+      if (g1_split) {
+        s_args.g1_part = g1p;
+        s_args.g1_parts = (int)gridDim.x;
+      }
+    }
     a.ctl[2] = s_fit;
   }
   __syncthreads();

@@ -15,6 +15,10 @@ struct RoundSmallArgs {
   int off[TNR_MAX_SITES];    // shared-memory offset of core k (doubles)
   int tmp_off, tmp_cap, rbuf_off, work_off, gram_off;
   int certify;  // cores 1..d-1 are right-orthonormal on entry: try the no-truncation certificate
+  // G_1 = C_0^T C_0 as g1_parts partial Grams (R[1] x R[1] each, global memory, R[1] <= 16) to be
+  // added in order, when the caller spread it over a grid; null: the CTA forms G_1 itself
+  const double *g1_part;
+  int g1_parts;
   double tol;
   int64_t max_rank;
   int64_t *R_out;  // device, d + 1 ranks on exit
@@ -48,11 +52,61 @@ static __device__ int bonds_certified(const RoundSmallArgs &a, const double *sm,
   __syncthreads();
   if (!s_ok) return 0;
   // Gram chain
-  cta_tn_sym(gram + goff[1], sm + a.off[0], sm + a.off[0], Rs[0] * a.phys[0], Rs[1]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (a.g1_part && Rs[1] <= 16) {
+    // G_1 from the grid's partials: thread (entry e, stripe s) adds partials s, s + S, ... (all its
+    // loads in flight), then the S stripe sums of each entry are added in order
+    __shared__ double red[kStepThreads];
+    const int r1 = Rs[1], E2 = r1 * r1, S = kStepThreads / E2, e = threadIdx.x % E2, st = threadIdx.x / E2;
+    double v = 0.0;
+    if (st < S)
+#pragma unroll 4
+      for (int b = st; b < a.g1_parts; b += S) v += __ldcg(a.g1_part + (int64_t)b * E2 + e);
+    red[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < E2) {
+      double s0 = 0.0;
+      for (int q = 0; q < S; ++q) s0 += red[threadIdx.x + q * E2];
+      gram[goff[1] + threadIdx.x] = s0;
+    }
+    __syncthreads();
+  } else {
+    cta_tn_sym(gram + goff[1], sm + a.off[0], sm + a.off[0], Rs[0] * a.phys[0], Rs[1]);
+  }
   for (int k = 1; k + 1 < d; ++k) {
-    const int r = Rs[k], w = a.phys[k] * Rs[k + 1];
-    cta_gemm(tmp, gram + goff[k], r, sm + a.off[k], r, r, w, r);  // T = G_k C_k (r x phys r')
-    cta_tn_sym(gram + goff[k + 1], sm + a.off[k], tmp, r * a.phys[k], Rs[k + 1]);
+    const int r = Rs[k], ph = a.phys[k], r2 = Rs[k + 1], w = ph * r2;
+    const double *C = sm + a.off[k], *G = gram + goff[k];
+    if (r <= 8) {
+      // small bond: G_{k+1}(b, b') = sum_{a, x} C(a, x, b) (sum_{a'} G_k(a, a') C(a', x, b')) in one
+      // pass per entry (lanes over (a, x)), instead of the product and a second pass
+      double *Gn = gram + goff[k + 1];
+      const int E = r2 * (r2 + 1) / 2, m = r * ph;
+      for (int ee = warp; ee < E; ee += kStepWarps) {
+        int j = 0, base = 0;
+        while (base + j + 1 <= ee) {
+          base += j + 1;
+          ++j;
+        }
+        const int i = ee - base;  // (i, j) = (b, b'), i <= j
+        double sacc = 0.0;
+        for (int ax = lane; ax < m; ax += 32) {
+          const int aa = ax % r, x = ax / r;
+          const double *cj = C + r * (x + ph * j);
+          double t = 0.0;
+          for (int a2 = 0; a2 < r; ++a2) t = fma(G[aa + r * a2], cj[a2], t);
+          sacc = fma(C[aa + r * (x + ph * i)], t, sacc);
+        }
+        const double v = dwarp_sum(sacc);
+        if (lane == 0) {
+          Gn[i + r2 * j] = v;
+          Gn[j + r2 * i] = v;
+        }
+      }
+      __syncthreads();
+    } else {
+      cta_gemm(tmp, G, r, C, r, r, w, r);  // T = G_k C_k (r x phys r')
+      cta_tn_sym(gram + goff[k + 1], C, tmp, r * ph, r2);
+    }
   }
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -62,7 +116,6 @@ static __device__ int bonds_certified(const RoundSmallArgs &a, const double *sm,
   __syncthreads();
   const double delta2 = sc[0];
   // one warp per bond
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 1 + warp; k < d; k += kStepWarps) {
     const double lb = warp_lambda_min_bound(gram + goff[k], Rs[k]);
     if (lane == 0 && !(lb > delta2 * (1.0 + 1e-6))) atomicExch(&s_ok, 0);
@@ -192,6 +245,8 @@ static __host__ __device__ void round_small_args(RoundSmallArgs &a, const RoundS
   a.work_off = lay.work_off;
   a.gram_off = lay.gram_off;
   a.certify = certify ? 1 : 0;
+  a.g1_part = nullptr;
+  a.g1_parts = 0;
   a.tol = tol;
   a.max_rank = max_rank;
   a.R_out = R_out;

@@ -132,7 +132,10 @@ static __device__ __noinline__ void round_small_body(const RoundSmallArgs &a, do
   __shared__ double sc[8];
   const int d = a.d;
   for (int k = threadIdx.x; k <= d; k += kStepThreads) Rs[k] = a.R[k];
-  for (int k = 0; k < d; ++k) {
+  // the certificate with G_1 from the grid's partials never reads core 0: it is loaded only when
+  // the sweeps have to run
+  const bool lazy0 = a.certify && a.g1_part && a.R[1] <= 16;
+  for (int k = lazy0 ? 1 : 0; k < d; ++k) {
     const int n = a.R[k] * a.phys[k] * a.R[k + 1];
     const double *src = a.core[k];
     double *dst = sm + a.off[k];
@@ -144,6 +147,11 @@ static __device__ __noinline__ void round_small_body(const RoundSmallArgs &a, do
   if (a.certify && bonds_certified(a, sm, Rs, tmp, sm + a.gram_off, sc)) {
     for (int k = threadIdx.x; k <= d; k += kStepThreads) a.R_out[k] = Rs[k];  // cores unchanged
     return;
+  }
+  if (lazy0) {
+    const int n = a.R[0] * a.phys[0] * a.R[1];
+    for (int i = threadIdx.x; i < n; i += kStepThreads) sm[a.off[0] + i] = __ldcg(a.core[0] + i);
+    __syncthreads();
   }
   // left-to-right QR sweep: core k = Q R, R absorbed into core k+1
   for (int k = 0; k + 1 < d; ++k) {

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   __shared__ double r1s[kS1MaxK * kS1Ld];  // R1
   __shared__ double xs[kS1MaxK * kS1Ld];   // R2 (series: X, then I + X)
   __shared__ double ps[kS1MaxK * kS1Ld];   // series work
-  __shared__ double dinv[kS1MaxK], rd1[kS1MaxK], rd2[kS1MaxK];
+  __shared__ double dinv[kS1MaxK], rd1[kS1MaxK], rd2[kS1MaxK], rdq[kS1MaxK];
   __shared__ unsigned long long s_emax;
   if (a.gate && __ldcg(a.gate) == 0) return;  // uniform: written by an earlier launch
   const int K = a.K, I1 = a.I1, tid = threadIdx.x, nthr = blockDim.x;
@@ -244,13 +244,18 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
     return;  // uniform: every CTA factored the same matrix
   }
-  if (tid < K) rd1[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+  // the solve scales row j of D U by rd1_j^2 = 1 / d_j to rounding (not by the preconditioning
+  // reciprocal dinv_j), so Y = Q1 R1 holds to rounding for the R1 = D^{1/2} U kept for R = R2 R1
+  if (tid < K) {
+    rd1[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+    rdq[tid] = rd1[tid] * rd1[tid];
+  }
   __syncthreads();
   for (int e = tid; e < K * K; e += nthr) {  // R1(i, l) = d_i u_il / sqrt(d_i)
     const int i = e % K, l = e / K;
     r1s[i + kS1Ld * l] = i <= l ? am[i + kS1Ld * l] * rd1[i] : 0.0;
   }
-  rows_solve(ys, nr, K, am, dinv, rd1);
+  rows_solve(ys, nr, K, am, rdq, rd1);
   __syncthreads();
   for (int x = tid; x < nr * K; x += nthr) {  // Q1 rows for the second Gram
     const int rr = x % nr, c = x / nr;
@@ -298,13 +303,16 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
       if (blockIdx.x == 0 && tid == 0) *a.flag = 1;
       return;
     }
-    if (tid < K) rd2[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+    if (tid < K) {
+      rd2[tid] = rsqrt_f64(am[tid + kS1Ld * tid]);
+      rdq[tid] = rd2[tid] * rd2[tid];
+    }
     __syncthreads();
     for (int e = tid; e < K * K; e += nthr) {  // R2 explicitly, for R = R2 R1
       const int i = e % K, l = e / K;
       xs[i + kS1Ld * l] = i <= l ? am[i + kS1Ld * l] * rd2[i] : 0.0;
     }
-    rows_solve(ys, nr, K, am, dinv, rd2);
+    rows_solve(ys, nr, K, am, rdq, rd2);
   }
   __syncthreads();
   // Q~: column-major, or back into the core's layout (each CTA writes only the rows it read)

@@ -134,7 +134,11 @@ def test_solve_c2_prescribed_fp64():
     """2^20 x 2^20 MPO with sigma_j = 0.7^j (rank 32), k=16, p=16, q=2: exact recovery."""
     c = W.c2_prescribed()
     S, So, err = _check_solve(c["A"], c["k"], c["p"], c["q"], c["seed"], c["tol"], c["max_rank"])
-    assert sv_rel_err(S, c["sigma"][:16]) <= 1e-10
+    # FP64 throughout: the prescribed values come back to a few units of rounding (every reduction
+    # runs in a fixed order, so this is reproducible); a factor that is off by more than rounding
+    # anywhere in the chain (e.g. a QR whose R does not match the Q it was solved with to rounding)
+    # shows up here long before the 1e-10 gates
+    assert sv_rel_err(S, c["sigma"][:16]) <= 3e-15
 
 
 def test_rank_deficient_site1_falls_back_to_householder():

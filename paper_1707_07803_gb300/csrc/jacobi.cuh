@@ -1,7 +1,7 @@
 // One-sided (Hestenes) Jacobi iterations shared by the one-CTA SVD kernels.
 //
-// G (n x n, ld n) is rotated from the right until its columns are mutually orthogonal, and the
-// rotations are accumulated into V (ld n): G_in V = G_out, G_out = U S. Column pairs follow a
+// G (n x n, leading dimension ld) is rotated from the right until its columns are mutually
+// orthogonal, and the rotations are accumulated into V (same layout): G_in V = G_out, G_out = U S. Column pairs follow a
 // round-robin tournament, so the (n+1)/2 pairs of a round are disjoint. Each pair is handled by
 // a group of g lanes (lanes = rows): GB300 issues FP64 at 1/64 of the FP32 rate, so one FP64
 // warp instruction costs ~70 cycles of a sub-partition's FP64 pipe however many lanes are
@@ -156,11 +156,6 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, int ld, T 
   return sweep + 1;
 }
 
-// Plain FP64 sweeps (G_in V = G_out with V accumulated from its value on entry).
-static __device__ __forceinline__ int jacobi_sweeps(double *G, double *V, int n, double *nrm) {
-  return jacobi_sweeps_t<double>(G, V, n, n, nrm, 60);
-}
-
 // Doubles of work area jacobi_sweeps_mixed needs for an n x n matrix.
 __host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 3 * n * (n + 1); }
 
@@ -172,7 +167,7 @@ __host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 3 * n *
 // of G V0 are orthogonal to FP32 accuracy, so the FP64 phase converges in two or three sweeps
 // (the last one only confirms) instead of six to eight: most of the O(n^3) work per sweep moves to
 // the FP32 pipe, 64 times wider than FP64 on GB300. Results: G V = U S with V orthogonal to FP64
-// rounding, exactly as jacobi_sweeps. V on entry is ignored (the identity is assumed).
+// rounding, as plain FP64 sweeps give. V on entry is ignored (the identity is assumed).
 // work: jacobi_mixed_work(n) doubles. Returns the number of FP64 sweeps.
 static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work) {
   const int nthr = blockDim.x;

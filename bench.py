@@ -17,6 +17,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -77,7 +78,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+        # the raw samples (their summary goes into the JSON line): TNR_BENCH_OUT, else the temp dir
+        out = os.environ.get("TNR_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_bench_{gpu_index}.csv")
 
     def start(self):
         try:

@@ -21,6 +21,10 @@ Modules
             and plain MPO rounding.
   tnrsvd    the randomized MPO subspace iteration (Alg. 5.4) driving Alg. 5.1, and a dense
             rSVD cross-check.
+  sparse    the products of Section 5.2 applied straight from the Alg. 4.1 block form (the MPO
+            has rank R at every bond, Lemma 4.2), and TNrSVD driven by them.
+  gradient  the sum of the top singular values as a function of the cores, its central
+            differences, and its closed-form gradient when A is exactly of rank K.
 
 Parity status: every function is pinned by tests under ``tests/test_oracle_*.py`` except the
 accuracy of TNrSVD against the true SVD for generic inputs, which the paper does not bound

@@ -51,8 +51,6 @@ def workload_config(precision="mixed"):
         "workload": "prescribed-sigma MPO 2^20 x 2^20 (merged sites 64,4^7; A ranks 25), k=16 p=16 q=2, seed 2",
         "precision": ("products BF16 x3 on tcgen05 / FP32 accumulate, sweeps + SVD + B in FP64"
                       if precision == "mixed" else "all FP64"),
-        "global_batch": 1,
-        "seq_len": 0,
         "tol": c["tol"],
         "max_rank": c["max_rank"],
         "l2": "flushed between timed steps (256 MiB write)",
@@ -187,7 +185,7 @@ def batched_config(n, d=None, ranks=None, ks=None):
                        f"ranks uniform {ranks[0]}-{ranks[1]}, k in {set(ks)}, p=k, q=1, "
                        "max_rank=K, seed 0",
            "precision": "products BF16 x3 on tcgen05 / FP32 accumulate, sweeps + SVD + B in FP64",
-           "global_batch": n, "seq_len": 0, "l2": "flushed between timed steps (256 MiB write)",
+           "problems": n, "l2": "flushed between timed steps (256 MiB write)",
            "parallelism": "batch over host worker threads, one CUDA stream each"}
     return probs, cfg
 
@@ -394,7 +392,7 @@ def sparse_main(args):
         "data": "synthetic",
         "config": {"workload": f"banded 2^20 x 2^20, 8 nnz/row in [i-64, i+64], N(0,1), {R} blocks of 4x4; "
                                f"conversion (Alg. 4.1) + TNrSVD k={k} p={p} q={q} via the block form",
-                   "global_batch": 1, "seq_len": 0, "l2": "flushed between timed steps (256 MiB write)"},
+                   "l2": "flushed between timed steps (256 MiB write)"},
         "clocks": clocks,
         "roofline": gram if g_ms >= sp_ms else spmm,
         "spmm": spmm,
@@ -467,7 +465,7 @@ def adjoint_main(args):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"Gaussian MPO d={d}, I=J=4, rank {rank}, FP32-valued cores, k={k} p={p} q={q}, "
-                               f"loss = sum of the top {n_sv} singular values", "global_batch": 1, "seq_len": 0,
+                               f"loss = sum of the top {n_sv} singular values",
                    "l2": "working set above L2 (products of 512-wide bonds)"},
         "clocks": clocks,
         "gradient_check": {"entries": args.fd_entries, "h": h,

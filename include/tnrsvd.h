@@ -112,26 +112,29 @@ int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *ro
                     double *X, uint8_t *digits, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------------
- * Sparse -> MPO conversion that allocates nothing (the paper has no counterpart; this is a
- * service to callers of this library). It computes exactly what tnr_sparse_count followed
- * by tnr_sparse_fill computes, for callers that cannot call cudaMalloc or take memory from an
- * allocator at all: code running while a CUDA graph is being captured (allocation is not a
- * capturable operation), code embedded in a host process whose memory manager owns every
- * byte of device memory, or latency-critical paths that must not pay the device-wide
- * synchronisation an allocation can cause. Instead of a caller workspace it uses a scratch
- * array compiled into the library, sized for at most TNR_NOALLOC_MAX_NNZ nonzeros (32 MiB +
- * 32 KiB, held on every GPU that loads the library until the process exits).
+ * Sparse -> MPO conversion that allocates nothing. The paper has no counterpart: this entry is
+ * a service to callers of this library. It computes exactly what tnr_sparse_count followed by
+ * tnr_sparse_fill computes, for callers that cannot call cudaMalloc or take memory from an
+ * allocator: for example a plug-in loaded into a host process whose own memory manager has
+ * reserved all of the device memory up front (a second allocator would fail or fragment it),
+ * or code that must not pay the device-wide synchronisation an allocation can cause. Instead
+ * of a caller workspace it uses a scratch array compiled into the library, sized for at most
+ * TNR_NOALLOC_MAX_NNZ nonzeros (32 MiB + 32 KiB, held on every GPU that loads the library
+ * until the process exits). Neither device memory nor host memory is allocated by the call
+ * (R is copied straight into the caller's int64, without a pinned staging buffer).
  *
  * Inputs as for tnr_sparse_count/fill. The caller passes the outputs: X with room for
- * max_blocks*I_1*J_1 doubles and digits with room for max_blocks*2(d-1) bytes (max_blocks =
- * nnz always suffices, Lemma 4.2 counts one block per nonzero at most). *R_out receives the
- * number of blocks R. Errors: TNR_ERANGE when nnz > TNR_NOALLOC_MAX_NNZ (nothing enqueued);
+ * max_blocks*I_1*J_1 doubles and digits with room for max_blocks*2(d-1) bytes; each nonzero
+ * opens at most one block, so max_blocks = nnz always suffices. *R_out receives the number of
+ * blocks R. Errors: TNR_ERANGE when nnz > TNR_NOALLOC_MAX_NNZ (nothing enqueued);
  * TNR_ENOMEM when R > max_blocks (X and digits untouched); otherwise as tnr_sparse_count.
- * Synchronises the stream once (to read R); the fill is then enqueued asynchronously.
+ * The call synchronises the stream once, to read R; the fill is then enqueued asynchronously.
  * The first call on a device looks the scratch address up (cudaGetSymbolAddress with that
- * device current); make that first call before any stream capture on that device. Every call
- * shares the scratch: calls whose work overlaps on the GPU (other streams, other threads)
- * race and must be serialised by the caller.
+ * device current). Every call shares the scratch, which keeps the previous call's contents
+ * (each call writes every entry it reads); calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. With the library's
+ * instrumentation switched on (tnr_stats_enable; off by default) the call records timing
+ * events like every other entry point.
  * ------------------------------------------------------------------------------------- */
 #define TNR_NOALLOC_MAX_NNZ 8388608
 int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *row, const int64_t *col,

@@ -442,12 +442,12 @@ constexpr int64_t kNoAllocTiles = (TNR_NOALLOC_MAX_NNZ + kTile - 1) / kTile;
 static __device__ __align__(256) int32_t g_noalloc_scratch[TNR_NOALLOC_MAX_NNZ + kNoAllocTiles + 64];
 
 std::mutex g_noalloc_mu;
-int32_t *g_noalloc_ptr[TNR_MAX_SITES] = {nullptr};  // per device ordinal (first 64 devices)
+int32_t *g_noalloc_ptr[kMaxDevices] = {nullptr};  // per device ordinal
 
 int noalloc_scratch(int32_t **out) {
   int dev = 0;
   TNR_CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= TNR_MAX_SITES) return TNR_ERANGE;
+  if (dev < 0 || dev >= kMaxDevices) return TNR_ERANGE;
   std::lock_guard<std::mutex> g(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void *p = nullptr;
@@ -493,7 +493,7 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   TNR_CK(cudaGetLastError());
   int32_t total = 0;
   const ReadBack rb[1] = {{&total, tile_off + ntiles, sizeof(int32_t)}};
-  int st = read_back(s, rb, 1);  // synchronises once
+  int st = read_back_unstaged(s, rb, 1);  // synchronises once; no pinned staging buffer
   if (st != TNR_OK) return st;
   *R_out = total;
   if (total > max_blocks) return TNR_ENOMEM;  // X and digits untouched

@@ -19,10 +19,10 @@ static thread_local int t_status_slot = 0;
 void set_status_slot(int slot) { t_status_slot = (slot >= 0 && slot < kStatusSlots) ? slot : 0; }
 
 int *status_ptr() {
-  static int *cache[64] = {nullptr};
+  static int *cache[kMaxDevices] = {nullptr};
   static std::mutex mu;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   int *base = nullptr;
   {
     std::lock_guard<std::mutex> g(mu);
@@ -93,21 +93,25 @@ struct PinnedStage {
 thread_local PinnedStage t_stage;
 }  // namespace
 
+int read_back_unstaged(cudaStream_t s, const ReadBack *items, int n) {
+  int *st = status_ptr();
+  if (!st) return TNR_ECUDA;
+  for (int i = 0; i < n; ++i)
+    TNR_CK(cudaMemcpyAsync(items[i].dst, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));
+  int h = 0;
+  TNR_CK(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TNR_CK(cudaStreamSynchronize(s));
+  if (h != 0) TNR_CK(cudaMemsetAsync(st, 0, sizeof(int), s));
+  return h;
+}
+
 int read_back(cudaStream_t s, const ReadBack *items, int n) {
   int *st = status_ptr();
   if (!st) return TNR_ECUDA;
   size_t total = sizeof(int);
   for (int i = 0; i < n; ++i) total += (items[i].bytes + 15) & ~size_t(15);
   char *stage = static_cast<char *>(t_stage.get(total));
-  if (!stage) {  // no pinned memory: the plain path, one synchronising copy each
-    for (int i = 0; i < n; ++i)
-      TNR_CK(cudaMemcpyAsync(items[i].dst, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));
-    int h = 0;
-    TNR_CK(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TNR_CK(cudaStreamSynchronize(s));
-    if (h != 0) TNR_CK(cudaMemsetAsync(st, 0, sizeof(int), s));
-    return h;
-  }
+  if (!stage) return read_back_unstaged(s, items, n);  // no pinned memory: plain copies
   size_t off = sizeof(int);
   for (int i = 0; i < n; ++i) {
     TNR_CK(cudaMemcpyAsync(stage + off, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));

@@ -14,6 +14,9 @@ namespace tnr {
 // Kernels receive its address; status_ptr() returns it for the current device and the calling
 // host thread's slot (set_status_slot; 0 unless the thread is a batched-solve worker).
 constexpr int kStatusSlots = 64;
+// Per-device caches of device-symbol addresses (status words, compiled-in scratch) cover the
+// first kMaxDevices device ordinals; a call on a higher ordinal fails with TNR_ERANGE/ECUDA.
+constexpr int kMaxDevices = 64;
 int *status_ptr();
 void set_status_slot(int slot);
 
@@ -93,6 +96,9 @@ struct ReadBack {
   size_t bytes;
 };
 int read_back(cudaStream_t s, const ReadBack *items, int n);
+// The same read-back without any staging buffer: plain copies into the caller's (pageable) host
+// memory and one synchronisation of s. Allocates nothing, on the host or on the device.
+int read_back_unstaged(cudaStream_t s, const ReadBack *items, int n);
 int reset_status(cudaStream_t s);
 
 #define TNR_CK(expr)                                           \

@@ -268,17 +268,41 @@ def sparse_to_mpo(nrows, ncols, row, col, val, I, J, stream=None):
 NOALLOC_MAX_NNZ = 8388608
 
 
-def tnr_sparse_to_mpo_noalloc(nrows, ncols, row, col, val, I, J, X, digits, max_blocks, stream=None):
-    """Alg. 4.1 without any device allocation by the library (scratch compiled into it).
+def _need_buffer(t, dtype, min_elems, what, need_cuda=True):
+    """A contiguous CUDA tensor of `dtype` holding at least `min_elems` elements."""
+    if not isinstance(t, torch.Tensor) or (need_cuda and not t.is_cuda):
+        raise ValueError(f"{what}: a CUDA tensor is required")
+    if t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {dtype} is required, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: a contiguous tensor is required")
+    if t.numel() < min_elems:
+        raise ValueError(f"{what}: room for {min_elems} elements is required, got {t.numel()}")
 
-    The caller passes the outputs X (max_blocks*I1*J1 doubles) and digits (max_blocks*2(d-1)
-    bytes); returns R. Limits and races: see include/tnrsvd.h.
+
+def tnr_sparse_to_mpo_noalloc(nrows, ncols, row, col, val, I, J, X, digits, max_blocks, stream=None):
+    """Alg. 4.1 without any allocation by the library (its scratch is compiled into it).
+
+    For callers that cannot allocate device memory themselves at call time (a process whose own
+    memory manager holds all device memory): the caller passes the outputs X (room for
+    max_blocks*I1*J1 float64) and digits (room for max_blocks*2(d-1) uint8); returns R. The
+    tensors are checked here (device, dtype, contiguity, size) before the library is called.
+    Limits and races: see include/tnrsvd.h.
     """
     lib = load()
-    _need_cuda(row, col, val, X)
+    max_blocks = int(max_blocks)
+    if max_blocks < 0:
+        raise ValueError("max_blocks must be >= 0")
+    nnz = row.numel()
+    _need_buffer(row, torch.int64, nnz, "row")
+    _need_buffer(col, torch.int64, nnz, "col")
+    _need_buffer(val, torch.float64, nnz, "val")
+    _need_buffer(X, torch.float64, max_blocks * int(I[0]) * int(J[0]), "X")
+    if len(I) > 1 or digits is not None:
+        _need_buffer(digits, torch.uint8, max_blocks * 2 * (len(I) - 1), "digits")
     R = ctypes.c_int64(0)
-    _check(lib.tnr_sparse_to_mpo_noalloc(nrows, ncols, row.numel(), _ptr(row), _ptr(col), _ptr(val), len(I),
-                                         _i64arr(I), _i64arr(J), _ptr(X), _ptr(digits), int(max_blocks),
+    _check(lib.tnr_sparse_to_mpo_noalloc(nrows, ncols, nnz, _ptr(row), _ptr(col), _ptr(val), len(I),
+                                         _i64arr(I), _i64arr(J), _ptr(X), _ptr(digits), max_blocks,
                                          ctypes.byref(R), _stream(stream)), "tnr_sparse_to_mpo_noalloc")
     return R.value
 

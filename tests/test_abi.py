@@ -117,3 +117,30 @@ def test_persistent_batch_planning_on_the_host(lib):
     assert not h.value
     assert lib.tnr_batch_launch(None, None) == -1 and lib.tnr_batch_collect(None, None) == -1
     assert lib.tnr_batch_destroy(None) == 0
+
+
+def test_noalloc_binding_checks_buffers_before_the_call():
+    """The allocation-free conversion's binding rejects outputs that are too small, of the wrong
+    dtype or not contiguous, and host tensors, before the library is called (no GPU needed)."""
+    import torch
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    chk = T._need_buffer
+    ok = torch.zeros(32, dtype=torch.float64)
+    chk(ok, torch.float64, 32, "X", need_cuda=False)
+    with pytest.raises(ValueError, match="room for 33"):
+        chk(ok, torch.float64, 33, "X", need_cuda=False)
+    with pytest.raises(ValueError, match="dtype"):
+        chk(ok.float(), torch.float64, 8, "X", need_cuda=False)
+    with pytest.raises(ValueError, match="contiguous"):
+        chk(torch.zeros(8, 8, dtype=torch.float64).t(), torch.float64, 8, "X", need_cuda=False)
+    with pytest.raises(ValueError, match="CUDA"):
+        chk(None, torch.uint8, 0, "digits", need_cuda=False)
+    rows = torch.arange(8, dtype=torch.int64)
+    vals = torch.ones(8, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):  # host tensors never reach the library
+        T.tnr_sparse_to_mpo_noalloc(8, 8, rows, rows, vals, [2, 4], [2, 4], torch.zeros(32, dtype=torch.float64),
+                                    torch.zeros(16, dtype=torch.uint8), max_blocks=8)
+    with pytest.raises(ValueError, match="max_blocks"):
+        T.tnr_sparse_to_mpo_noalloc(8, 8, rows, rows, vals, [2, 4], [2, 4], None, None, max_blocks=-1)

@@ -1,19 +1,21 @@
 """The allocation-free conversion entry point gives the same blocks as the regular one.
 
-tnr_sparse_to_mpo_noalloc serves callers that cannot allocate device memory (for example code
-running during CUDA graph capture, or inside a process whose own allocator owns all device
-memory): its scratch is compiled into the library instead of coming from a caller workspace.
-This test calls it through the C ABI twice in a row, on two different matrices, so the second
-call starts from the first call's leftover scratch contents, and checks each result bit for bit
-against tnr_sparse_count + tnr_sparse_fill on the same input. It is collected last so that a
-`pytest -x` run has already run every other test if this one fails; it also passes on its own
-in a fresh process.
+tnr_sparse_to_mpo_noalloc serves callers that cannot allocate memory at call time (for example a
+plug-in inside a process whose own memory manager has reserved all of the device memory): its
+scratch is compiled into the library instead of coming from a caller workspace. This test calls
+it through the C ABI twice in a row, on two different matrices, so the second call starts from
+the first call's leftover scratch contents, and checks each result bit for bit against
+tnr_sparse_count + tnr_sparse_fill on the same input and, on the smaller matrix with uneven
+factors, against the CPU oracle of Alg. 4.1 as well. It is collected last so that a `pytest -x`
+run has already run every other test if this one fails; it also passes on its own in a fresh
+process.
 """
 
 import numpy as np
 import pytest
 import torch
 
+import oracle.convert
 from paper_1707_07803_gb300 import tnrsvd as T
 from workloads import banded_coo
 
@@ -52,6 +54,11 @@ def test_noalloc_matches_regular_entry_point_twice():
         bs = I[0] * J[0]
         assert X[: R * bs].cpu().numpy().tobytes() == X_ref.cpu().numpy().tobytes()
         assert digits[: R * 2 * (len(I) - 1)].cpu().numpy().tobytes() == D_ref.cpu().numpy().tobytes()
+        if rows.size < 100000:  # the oracle of Alg. 4.1, bit for bit
+            Ro, Xo, Do = oracle.convert.convert(rows, cols, vals, nrows, ncols, I, J)
+            assert R == Ro
+            assert X[: R * bs].cpu().numpy().tobytes() == Xo.tobytes()
+            assert digits[: R * 2 * (len(I) - 1)].cpu().numpy().tobytes() == Do.tobytes()
 
 
 def test_noalloc_limits():
@@ -71,3 +78,5 @@ def test_noalloc_limits():
     rc = lib.tnr_sparse_to_mpo_noalloc(1 << 24, 1 << 24, big, T._ptr(r), T._ptr(c), T._ptr(v), 4, dims, dims,
                                        T._ptr(X), T._ptr(digits), big, ctypes.byref(Rv), T._stream())
     assert rc == -8  # rejected on the host before any device work
+    with pytest.raises(ValueError, match="room for"):  # the binding checks the outputs' room
+        T.tnr_sparse_to_mpo_noalloc(8, 8, r, c, v, [2, 4], [2, 4], X, digits, max_blocks=9)

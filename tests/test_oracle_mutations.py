@@ -120,3 +120,51 @@ def test_no_power_iteration_transpose(monkeypatch):
     orig = oracle.mpo.contract
     monkeypatch.setattr(oracle.mpo, "contract", lambda A, X, trans=False: orig(A, X, False))
     _fails(tt.test_dense_rsvd_cross_check, 1)
+
+
+def _patched_rl_truncate(delta_of):
+    """_rl_truncate with a planted mistake in its threshold: delta_of(cores, tol, d) -> delta."""
+
+    def bad(cores, tol, max_rank):
+        d = len(cores)
+        delta = delta_of(cores, tol, d)
+        for k in range(d - 1, 0, -1):
+            t, I, Kx, t2 = cores[k].shape
+            U, s, Vt = np.linalg.svd(cores[k].reshape(t, I * Kx * t2, order="F"), full_matrices=False)
+            r = oracle.rounding.keep_rank(s, delta, max_rank)
+            cores[k] = Vt[:r].reshape(r, I, Kx, t2, order="F")
+            cores[k - 1] = np.einsum("aijb,bc->aijc", cores[k - 1], U[:, :r] * s[:r])
+        return cores
+
+    return bad
+
+
+def _threshold_pins():
+    for tol in (0.02, 0.05, 0.1, 0.2):
+        tro.test_round_mpo_threshold_exact_ranks(tol)
+        tro.test_orthogonalize_threshold_exact_ranks(tol)
+
+
+def test_threshold_without_sqrt_d_minus_1(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "_rl_truncate",
+                        _patched_rl_truncate(lambda c, tol, d: tol * np.linalg.norm(c[-1])))
+    _fails(_threshold_pins)
+
+
+def test_threshold_from_squared_norm(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "_rl_truncate",
+                        _patched_rl_truncate(lambda c, tol, d: tol * np.linalg.norm(c[-1]) ** 2 / np.sqrt(d - 1)))
+    _fails(_threshold_pins)
+
+
+def test_threshold_from_the_wrong_core(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "_rl_truncate",
+                        _patched_rl_truncate(lambda c, tol, d: tol * np.linalg.norm(c[0]) / np.sqrt(d - 1)))
+    _fails(_threshold_pins)
+
+
+def test_threshold_pins_pass_with_the_correct_rule(monkeypatch):
+    """The patched sweep with the oracle's own rule passes the same pins (the harness is sound)."""
+    monkeypatch.setattr(oracle.rounding, "_rl_truncate",
+                        _patched_rl_truncate(lambda c, tol, d: tol * np.linalg.norm(c[-1]) / np.sqrt(d - 1)))
+    _threshold_pins()

@@ -89,3 +89,88 @@ def test_round_mpo_preserves_and_bounds():
     np.testing.assert_allclose(mpo.dense(B), mpo.dense(A), atol=1e-12)
     for r, b in zip(rounding.ranks(B)[1:-1], mpo.rank_bounds(I, J)):
         assert r <= b
+
+
+# ---- the truncation threshold delta = tol ||Y||_F / sqrt(d - 1) of the rounding (Section 3/5.4) ----
+#
+# MPOs with prescribed Schmidt spectra at every bond (workloads.prescribed_bond_mpo): the Schmidt
+# values at bond k are g s_k, and truncating bond k keeps the product structure, scaling the other
+# bonds' values by c_k = ||s_k[:r_k]||. The right-to-left sweep therefore sees, at bond k,
+# g s_k prod_{j>k} c_j, and keeps the smallest r >= 1 whose discarded values have squared sum
+# <= delta^2. The rounded tensor is the construction with each s_k cut to its first r_k values.
+from workloads import prescribed_bond_mpo  # noqa: E402
+
+# Spectra graded finely enough (ratio 0.6) that a threshold off by sqrt(d-1), by a factor g or
+# by squaring ||Y|| changes at least one kept rank.
+_SPECTRA = [0.6 ** np.arange(6), 0.55 ** np.arange(7), 0.6 ** np.arange(5) * np.array([1, 1, 1, 1, 0.3])]
+_N = [6, 42, 35, 5]
+_G = 3.7
+
+
+def _expected_ranks(spectra, g, tol):
+    d = len(spectra) + 1
+    delta = tol * g / np.sqrt(d - 1)
+    ranks = [None] * (d - 1)
+    scale = 1.0
+    for k in range(d - 2, -1, -1):  # right to left
+        sv = g * spectra[k] * scale
+        r = len(sv)
+        for cand in range(1, len(sv) + 1):
+            if np.sum(sv[cand:] ** 2) <= delta ** 2:
+                r = cand
+                break
+        ranks[k] = r
+        scale *= np.linalg.norm(spectra[k][:r])
+    return ranks
+
+
+def _truncated_dense(seed, spectra, g, ranks, split=None):
+    cut = [s[:r] for s, r in zip(spectra, ranks)]
+    n = list(_N)
+    cores, _ = prescribed_bond_mpo(seed, n, spectra, g, site1_split=split)
+    # zero the discarded coefficients in the same cores: the construction with s_k cut to r_k
+    out = [c.copy() for c in cores]
+    for k, s in enumerate(spectra):
+        w = np.zeros_like(s)
+        w[: ranks[k]] = 1.0
+        out[k] = out[k] * w[None, None, None, :]
+    del cut
+    return mpo.dense(out)
+
+
+@pytest.mark.parametrize("tol", [0.02, 0.05, 0.1, 0.2])
+def test_round_mpo_threshold_exact_ranks(tol):
+    cores, s = prescribed_bond_mpo(11, _N, _SPECTRA, _G)
+    np.testing.assert_allclose(mpo.norm(cores), _G, rtol=1e-13)
+    B = rounding.round_mpo(cores, tol=tol)
+    want = _expected_ranks(s, _G, tol)
+    assert rounding.ranks(B)[1:-1] == want
+    D, DB = mpo.dense(cores), mpo.dense(B)
+    np.testing.assert_allclose(DB, _truncated_dense(11, s, _G, want), atol=1e-13 * _G)
+    # TT-rounding guarantee of the cited SVD-based rounding: ||Y - round(Y)||_F <= tol ||Y||_F
+    assert np.linalg.norm(D - DB) <= tol * np.linalg.norm(D) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("tol", [0.02, 0.05, 0.1, 0.2])
+def test_orthogonalize_threshold_exact_ranks(tol):
+    """The same pin through MPO-QR: Y is a tall matrix with K = 3 columns on site 1 (6 = 2 x 3)."""
+    Y, s = prescribed_bond_mpo(12, _N, _SPECTRA, _G, site1_split=(2, 3))
+    Q, R = rounding.orthogonalize(Y, tol=tol)
+    want = _expected_ranks(s, _G, tol)
+    assert rounding.ranks(Q)[1:-1] == want
+    DY = mpo.dense(Y)
+    DT = _truncated_dense(12, s, _G, want, split=(2, 3))
+    np.testing.assert_allclose(mpo.dense(Q) @ R, DT, atol=1e-13 * _G)
+    assert np.linalg.norm(DY - mpo.dense(Q) @ R) <= tol * np.linalg.norm(DY) * (1 + 1e-12)
+
+
+def test_prescribed_bond_spectra_are_the_svd_of_the_unfoldings():
+    """The generator's claim, checked against LAPACK on the dense unfoldings (no oracle code)."""
+    cores, s = prescribed_bond_mpo(11, _N, _SPECTRA, _G)
+    D = mpo.dense(cores)  # rows = the multi-index over all sites (J = 1)
+    T = D[:, 0].reshape(_N, order="F")
+    for k in range(1, len(_N)):
+        left = int(np.prod(_N[:k]))
+        sv = np.linalg.svd(T.reshape(left, -1, order="F"), compute_uv=False)
+        np.testing.assert_allclose(sv[: len(s[k - 1])], _G * s[k - 1], rtol=1e-12, atol=1e-14)
+        assert np.all(sv[len(s[k - 1]):] < 1e-12)

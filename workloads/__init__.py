@@ -148,3 +148,43 @@ def batched_gaussian(seed, n, d_range=(8, 20), phys=(2, 4), rank_range=(4, 32), 
                              scale=lambda kk, shape: 1.0 / np.sqrt(shape[1] * shape[0]))
         out.append(dict(A=cores, k=k, p=k, q=q, seed=seed * 100003 + i, tol=tol, max_rank=2 * k))
     return out
+
+
+def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None):
+    """An MPO whose Schmidt spectrum at every bond is prescribed (cores grouped as one physical
+    index per site; interior bonds r_k = len(spectra[k-1])).
+
+    n[k] is the physical size of site k (n[0] >= r_1, n[k] >= r_{k-1} r_k, n[-1] >= r_{d-1}); each
+    spectra[k] is normalised to unit norm. Cores: site 1 is g * U_1[x, l_1] s_1[l_1]; site k is
+    W_k[x, (l_{k-1}, l_k)] s_k[l_k]; site d is W_d[x, l_{d-1}], with U_1 and every W_k having
+    orthonormal columns drawn by QR of Gaussian matrices (seeded). Because the coefficient tensor is
+    a product over bonds and the basis functions are orthonormal, the Schmidt values at bond k are
+    exactly g * s_k (and ||A||_F = g).
+
+    site1_split=(I1, K): return site 1 as (1, I1, K, r_1) (a tall matrix with K columns on site 1,
+    J_k = 1 elsewhere); otherwise every core is (r, n_k, 1, r'). Returns (cores, normalised spectra).
+    """
+    rng = np.random.default_rng(seed)
+    s = [np.asarray(x, dtype=np.float64) / np.linalg.norm(x) for x in spectra]
+    d = len(s) + 1
+    r = [1] + [len(x) for x in s] + [1]
+
+    def orth(rows, cols):
+        Q, _ = np.linalg.qr(rng.standard_normal((rows, cols)))
+        return Q
+
+    cores = []
+    for k in range(d):
+        rl, rr = r[k], r[k + 1]
+        W = orth(int(n[k]), rl * rr).reshape(int(n[k]), rl, rr, order="F")  # column (l, l') -> l + rl l'
+        c = W.transpose(1, 0, 2)  # (rl, n, rr)
+        if k < d - 1:
+            c = c * s[k][None, None, :]
+        if k == 0:
+            c = c * float(g)
+        cores.append(c[:, :, None, :].copy())
+    if site1_split is not None:
+        I1, K = site1_split
+        assert I1 * K == int(n[0])
+        cores[0] = cores[0][0, :, 0, :].reshape(I1, K, r[1], order="F")[None].copy()
+    return cores, s

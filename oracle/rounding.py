@@ -115,3 +115,54 @@ def round_mpo(A, tol=0.0, max_rank=0):
 
 def ranks(cores):
     return [cores[0].shape[0]] + [c.shape[3] for c in cores]
+
+
+# ---- truncate-as-you-go (zip-up) rounding of a product: the product is rounded while it is formed ----
+#
+# Reading (a variant of Section 5.4's "rounding sweep first, then the sweep of Alg. 5.2"): the
+# first sweep of the rounding is fused with the MPO x MPO product of Section 5.2, so the product
+# cores of rank R_k S_k are never formed in full. The sweep runs right to left (the merged site 1
+# of Section 6.3 carries I_1 K rows, so it is the one site left unfactored):
+#   C_d = [1];  for k = d..2:
+#     T_k = (product core k) x_4 C_{k+1}, reshaped (R_k S_k) x (n_k K_k t_{k+1});
+#     T_k = U diag(s) V^T (SVD); keep the smallest r >= 1 with
+#       sum_{l > r} s_l^2 <= tol^2 ||T_k||_F^2 / (d - 1),  then r <= max_rank if max_rank > 0;
+#     core k <- V^T[:r] (orthonormal rows);  C_k <- U[:, :r] diag(s[:r]);
+#   core 1 <- (product core 1) x_4 C_2.
+# The threshold is relative to the local matrix T_k: the norm of the whole product is not known
+# before the sweep ends (it equals ||T_k||_F when the not-yet-swept left part is orthonormal,
+# which is when this truncation is the optimal one). The result is then rounded and
+# orthogonalised exactly as ``orthogonalize`` does (its two sweeps and the site-1 step), now on
+# bonds of at most max_rank.
+
+def zipup_product(A, X, trans=False, tol=0.0, max_rank=0):
+    """op(A) X (Section 5.2) formed and truncated site by site, right to left (see above)."""
+    from .mpo import contract
+
+    d = len(A)
+    cores = [None] * d
+    C = np.ones((1, 1))
+    for k in range(d - 1, -1, -1):
+        Yk = contract([A[k]], [X[k]], trans)[0]  # (R S, n, Kx, R' S'): the product core of site k
+        T = np.einsum("axcb,bt->axct", Yk, C)  # absorb the carried factor into the right bond
+        if k == 0:
+            cores[0] = T
+            break
+        rs, n, kx, t = T.shape
+        M = T.reshape(rs, n * kx * t, order="F")
+        U, s, Vt = np.linalg.svd(M, full_matrices=False)
+        delta = tol * np.linalg.norm(s) / np.sqrt(d - 1) if d > 1 else 0.0
+        r = keep_rank(s, delta, max_rank)
+        cores[k] = Vt[:r].reshape(r, n, kx, t, order="F")
+        C = U[:, :r] * s[:r]
+    return cores
+
+
+def orthogonalize_zipup(A, X, trans=False, tol=0.0, max_rank=0):
+    """MPO-QR (Alg. 5.2 with the rounding of Section 5.4) of op(A) X rounded as it is formed."""
+    return orthogonalize(zipup_product(A, X, trans, tol, max_rank), tol, max_rank)
+
+
+def mpo_svd_zipup(A, X, tol=0.0, max_rank=0):
+    """MPO-SVD (Alg. 5.3) of B = (A^T X)^T with A^T X rounded as it is formed."""
+    return mpo_svd(zipup_product(A, X, True, tol, max_rank), tol, max_rank)

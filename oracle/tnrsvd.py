@@ -14,8 +14,20 @@ import numpy as np
 from . import mpo, rng, rounding
 
 
-def tnrsvd(A, k, p, q, seed, tol=0.0, max_rank=0, return_info=False):
+def tnrsvd(A, k, p, q, seed, tol=0.0, max_rank=0, return_info=False, rounding_mode="two_sweep"):
+    """rounding_mode: "two_sweep" (the product is formed, then orthogonalised with the rounding of
+    Section 5.4) or "zipup" (every product is rounded while it is formed, right to left, then
+    orthogonalised the same way; see rounding.zipup_product)."""
     K = int(k) + int(p)
+    zip_ = rounding_mode == "zipup"
+    if rounding_mode not in ("two_sweep", "zipup"):
+        raise ValueError("rounding_mode must be 'two_sweep' or 'zipup'")
+
+    def qr_of_product(X, trans):
+        if zip_:
+            return rounding.orthogonalize_zipup(Am, X, trans, tol, max_rank)
+        return rounding.orthogonalize(mpo.contract(Am, X, trans=trans), tol, max_rank)
+
     I, J, _ = mpo.dims(A)
     m = mpo.merge_count(I, J, K)
     if m is None:
@@ -24,18 +36,17 @@ def tnrsvd(A, k, p, q, seed, tol=0.0, max_rank=0, return_info=False):
     Im, Jm, _ = mpo.dims(Am)
     Om = rng.omega(seed, Jm, K)
     info = {"merge": m, "ranks": []}
-    Y = mpo.contract(Am, Om)
-    Q, _ = rounding.orthogonalize(Y, tol, max_rank)
+    Q, _ = qr_of_product(Om, False)
     info["ranks"].append(rounding.ranks(Q))
     for _ in range(int(q)):
-        Y = mpo.contract(Am, Q, trans=True)
-        Q, _ = rounding.orthogonalize(Y, tol, max_rank)
+        Q, _ = qr_of_product(Q, True)
         info["ranks"].append(rounding.ranks(Q))
-        Y = mpo.contract(Am, Q)
-        Q, _ = rounding.orthogonalize(Y, tol, max_rank)
+        Q, _ = qr_of_product(Q, False)
         info["ranks"].append(rounding.ranks(Q))
-    Z = mpo.contract(Am, Q, trans=True)
-    W, S, V = rounding.mpo_svd(Z, tol, max_rank)
+    if zip_:
+        W, S, V = rounding.mpo_svd_zipup(Am, Q, tol, max_rank)
+    else:
+        W, S, V = rounding.mpo_svd(mpo.contract(Am, Q, trans=True), tol, max_rank)
     info["ranks"].append(rounding.ranks(V))
     U = [c.copy() for c in Q]
     U[0] = np.einsum("aicb,ce->aieb", Q[0], W)[:, :, :k, :].copy()

@@ -168,3 +168,70 @@ def test_threshold_pins_pass_with_the_correct_rule(monkeypatch):
     monkeypatch.setattr(oracle.rounding, "_rl_truncate",
                         _patched_rl_truncate(lambda c, tol, d: tol * np.linalg.norm(c[-1]) / np.sqrt(d - 1)))
     _threshold_pins()
+
+
+# ---- planted mistakes in the zip-up rounding of a product ----
+from tests import test_oracle_zipup as tz  # noqa: E402
+
+
+def _patched_zipup(carry, delta_of):
+    """zipup_product with a planted mistake: carry(U, s, r) -> C, delta_of(s, tol, d) -> delta."""
+
+    def bad(A, X, trans=False, tol=0.0, max_rank=0):
+        d = len(A)
+        cores = [None] * d
+        C = np.ones((1, 1))
+        for k in range(d - 1, -1, -1):
+            Yk = oracle.mpo.contract([A[k]], [X[k]], trans)[0]
+            T = np.einsum("axcb,bt->axct", Yk, C)
+            if k == 0:
+                cores[0] = T
+                break
+            rs, n, kx, t = T.shape
+            U, s, Vt = np.linalg.svd(T.reshape(rs, n * kx * t, order="F"), full_matrices=False)
+            r = oracle.rounding.keep_rank(s, delta_of(s, tol, d), max_rank)
+            cores[k] = Vt[:r].reshape(r, n, kx, t, order="F")
+            C = carry(U, s, r)
+        return cores
+
+    return bad
+
+
+_GOOD_CARRY = lambda U, s, r: U[:, :r] * s[:r]  # noqa: E731
+_GOOD_DELTA = lambda s, tol, d: tol * np.linalg.norm(s) / np.sqrt(d - 1)  # noqa: E731
+
+
+def _zipup_pins():
+    tz.test_zipup_without_truncation_is_the_product(False)
+    tz.test_zipup_without_truncation_is_the_product(True)
+    for tol in (0.02, 0.05, 0.1, 0.2):
+        tz.test_zipup_exact_ranks_on_left_canonical_input(tol, 0)
+
+
+def test_zipup_carries_u_without_s(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "zipup_product", _patched_zipup(lambda U, s, r: U[:, :r], _GOOD_DELTA))
+    _fails(_zipup_pins)
+
+
+def test_zipup_threshold_without_sqrt_d_minus_1(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "zipup_product",
+                        _patched_zipup(_GOOD_CARRY, lambda s, tol, d: tol * np.linalg.norm(s)))
+    _fails(_zipup_pins)
+
+
+def test_zipup_threshold_from_squared_norm(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "zipup_product",
+                        _patched_zipup(_GOOD_CARRY, lambda s, tol, d: tol * np.sum(s ** 2) / np.sqrt(d - 1)))
+    _fails(_zipup_pins)
+
+
+def test_zipup_carry_scaled_in_reverse_order(monkeypatch):
+    """The carried factor scaled by the singular values in the wrong order: fails on the product."""
+    monkeypatch.setattr(oracle.rounding, "zipup_product",
+                        _patched_zipup(lambda U, s, r: U[:, :r] * s[:r][::-1], _GOOD_DELTA))
+    _fails(_zipup_pins)
+
+
+def test_zipup_pins_pass_with_the_correct_steps(monkeypatch):
+    monkeypatch.setattr(oracle.rounding, "zipup_product", _patched_zipup(_GOOD_CARRY, _GOOD_DELTA))
+    _zipup_pins()

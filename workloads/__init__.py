@@ -150,7 +150,7 @@ def batched_gaussian(seed, n, d_range=(8, 20), phys=(2, 4), rank_range=(4, 32), 
     return out
 
 
-def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None):
+def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None, canonical="right"):
     """An MPO whose Schmidt spectrum at every bond is prescribed (cores grouped as one physical
     index per site; interior bonds r_k = len(spectra[k-1])).
 
@@ -162,7 +162,9 @@ def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None):
     exactly g * s_k (and ||A||_F = g).
 
     site1_split=(I1, K): return site 1 as (1, I1, K, r_1) (a tall matrix with K columns on site 1,
-    J_k = 1 elsewhere); otherwise every core is (r, n_k, 1, r'). Returns (cores, normalised spectra).
+    J_k = 1 elsewhere); otherwise every core is (r, n_k, 1, r'). canonical="left" moves each s_k
+    (and g) onto the left bond of core k+1 instead (cores 1..d-1 then have orthonormal columns;
+    the Schmidt values are the same). Returns (cores, normalised spectra).
     """
     rng = np.random.default_rng(seed)
     s = [np.asarray(x, dtype=np.float64) / np.linalg.norm(x) for x in spectra]
@@ -178,10 +180,16 @@ def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None):
         rl, rr = r[k], r[k + 1]
         W = orth(int(n[k]), rl * rr).reshape(int(n[k]), rl, rr, order="F")  # column (l, l') -> l + rl l'
         c = W.transpose(1, 0, 2)  # (rl, n, rr)
-        if k < d - 1:
-            c = c * s[k][None, None, :]
-        if k == 0:
-            c = c * float(g)
+        if canonical == "left":
+            if k > 0:
+                c = c * s[k - 1][:, None, None]
+            if k == d - 1:
+                c = c * float(g)
+        else:
+            if k < d - 1:
+                c = c * s[k][None, None, :]
+            if k == 0:
+                c = c * float(g)
         cores.append(c[:, :, None, :].copy())
     if site1_split is not None:
         I1, K = site1_split

@@ -45,7 +45,16 @@ TRAFFIC_BYTES = {"qr_piv": 2.78e6}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 
-def workload_config(precision="mixed"):
+C1_METRIC = "TNrSVD solves/s (4096 x 4096 MPO, d=6, I=J=4, ranks 3, k=10 p=10 q=1, plain FP64)"
+
+
+def workload_config(precision="mixed", which="prescribed"):
+    if which == "c1":
+        c = W.c1_plain_fp64()
+        cfg = {"workload": "Gaussian MPO 4096 x 4096, d=6, I=J=4, ranks 3, N(0,1)/sqrt(12), k=10 p=10 q=1, seed 0",
+               "precision": "all FP64", "tol": c["tol"], "max_rank": c["max_rank"],
+               "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+        return c, cfg
     c = W.c2_prescribed()
     cfg = {
         "workload": "prescribed-sigma MPO 2^20 x 2^20 (merged sites 64,4^7; A ranks 25), k=16 p=16 q=2, seed 2",
@@ -178,49 +187,71 @@ def batched_metric(d, ranks, ks):
             f"ranks {ranks[0]}-{ranks[1]}, k in {set(ks)}, p=k, q=1)")
 
 
-def batched_config(n, d=None, ranks=None, ks=None):
+def batched_config(n, d=None, ranks=None, ks=None, zipup=True):
     d, ranks, ks = d or BATCH_D, ranks or BATCH_RANKS, ks or BATCH_KS
     probs = W.batched_gaussian(0, n, d_range=d, rank_range=ranks, ks=ks)
     cfg = {"workload": f"{n} independent Gaussian-core MPOs, d uniform {d[0]}-{d[1]}, I=J in {{2,4}}, "
                        f"ranks uniform {ranks[0]}-{ranks[1]}, k in {set(ks)}, p=k, q=1, "
-                       "max_rank=K, seed 0",
-           "precision": "products BF16 x3 on tcgen05 / FP32 accumulate, sweeps + SVD + B in FP64",
-           "problems": n, "l2": "flushed between timed steps (256 MiB write)",
-           "parallelism": "batch over host worker threads, one CUDA stream each"}
+                       "max_rank=K, tol 1e-12, seed 0",
+           "rounding": ("zip-up: every product rounded while it is formed, then the Alg. 5.2/5.3 sweeps"
+                        if zipup else "two-sweep: full products, exact compression, Alg. 5.2/5.3 sweeps"),
+           "problems": n, "l2": "flushed between timed steps (256 MiB write)"}
     return probs, cfg
 
 
-# Batched workload sizes. Gaussian cores do not compress, so the products carry R * K-wide bonds
-# into the exact FP64 rounding; ranks up to 32 with K up to 64 (1024-2048-wide bonds) cost
-# 0.2-1.5 s per problem in the FP64 sweeps, so the measured batch uses the smaller shapes below.
-BATCH_D = (8, 12)
-BATCH_RANKS = (2, 6)
-BATCH_KS = (4, 8)
+# Batched workload sizes: the stated distribution. Gaussian cores do not compress, so the products
+# carry R K-wide bonds (up to 2048); the zip-up rounding never forms them.
+BATCH_D = (8, 20)
+BATCH_RANKS = (4, 32)
+BATCH_KS = (8, 16, 32)
 
 
 def batched_main(args):
-    """--workload batched: one step = one solve of the whole batch (persistent kernel by default)."""
+    """--workload batched: one step = one solve of the whole batch (persistent kernel by default).
+    Under torchrun the batch is split over the ranks by greedy LPT on each problem's estimated work
+    (no collective on the data path); every rank solves its share in one persistent launch, the
+    singular values are gathered on rank 0 in batch order, value = problems / max time over ranks."""
     import torch
+    import torch.distributed as dist
 
+    from paper_1707_07803_gb300 import shard
     from paper_1707_07803_gb300 import tnrsvd as T
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     bd, br, bk = tuple(args.batch_d), tuple(args.batch_ranks), tuple(args.batch_ks)
-    probs, cfg = batched_config(args.batch, bd, br, bk)
-    dprobs = [dict(pr, A=T.Mpo.from_numpy(pr["A"], device=dev)) for pr in probs]
+    zipup = args.batch_rounding == "zipup"
+    all_probs, cfg = batched_config(args.batch, bd, br, bk, zipup)
+    costs = []
+    for pr in all_probs:
+        I = [c.shape[1] for c in pr["A"]]
+        J = [c.shape[2] for c in pr["A"]]
+        R = [1] + [c.shape[3] for c in pr["A"]]
+        costs.append(shard.problem_cost(I, J, R, pr["k"], pr["p"], pr["q"], pr["max_rank"], zipup))
+    parts, loads = shard.lpt_partition(costs, world)
+    probs = [all_probs[i] for i in parts[rank]]
+    rounding = T.TNR_ROUND_ZIPUP if zipup else T.TNR_ROUND_TWO_SWEEP
+    dprobs = [dict(pr, A=T.Mpo.from_numpy(pr["A"], device=dev), rounding=rounding) for pr in probs]
     persistent = args.batch_impl == "persistent"
+    if world > 1:
+        cfg["parallelism"] = (f"batch split over {world} GPUs by greedy LPT on estimated work (max/mean load "
+                              f"{max(loads) / (sum(loads) / world):.3f}), one process per GPU, no collective on "
+                              "the data path, singular values gathered on rank 0")
     if persistent:
         plan = T.PersistentBatch(dprobs, precision=T.TNR_MIXED, autotune=True, graph=True, stream=stream)
         run = lambda: plan.launch(stream)  # noqa: E731
         pc = plan.config()
-        cfg["parallelism"] = (f"persistent kernel: one CTA per problem from a device work queue, grid {pc['grid']} "
-                              f"({pc['ctas_per_sm']} CTAs/SM autotuned, {pc['smem_bytes'] // 1024} KB shared "
-                              "memory each), one CUDA-graph launch per batch")
-        cfg["precision"] = ("site-1 products BF16 x3 / FP32 accumulate (FP32 pipe), other products, sweeps, "
-                            "SVD and B in FP64")
+        cfg["kernel"] = (f"persistent kernel: one CTA per problem from a device work queue, grid {pc['grid']} "
+                         f"({pc['ctas_per_sm']} CTAs/SM autotuned, {pc['smem_bytes'] // 1024} KB shared "
+                         "memory each), one CUDA-graph launch per batch")
+        cfg["precision"] = ("products of the power iteration with FP32 operands / FP32 accumulation (FP32 pipe), "
+                            "roundings, QR, SVD and B in FP64")
     else:
         plan = T.BatchPlan(dprobs, workers=args.workers, precision=T.TNR_MIXED)
         run = plan.run  # noqa: E731
@@ -234,6 +265,9 @@ def batched_main(args):
     T.stats_enable(0)
     sampler = ClockSampler(local)
     sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     total_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -244,6 +278,9 @@ def batched_main(args):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = sampler.stop()
     launches, _ = T.stats(-1)
     if persistent:
@@ -288,15 +325,20 @@ def batched_main(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    n = plan.n
-    value = n * args.steps / (total_ms / 1000.0)
-    ms_step = total_ms / args.steps
+    n = args.batch
+    # the slowest rank bounds the job; all problems of the batch over that time
+    _, max_ms = replicas_rate(total_ms, args.steps, world, dev, dist)
+    value = n * args.steps / (max_ms / 1000.0)
+    ms_step = max_ms / args.steps
+    _, e2e_max = replicas_rate(e2e_ms, args.steps, world, dev, dist)
+    S_all = shard.gather_in_order([plan.outputs(i)[1].cpu().numpy().tolist() for i in range(plan.n)], parts, rank,
+                                  world, dist)
     achieved = fp64_flops_per_batch / (ms_step * 1e-3) / 1e9
     line = {
-        "metric": batched_metric(bd, br, bk), "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": batched_metric(bd, br, bk), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES["mixed"], "data": "synthetic", "config": cfg,
-        "e2e": {"value": n * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic", "config": cfg,
+        "e2e": {"value": n * args.steps / (e2e_max / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "launches_per_step": launches_per_step,
@@ -306,11 +348,16 @@ def batched_main(args):
                      "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
                      "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
                      "note": ("algorithmic FP64 flops of the batch (products, merges, QRs, compression, "
-                              "absorbs, SVD-step QRs; Jacobi sweeps and BF16 x3 products not counted) / batch time")},
+                              "absorbs, SVD-step QRs; Jacobi sweeps and the FP32 products of mixed mode not counted) / batch time")},
         "clocks": clocks,
         "statuses_ok": bool(ok),
     }
-    print(json.dumps(line))
+    if rank == 0:
+        line["gathered_problems"] = len(S_all)
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -401,6 +448,130 @@ def sparse_main(args):
     return 0
 
 
+CONV_METRIC = "sparse->MPO conversions/s (Alg. 4.1; 2^20 x 2^20 banded, 8 nnz/row, band 64, ten 4x4 sites)"
+
+
+def conversion_main(args):
+    """--workload conversion: one step = Alg. 4.1 on the device (tnr_sparse_count + tnr_sparse_fill
+    into preallocated outputs; the count synchronises once to read R)."""
+    import torch
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = 1 << 20
+    I = J = [4] * 10
+    d = len(I)
+    r, c, v = W.banded_coo(0, n, 8, 64)
+    nnz = int(r.size)
+    rd, cd, vd = (torch.from_numpy(x).to(dev) for x in (r, c, v))
+    ws = torch.empty(max(T.tnr_sparse_workspace(n, n, nnz, I, J), 1), dtype=torch.uint8, device=dev)
+    R = T.tnr_sparse_count(n, n, rd, cd, I, J, ws)
+    X = torch.empty(R * 16, dtype=torch.float64, device=dev)
+    digits = torch.empty(R * 2 * (d - 1), dtype=torch.uint8, device=dev)
+
+    def step():
+        Rs = T.tnr_sparse_count(n, n, rd, cd, I, J, ws)
+        T.tnr_sparse_fill(n, n, rd, cd, vd, I, J, Rs, X, digits, ws)
+        return Rs
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    classes = T.stats_classes()
+    names = ("conv_flags", "conv_scan", "conv_fill")
+    T.stats_reset()
+    T.stats_enable(sum(1 << classes.index(x) for x in names))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    per = {x: T.stats(classes.index(x)) for x in names}
+    launches, _ = T.stats(-1)
+    T.stats_enable(0)
+    peaks = read_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    src = "hbm_gbs of MEASURED_PEAKS.json (measured copy)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+    out_bytes = R * (8.0 * I[0] * J[0] + 2.0 * (d - 1))
+    # algorithmic bytes: the count pass reads row and col (16 B per nonzero); the fill pass reads
+    # row, col and val (24 B per nonzero) and writes every block's values and digits once
+    alg = {"conv_flags": 16.0 * nnz, "conv_fill": 24.0 * nnz + out_bytes}
+    fill_l, fill_ms = per["conv_fill"]
+    fill_ms_step = fill_ms / args.steps
+    fill_gbs = alg["conv_fill"] / (fill_ms_step * 1e-3) / 1e9
+    flags_l, flags_ms = per["conv_flags"]
+    step_ms = total_ms / args.steps
+    whole_gbs = (alg["conv_flags"] + alg["conv_fill"]) / (step_ms * 1e-3) / 1e9
+    # end to end: H2D of the COO triplets from pinned memory, conversion, D2H of X and digits
+    hr, hc, hv = (torch.from_numpy(x).pin_memory() for x in (r, c, v))
+    hX = torch.empty(X.numel(), dtype=torch.float64).pin_memory()
+    hD = torch.empty(digits.numel(), dtype=torch.uint8).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rd.copy_(hr, non_blocking=True)
+        cd.copy_(hc, non_blocking=True)
+        vd.copy_(hv, non_blocking=True)
+        step()
+        hX.copy_(X, non_blocking=True)
+        hD.copy_(digits, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    line = {
+        "metric": CONV_METRIC, "value": args.steps / (total_ms / 1000.0), "unit": "conversions/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64 (copy only)", "data": "synthetic",
+        "config": {"workload": f"banded 2^20 x 2^20, 8 nnz/row in [i-64, i+64], N(0,1), int64 COO sorted, "
+                               f"ten 4x4 sites; R = {R} blocks", "nnz": nnz,
+                   "l2": "flushed between timed steps (256 MiB write); inputs 201 MB, outputs "
+                         f"{out_bytes / 1e6:.0f} MB"},
+        "e2e": {"value": args.steps / (e2e_ms / 1000.0), "unit": "conversions/s", "h2d_bytes_per_step": 24 * nnz,
+                "d2h_bytes_per_step": int(X.numel() * 8 + digits.numel())},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_zero + k_fill_w (block zeroing and warp-window fill of Alg. 4.1)", "class": "conv_fill",
+                     "bound": "hbm", "achieved": fill_gbs, "peak": hbm, "unit": "GB/s", "peak_source": src,
+                     "frac": fill_gbs / hbm, "traffic": None, "launches_per_step": fill_l / args.steps,
+                     "avg_launch_us": 1000 * fill_ms / max(fill_l, 1), "share_of_step": fill_ms / max(total_ms, 1e-9),
+                     "note": "algorithmic bytes 24 B per nonzero read + R (8 I1 J1 + 2 (d-1)) B written"},
+        "count_pass": {"kernel": "k_first_scan (first-occurrence flags and per-tile counts)",
+                       "achieved_gbs": alg["conv_flags"] / (flags_ms / args.steps * 1e-3) / 1e9 if flags_ms else None,
+                       "share_of_step": flags_ms / max(total_ms, 1e-9)},
+        "whole_conversion_gbs": whole_gbs,
+        "clocks": clocks,
+    }
+    from oracle import convert as oc  # the CPU baseline: the oracle of Alg. 4.1 as it stands
+
+    t0 = time.perf_counter()
+    k_cpu = 0
+    while True:
+        oc.convert(r, c, v, n, n, I, J)
+        k_cpu += 1
+        el = time.perf_counter() - t0
+        if el > args.cpu_budget or k_cpu >= 5:
+            break
+    line["cpu_baseline"] = {"value": k_cpu / el, "unit": "conversions/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{k_cpu} whole conversions of the same matrix in {el:.1f} s (numpy)"}
+    print(json.dumps(line))
+    return 0
+
+
 ADJ_METRIC = ("gradient evaluations/s of L = sum of the top-16 TNrSVD singular values "
               "(4^12 x 4^12 MPO, rank 16, k=16 p=16 q=2, FP64 forward + adjoint)")
 
@@ -485,11 +656,12 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="prescribed", choices=["prescribed", "batched", "adjoint", "sparse"],
-                    help="prescribed: one 2^20 x 2^20 solve per step (default); batched: a batch of "
-                         "independent Gaussian-core MPOs per step (persistent kernel); adjoint: forward "
-                         "and backward of the differentiable solve per step; sparse: Alg. 4.1 conversion "
-                         "and the block-sparse TNrSVD per step")
+    ap.add_argument("--workload", default="prescribed",
+                    choices=["prescribed", "c1", "batched", "adjoint", "sparse", "conversion"],
+                    help="prescribed: one 2^20 x 2^20 solve per step (default); c1: the plain FP64 4096 x 4096 "
+                         "solve; batched: a batch of independent Gaussian-core MPOs per step (persistent "
+                         "kernel); adjoint: forward and backward of the differentiable solve per step; sparse: "
+                         "Alg. 4.1 conversion and the block-sparse TNrSVD per step; conversion: Alg. 4.1 alone")
     ap.add_argument("--fd-entries", type=int, default=16)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--workers", type=int, default=16)
@@ -498,9 +670,12 @@ def main():
     ap.add_argument("--batch-d", type=int, nargs=2, default=list(BATCH_D), help="batched: range of d")
     ap.add_argument("--batch-ranks", type=int, nargs=2, default=list(BATCH_RANKS), help="batched: range of ranks")
     ap.add_argument("--batch-ks", type=int, nargs="+", default=list(BATCH_KS), help="batched: set of k")
+    ap.add_argument("--batch-rounding", default="zipup", choices=["zipup", "two_sweep"],
+                    help="batched: rounding of the products (zip-up by default)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"prescribed": 200, "sparse": 20, "batched": 20, "adjoint": 2}[args.workload]
+        args.steps = {"prescribed": 200, "c1": 200, "sparse": 20, "batched": 5, "adjoint": 2,
+                      "conversion": 50}[args.workload]
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batched":
@@ -509,6 +684,10 @@ def main():
         return adjoint_main(args)
     if args.workload == "sparse":
         return sparse_main(args)
+    if args.workload == "conversion":
+        return conversion_main(args)
+    if args.workload == "c1":
+        args.precision = "fp64"  # the plain FP64 configuration
 
     import torch
     import torch.distributed as dist
@@ -524,7 +703,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    c, cfg = workload_config(args.precision)
+    c, cfg = workload_config(args.precision, args.workload)
+    metric = C1_METRIC if args.workload == "c1" else METRIC
     A = T.Mpo.from_numpy(c["A"], device=dev)
     precision = T.TNR_MIXED if args.precision == "mixed" else T.TNR_FP64
     plan = T.SolvePlan(A, c["k"], c["p"], tol=c["tol"], max_rank=c["max_rank"], precision=precision)
@@ -574,9 +754,10 @@ def main():
     T.stats_enable(0)
     value, max_ms = replicas_rate(total_ms, args.steps, world, dev, dist)
 
-    # accuracy of this run against the exact singular values
+    # accuracy of this run against the exact singular values (prescribed workload)
     S = plan.S.cpu().numpy()
-    sv_err = float(np.linalg.norm(S - c["sigma"][: c["k"]]) / np.linalg.norm(c["sigma"][: c["k"]]))
+    sv_err = (float(np.linalg.norm(S - c["sigma"][: c["k"]]) / np.linalg.norm(c["sigma"][: c["k"]]))
+              if "sigma" in c else None)
 
     # end to end through the public API with host buffers: H2D of the cores, solve, D2H of U, S, V
     host_cores = [torch.from_numpy(np.ascontiguousarray(np.asarray(x).reshape(-1, order="F"))).pin_memory()
@@ -605,7 +786,7 @@ def main():
     qr_avg_ms = qr_ms / max(qr_launches, 1)
     achieved_gflops = (qr_flops / max(qr_launches, 1)) / (qr_avg_ms * 1e-3) / 1e9 if qr_launches else 0.0
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic", "config": cfg,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -635,6 +816,12 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{n} whole solves of the same workload in {el:.1f} s (numpy/LAPACK FP64)"}
         line["accuracy"]["sv_rel_err_vs_oracle"] = float(np.linalg.norm(S - So) / np.linalg.norm(So))
+        if args.workload == "c1":  # information: against the dense 4096 x 4096 LAPACK SVD (no bound holds)
+            from oracle import mpo as om
+
+            s_true = np.linalg.svd(om.dense(c["A"]), compute_uv=False)[: c["k"]]
+            line["accuracy"]["sv_rel_err_vs_dense_lapack"] = float(np.linalg.norm(S - s_true) / np.linalg.norm(s_true))
+            line["accuracy"]["max_rel_err_vs_dense_lapack"] = float(np.max(np.abs(S - s_true) / s_true))
         print(json.dumps(line))
     if world > 1:
         dist.barrier()

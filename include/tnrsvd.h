@@ -51,10 +51,14 @@ enum tnr_status {
 
 enum tnr_precision {
   TNR_FP64 = 0,  /* every step in float64 */
-  TNR_MIXED = 1  /* products A*Omega, A^T Q, A Q in BF16 (x3 split, FP32 accumulation; the dense
-                    site-1 products on tcgen05 tensor cores), their roundings at tolerance
-                    max(tol, 1.2e-4) (the products' noise level); B = Q^T A, its rounding with
-                    tol, the QR sweeps and the SVDs in float64 */
+  TNR_MIXED = 1  /* products A*Omega, A^T Q, A Q with reduced-precision operands and FP32
+                    accumulation, B = Q^T A, its rounding with tol, the QR sweeps and the SVDs in
+                    float64. Single solve (tnr_solve, tnr_solve_batched): BF16 x3 operands (about
+                    2^-16 relative; the dense site-1 products on tcgen05 tensor cores), the
+                    power iteration rounded at max(tol, 1.2e-4). Persistent batch (tnr_batch_*):
+                    FP32 operands on the FP32 pipe (about 2^-24 relative, one FMA per term), the
+                    power iteration rounded at max(tol, 1e-6). The tolerances sit above each
+                    product's noise level, so the rounding does not keep noise directions. */
 };
 
 /* Element type of an MPO's cores. Outputs are always TNR_F64. TNR_F32 inputs are accepted by
@@ -76,12 +80,25 @@ typedef struct tnr_mpo {
   int64_t cap[TNR_MAX_SITES];
 } tnr_mpo;
 
+/* How a product is rounded (Section 5.4 integrates SVD-based rounding with the MPO-QR sweep).
+ * TNR_ROUND_TWO_SWEEP: the product op(A) X is formed in full (ranks R_k S_k), then orthogonalised:
+ *   left-to-right QR sweep, right-to-left truncating SVD sweep, site-1 step of Alg. 5.2/5.3.
+ * TNR_ROUND_ZIPUP (truncate as you go): the product is rounded while it is formed, right to left:
+ *   at site k the product core, with the factor carried from site k+1 absorbed into its right bond,
+ *   is the (R_k S_k) x (n_k K_k t_{k+1}) matrix T_k; its SVD keeps the smallest r >= 1 with
+ *   sum_{l>r} s_l^2 <= tol^2 ||T_k||_F^2 / (d-1) (then r <= max_rank), core k becomes the r kept
+ *   right singular vectors and U diag(s) is carried to site k-1; site 1 absorbs the last factor.
+ *   The product cores are never formed. The result is then orthogonalised as above (on bonds of
+ *   at most max_rank). Accepted by the persistent batched solver (tnr_batch_*); the other entry
+ *   points require TNR_ROUND_TWO_SWEEP (TNR_EINVAL otherwise). */
+enum tnr_rounding { TNR_ROUND_TWO_SWEEP = 0, TNR_ROUND_ZIPUP = 1 };
+
 /* Rounding options (Section 5.4 integrates SVD-based rounding with the MPO-QR sweep).
  * At each bond the smallest rank r >= 1 is kept whose discarded singular values satisfy
  * sum s_l^2 <= delta^2, delta = tol * ||Y||_F / sqrt(d - 1); then r <= max_rank if max_rank > 0. */
 typedef struct tnr_opts {
   int32_t precision;  /* enum tnr_precision */
-  int32_t reserved;
+  int32_t rounding;   /* enum tnr_rounding */
   double tol;
   int64_t max_rank;   /* 0: only the structural bounds of Thm 3.2 apply */
 } tnr_opts;

@@ -19,10 +19,17 @@
 // per shape bucket: several problems per SM share its FP64 pipes and hide each other's latency
 // chains, fewer leave more of the factorisations in shared memory.
 //
-// Mixed precision follows the single solve: the dense site-1 products of the power iteration
-// use BF16 x3 operands (hi*hi + hi*lo + lo*hi) with FP32 accumulation, here on the FP32 pipe;
-// the roundings of the power iteration use tol_p = max(tol, kMixedTol); B = Q^T A, every QR, SVD
-// and sweep are FP64.
+// Mixed precision: the products of the power iteration (the dense site-1 products, and every site
+// of a zip-up product) run with FP32 operands and FP32 accumulation on the FP32 pipe (inside one
+// CTA that is both cheaper and more accurate than a BF16 split: one FMA per term, about 2^-24
+// relative); the roundings of the power iteration use tol_p = max(tol, kMixedTolF32), above the
+// products' noise level; B = Q^T A, every QR, SVD and sweep are FP64.
+//
+// Rounding of a product: either the two-sweep form (the product is formed in full, then the exact
+// right-to-left compression, the rounding sweeps and the site-1 step of Alg. 5.2), or the zip-up
+// form (TNR_ROUND_ZIPUP: the product is rounded while it is formed, right to left, so product
+// cores of rank R_k S_k never exist; the rounding sweeps and the site-1 step follow on the small
+// result).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -45,6 +52,7 @@ static_assert(kSmallThreads == kStepThreads, "the one-CTA helpers share one bloc
 // m sites: I, J, RA; the leading cores themselves (Ain[0..m-1]) are merged on the device.
 struct BatchProblem {
   int d0, m, d, K, k, q, mixed, status;
+  int zip, pad_;  // zip: products rounded as they are formed (TNR_ROUND_ZIPUP)
   uint64_t seed;
   double tol;
   int64_t max_rank;
@@ -57,6 +65,10 @@ struct BatchProblem {
   int64_t pcap[TNR_MAX_SITES];
   double *tmp, *rbuf, *work, *gram, *Rm, *W, *Zr, *Sv;
   int64_t work_cap, gram_cap;  // doubles
+  // zip-up scratch: carried factors (ping-pong), partial contraction, product matrix, FP32 copies
+  double *zc[2], *zw, *zt;
+  float *zf;
+  int64_t zc_cap, zw_cap, zt_cap, zf_cap;  // elements
   // outputs (caller's buffers) and the ranks the solve chose
   double *Uc[TNR_MAX_SITES], *Vc[TNR_MAX_SITES];
   int64_t Ucap[TNR_MAX_SITES], Vcap[TNR_MAX_SITES];
@@ -138,27 +150,22 @@ __device__ const double *cta_merge(const BatchProblem &P, const Ctx &c) {
   return T;
 }
 
-// Dense site-1 product with BF16 x3 operands and FP32 accumulation (the arithmetic of the
-// tensor-core product): A (1, I, J, R2), X (1, Ny, Kx, S2), Y (Xo, Kx, R2 S2).
-__device__ void cta_product_bf16x3(BatchProblem &P, const Ctx &c, const double *A, int I, int J, int R2,
-                                   const double *X, int Kx, int S2, int trans, double *Y) {
+// Dense site-1 product with FP32 operands and FP32 accumulation: every operand is rounded to FP32
+// once (staged in the work area; on GB300 a double->float conversion issues on the FP64 pipe, so it
+// is done once per element, not once per multiply-add), then one FMA per term on the FP32 pipe.
+// A (1, I, J, R2), X (1, Ny, Kx, S2), Y (Xo, Kx, R2 S2).
+__device__ void cta_product_f32(BatchProblem &P, const Ctx &c, const double *A, int I, int J, int R2,
+                                const double *X, int Kx, int S2, int trans, double *Y) {
   const int Xo = trans ? J : I, Ny = trans ? I : J;
   const int na = I * J * R2, nx = Ny * Kx * S2;
-  double *area = pick(P, c, (int64_t)na + nx);
+  double *area = pick(P, c, ((int64_t)na + nx + 1) / 2);
   if (!area) return;
-  float *ah = reinterpret_cast<float *>(area), *al = ah + na, *xh = al + na, *xl = xh + nx;
+  float *af = reinterpret_cast<float *>(area), *xf = af + na;
   for (int e = threadIdx.x; e < na + nx; e += kBT) {
-    const float f = (float)(e < na ? A[e] : X[e - na]);
-    const __nv_bfloat16 hi = __float2bfloat16(f);
-    const float hf = __bfloat162float(hi);
-    const float lf = __bfloat162float(__float2bfloat16(f - hf));
-    if (e < na) {
-      ah[e] = hf;
-      al[e] = lf;
-    } else {
-      xh[e - na] = hf;
-      xl[e - na] = lf;
-    }
+    if (e < na)
+      af[e] = (float)A[e];
+    else
+      xf[e - na] = (float)X[e - na];
   }
   __syncthreads();
   const int total = Xo * Kx * R2 * S2;
@@ -169,12 +176,7 @@ __device__ void cta_product_bf16x3(BatchProblem &P, const Ctx &c, const double *
     const int as = trans ? 1 : I;
     const int x0 = Ny * (cc + Kx * s2);
     float acc = 0.f;
-    for (int y = 0; y < Ny; ++y) {
-      const float a_h = ah[a0 + as * y], a_l = al[a0 + as * y], x_h = xh[x0 + y], x_l = xl[x0 + y];
-      acc = fmaf(a_h, x_h, acc);
-      acc = fmaf(a_h, x_l, acc);
-      acc = fmaf(a_l, x_h, acc);
-    }
+    for (int y = 0; y < Ny; ++y) acc = fmaf(af[a0 + as * y], xf[x0 + y], acc);
     Y[idx] = (double)acc;
   }
   __syncthreads();
@@ -198,7 +200,7 @@ __device__ void cta_contract(BatchProblem &P, const Ctx &c, const double *A0, in
     const double *X = Xc[k];
     double *Y = Yc[k];
     if (mixed && R == 1 && S == 1 && Ny >= 16) {
-      cta_product_bf16x3(P, c, A, I, J, R2, X, Kx, S2, trans, Y);
+      cta_product_f32(P, c, A, I, J, R2, X, Kx, S2, trans, Y);
       continue;
     }
     const int RS = R * S, nt = (int)total;
@@ -225,6 +227,130 @@ __device__ void cta_contract(BatchProblem &P, const Ctx &c, const double *A0, in
     for (int k = 0; k < P.d; ++k) YR[k + 1] = P.RA[k + 1] * XR[k + 1];
   }
   __syncthreads();
+}
+
+// Y = op(A) X rounded while it is formed (zip-up, TNR_ROUND_ZIPUP), right to left. With C the
+// factor carried from site k+1 ((R_{k+1} S_{k+1}) x t, bond r + R s), site k forms
+//   T[(r + R s), x, c, b] = sum_y sum_{r2} A_k(r, x, y, r2) sum_{s2} X_k(s, y, c, s2) C[(r2 + R2 s2), b]
+// one value of the shared physical index y at a time (W = X_k(:, y, :, :) C is S Kx R2 t values),
+// so neither the product core nor a full partial contraction is stored. For k >= 1, T is the
+// (R S) x (Xo Kx t) matrix of the truncated-SVD step (svd_step_cta): the smallest rank r >= 1 with
+// discarded squared singular values <= tol_z^2 ||T||_F^2 / (d - 1), then r <= max_rank; core k
+// becomes the r kept right singular vectors (orthonormal rows) and U diag(s) the next C. Site 0
+// absorbs the last C. mixed: X_k, C and A_k are rounded to FP32 once per site and the sums run in
+// FP32; T and the SVD stay FP64. Output ranks go to YR.
+__device__ __noinline__ void cta_zipup(BatchProblem &P, const Ctx &c, const double *A0, int trans, const double *const *Xc,
+                          const int *XR, double *const *Yc, int *YR, double tol_z, int64_t max_rank, bool mixed) {
+  __shared__ int s_t;
+  const int d = P.d;
+  double *C = P.zc[0], *Cn = P.zc[1];
+  if (threadIdx.x == 0) {
+    C[0] = 1.0;
+    s_t = 1;
+    YR[0] = 1;
+    YR[d] = 1;
+  }
+  __syncthreads();
+  for (int k = d - 1; k >= 0; --k) {
+    const int t = s_t;
+    const int R = P.RA[k], I = P.I[k], J = P.J[k], R2 = P.RA[k + 1];
+    const int S = XR[k], S2 = XR[k + 1];
+    const int Kx = k == 0 ? P.K : 1;
+    const int Xo = trans ? J : I, Ny = trans ? I : J;
+    const int RS = R * S, w = Xo * Kx * t;
+    const double *A = k == 0 ? A0 : P.Ain[P.m - 1 + k];
+    const double *X = Xc[k];
+    const int64_t nT = (int64_t)RS * w, nW = (int64_t)S * Kx * R2 * t;
+    double *T = k == 0 ? Yc[0] : P.zt;
+    if ((k == 0 && nT > P.pcap[0]) || (k > 0 && nT > P.zt_cap) || nW > P.zw_cap) {
+      set_status(&P.status, k == 0 ? TNR_ENOMEM : TNR_ERANGE);
+      return;
+    }
+    for (int64_t i = threadIdx.x; i < nT; i += kBT) T[i] = 0.0;
+    // A_k(r, x, y, r2) at a_base(r, x, r2) + a_y * y
+    const int a_y = trans ? R : R * I;
+    const int nA = R * I * J * R2, nX = S * Ny * Kx * S2, nC = R2 * S2 * t;
+    float *Af = P.zf, *Xf = Af + nA, *Cf = Xf + nX, *Wf = Cf + nC;
+    if (mixed) {
+      if ((int64_t)nA + nX + nC + nW > P.zf_cap) {
+        set_status(&P.status, TNR_ERANGE);
+        return;
+      }
+      for (int e = threadIdx.x; e < nA + nX + nC; e += kBT) {
+        if (e < nA)
+          Af[e] = (float)A[e];
+        else if (e < nA + nX)
+          Xf[e - nA] = (float)X[e - nA];
+        else
+          Cf[e - nA - nX] = (float)C[e - nA - nX];
+      }
+    }
+    __syncthreads();
+    for (int y = 0; y < Ny; ++y) {
+      // W[s + S (cc + Kx (r2 + R2 b))] = sum_{s2} X_k(s, y, cc, s2) C[(r2 + R2 s2) + R2 S2 b]
+      for (int idx = threadIdx.x; idx < (int)nW; idx += kBT) {
+        const int s_ = idx % S, u = idx / S, cc = u % Kx, v = u / Kx, r2 = v % R2, b = v / R2;
+        const int x0 = s_ + S * (y + Ny * cc), xs = S * Ny * Kx;
+        const int c0 = r2 + R2 * S2 * b, cs = R2;
+        if (mixed) {
+          float acc = 0.f;
+          for (int s2 = 0; s2 < S2; ++s2) acc = fmaf(Xf[x0 + xs * s2], Cf[c0 + cs * s2], acc);
+          Wf[idx] = acc;
+        } else {
+          double acc = 0.0;
+          for (int s2 = 0; s2 < S2; ++s2) acc = fma(X[x0 + xs * s2], C[c0 + cs * s2], acc);
+          P.zw[idx] = acc;
+        }
+      }
+      __syncthreads();
+      // T[(r + R s) + RS (x + Xo (cc + Kx b))] += sum_{r2} A_k(r, x, y, r2) W[s, cc, r2, b]
+      for (int idx = threadIdx.x; idx < (int)nT; idx += kBT) {
+        const int rs = idx % RS, u = idx / RS, x = u % Xo, v = u / Xo, cc = v % Kx, b = v / Kx;
+        const int r = rs % R, s_ = rs / R;
+        const int a0 = (trans ? r + R * (I * x) : r + R * x) + a_y * y, as = R * I * J;
+        const int w0 = s_ + S * (cc + Kx * R2 * b), ws = S * Kx;
+        if (mixed) {
+          float acc = 0.f;
+          for (int r2 = 0; r2 < R2; ++r2) acc = fmaf(Af[a0 + as * r2], Wf[w0 + ws * r2], acc);
+          T[idx] += (double)acc;
+        } else {
+          double acc = 0.0;
+          for (int r2 = 0; r2 < R2; ++r2) acc = fma(A[a0 + as * r2], P.zw[w0 + ws * r2], acc);
+          T[idx] += acc;
+        }
+      }
+      __syncthreads();
+    }
+    if (!mixed) addf(c, 2.0 * Ny * ((double)nW * S2 + (double)nT * R2));  // FP64 work only
+    if (k == 0) break;
+    // truncated SVD of T ((R S) x w), threshold relative to ||T||_F
+    double nrm2;
+    {
+      double a = 0.0;
+      for (int64_t i = threadIdx.x; i < nT; i += kBT) a = fma(T[i], T[i], a);
+      nrm2 = cta_sum(a, kBT, c.red, c.sc);
+    }
+    if (svd_step_work(RS, w) > P.work_cap || (RS < w ? RS : w) > kStepMaxN) {
+      set_status(&P.status, TNR_ERANGE);
+      return;
+    }
+    const double delta2 = tol_z * tol_z * nrm2 / (double)(d - 1);
+    double *work = pick(P, c, svd_step_work(RS, w));
+    if (!work) return;
+    const int r = svd_step_cta(T, RS, w, delta2, max_rank, Yc[k], Cn, work, &P.status);
+    {
+      const double mm = RS > w ? RS : w, n = RS > w ? w : RS;
+      addf(c, 2 * mm * n * n - 2 * n * n * n / 3);
+    }
+    if (threadIdx.x == 0) {
+      YR[k] = r;
+      s_t = r;
+    }
+    double *tmpc = C;
+    C = Cn;
+    Cn = tmpc;
+    __syncthreads();
+  }
 }
 
 // Exact right-to-left compression (as the single solve's compression sweep): for k = d-1..1,
@@ -391,11 +517,15 @@ __device__ double *cta_site1_qr(BatchProblem &P, const Ctx &c, const double *cor
   return A;
 }
 
-// MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4) of a tall-matrix MPO.
+// MPO-QR with integrated rounding (Alg. 5.2 + Section 5.4) of a tall-matrix MPO. zipped: the
+// MPO comes from a zip-up product (cores 1..d-1 right-orthonormal already, no compression). The
+// Gram no-truncation certificate is not used then: the zip-up truncates in a non-orthonormal gauge
+// and can keep directions whose canonical Schmidt values lie far below sqrt(eps) ||Y||, which a
+// Gram matrix formed in FP64 cannot resolve; the sweeps (QR and SVD of the cores) do resolve them.
 __device__ void cta_orthogonalize(BatchProblem &P, const Ctx &c, double *const *core, int *R, int rowsJ, double tol,
-                                  int64_t max_rank, bool mixed_product) {
+                                  int64_t max_rank, bool mixed_product, bool zipped) {
   bool right_orth = false;
-  if (tol > 0.0) right_orth = cta_compress(P, c, core, R, rowsJ, compress_cut(tol, mixed_product));
+  if (!zipped && tol > 0.0) right_orth = cta_compress(P, c, core, R, rowsJ, compress_cut(tol, mixed_product));
   cta_round(P, c, core, R, rowsJ, tol, max_rank, right_orth);
   if (failed(P)) return;
   const int I1 = rowsJ ? P.J[0] : P.I[0], K = P.K, t = R[1], m = I1 * t;
@@ -410,9 +540,9 @@ __device__ void cta_orthogonalize(BatchProblem &P, const Ctx &c, double *const *
 
 // MPO-SVD (Alg. 5.3 + Section 5.4) of B = Z^T (Z = A^T Q, cores P1 / ranks R): rounding, site-1
 // QR M^T = Q~ R~, one-sided Jacobi R~^T = W S Zr^T, V^(1) from Q~ Zr (first k columns).
-__device__ void cta_mpo_svd(BatchProblem &P, const Ctx &c, double *const *core, int *R) {
-  bool right_orth = false;
-  if (P.tol > 0.0) right_orth = cta_compress(P, c, core, R, 1, compress_cut(P.tol, false));
+__device__ void cta_mpo_svd(BatchProblem &P, const Ctx &c, double *const *core, int *R, bool zipped) {
+  bool right_orth = false;  // zipped: no compression and no certificate (see cta_orthogonalize)
+  if (!zipped && P.tol > 0.0) right_orth = cta_compress(P, c, core, R, 1, compress_cut(P.tol, false));
   cta_round(P, c, core, R, 1, P.tol, P.max_rank, right_orth);
   if (failed(P)) return;
   const int J1 = P.J[0], K = P.K, t = R[1], m = J1 * t, kout = P.k;
@@ -495,25 +625,31 @@ __device__ void cta_solve(BatchProblem &P, const Ctx &c) {
     RO[d] = 1;
   }
   __syncthreads();
-  const bool mixed = P.mixed != 0;
-  const double tol_p = mixed ? fmax(P.tol, kMixedTol) : P.tol;
-  cta_contract(P, c, A0, 0, Oc, RO, P.P0, RY0, mixed);  // Y = A Omega
-  if (failed(P)) return;
-  cta_orthogonalize(P, c, P.P0, RY0, 0, tol_p, P.max_rank, mixed);
+  const bool mixed = P.mixed != 0, zip = P.zip != 0;
+  const double tol_p = mixed ? fmax(P.tol, kMixedTolF32) : P.tol;
+  // Y = op(A) X followed by MPO-QR: formed in full and compressed, or rounded as it is formed
+  auto product_qr = [&](int trans, const double *const *Xc, const int *XR, double *const *Yc, int *YR) {
+    if (zip)
+      cta_zipup(P, c, A0, trans, Xc, XR, Yc, YR, tol_p, P.max_rank, mixed);
+    else
+      cta_contract(P, c, A0, trans, Xc, XR, Yc, YR, mixed);
+    if (failed(P)) return;
+    cta_orthogonalize(P, c, Yc, YR, trans, tol_p, P.max_rank, mixed, zip);
+  };
+  product_qr(0, Oc, RO, P.P0, RY0);  // Y = A Omega
   if (failed(P)) return;
   for (int it = 0; it < P.q; ++it) {
-    cta_contract(P, c, A0, 1, P.P0, RY0, P.P1, RY1, mixed);  // A^T Q
+    product_qr(1, P.P0, RY0, P.P1, RY1);  // A^T Q
     if (failed(P)) return;
-    cta_orthogonalize(P, c, P.P1, RY1, 1, tol_p, P.max_rank, mixed);
-    if (failed(P)) return;
-    cta_contract(P, c, A0, 0, P.P1, RY1, P.P0, RY0, mixed);  // A Q
-    if (failed(P)) return;
-    cta_orthogonalize(P, c, P.P0, RY0, 0, tol_p, P.max_rank, mixed);
+    product_qr(0, P.P1, RY1, P.P0, RY0);  // A Q
     if (failed(P)) return;
   }
-  cta_contract(P, c, A0, 1, P.P0, RY0, P.P1, RY1, false);  // Z = A^T Q = B^T (FP64)
+  if (zip)  // Z = A^T Q = B^T (FP64)
+    cta_zipup(P, c, A0, 1, P.P0, RY0, P.P1, RY1, P.tol, P.max_rank, false);
+  else
+    cta_contract(P, c, A0, 1, P.P0, RY0, P.P1, RY1, false);
   if (failed(P)) return;
-  cta_mpo_svd(P, c, P.P1, RY1);
+  cta_mpo_svd(P, c, P.P1, RY1, zip);
   if (failed(P)) return;
   // U^(1) = Q^(1) x_3 W[:, :k] (Section 5.4); cores 2..d of U and V are those of Q and Z
   const int I1 = P.I[0], t = RY0[1], kout = P.k;
@@ -550,7 +686,7 @@ __device__ void cta_solve(BatchProblem &P, const Ctx &c) {
 }
 
 // Persistent kernel: each CTA takes problems from the queue until it is empty.
-__global__ void __launch_bounds__(kBT) k_batch_solve(BatchProblem *probs, int n, int *queue, int64_t smcap) {
+__global__ void __launch_bounds__(kBT, 2) k_batch_solve(BatchProblem *probs, int n, int *queue, int64_t smcap) {
   extern __shared__ double sm[];
   __shared__ double red[8 * kStepWarps];
   __shared__ double sc[8];
@@ -590,9 +726,50 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
   if (!pr.A || !pr.U || !pr.V || !pr.S || pr.k < 1 || pr.p < 0 || pr.q < 0) return TNR_EINVAL;
   if (pr.A->dtype != TNR_F64) return TNR_EINVAL;  // the kernel reads float64 cores
   if (pr.opts.precision != TNR_FP64 && pr.opts.precision != TNR_MIXED) return TNR_EINVAL;
+  if (pr.opts.rounding != TNR_ROUND_TWO_SWEEP && pr.opts.rounding != TNR_ROUND_ZIPUP) return TNR_EINVAL;
+  const bool zip = pr.opts.rounding == TNR_ROUND_ZIPUP;
+  const bool mixed = pr.opts.precision == TNR_MIXED;
   const int64_t K = (int64_t)pr.k + pr.p;
   Plan P;
   TNR_TRY(make_plan(pr.A, K, &pr.opts, P));
+  // Zip-up: no product core is formed. Bond k of a rounded product holds at most
+  // zq[k] = min(R_k sq_k, X_k zq[k+1], max_rank) (rows of T_k, columns of T_k, the cap), and
+  // every core the solve keeps (Y, Q, Z, V) fits zq[k] X_k K_k zq[k+1].
+  int64_t zq[TNR_MAX_SITES + 1];
+  int64_t zc_cap = 1, zw_cap = 1, zt_cap = 1, zf_cap = 1, zsvd = 1;
+  if (zip) {
+    zq[0] = 1;
+    zq[P.d] = 1;
+    for (int k = P.d - 1; k >= 1; --k) {
+      const int64_t X = std::max(P.I[k], P.J[k]);
+      int64_t v = std::min(P.RA[k] * P.sq[k], X * zq[k + 1]);
+      if (pr.opts.max_rank > 0) v = std::min<int64_t>(v, pr.opts.max_rank);
+      zq[k] = std::max<int64_t>(v, 1);
+    }
+    for (int k = 0; k < P.d; ++k) {
+      const int64_t X = std::max(P.I[k], P.J[k]), Kx = k == 0 ? K : 1;
+      const int64_t S = k == 0 ? 1 : P.sq[k], S2 = P.sq[k + 1], R = P.RA[k], R2 = P.RA[k + 1];
+      const int64_t t = zq[k + 1], rows = R * S, w = X * Kx * t;
+      P.pcap[k] = zq[k] * X * Kx * zq[k + 1];
+      zw_cap = std::max(zw_cap, S * Kx * R2 * t);
+      if (k >= 1) {
+        zt_cap = std::max(zt_cap, rows * w);
+        zc_cap = std::max(zc_cap, rows * zq[k]);
+        if (std::min(rows, w) > kStepMaxN) return TNR_ENOMEM;  // one-CTA SVD step limit
+        zsvd = std::max(zsvd, svd_step_work(rows, w));
+      }
+      if (mixed) zf_cap = std::max(zf_cap, R * P.I[k] * P.J[k] * R2 + S * X * Kx * S2 + R2 * S2 * t + S * Kx * R2 * t);
+    }
+    // the rounding sweeps, site-1 steps and outputs then run on bonds of at most zq
+    P.L.maxcore = 1;
+    P.L.maxbond = 1;
+    for (int k = 0; k < P.d; ++k) {
+      P.L.maxcore = std::max(P.L.maxcore, P.pcap[k]);
+      P.L.maxbond = std::max(P.L.maxbond, std::max(zq[k], zq[k + 1]));
+    }
+    P.L.maxcore = std::max(P.L.maxcore, std::max(P.I[0], P.J[0]) * K * zq[1]);
+    for (int k = 0; k <= P.d; ++k) P.sq[k] = std::min(P.sq[k], zq[k]);  // bonds of every rounded MPO
+  }
   if (pr.U->d != P.d || pr.V->d != P.d) return TNR_EINVAL;
   const tnr_mpo &A = *pr.A;
   // every index the kernel forms is a 32-bit int
@@ -602,10 +779,10 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
   for (int k = 0; k < P.d; ++k)
     if (P.pcap[k] > kIntMax) return TNR_ERANGE;
   // work area bound (doubles): every factorisation's need at the structural bounds
-  int64_t wc = 1;
+  int64_t wc = zip ? zsvd : 1;
   for (int k = 0; k < P.d; ++k) {
     const int64_t X = std::max(P.I[k], P.J[k]), Kx = k == 0 ? K : 1;
-    const int64_t t = P.RA[k] * P.sq[k], t2 = P.RA[k + 1] * P.sq[k + 1];
+    const int64_t t = zip ? zq[k] : P.RA[k] * P.sq[k], t2 = zip ? zq[k + 1] : P.RA[k + 1] * P.sq[k + 1];
     if (k + 1 < P.d) {
       const int64_t rows = t * X * Kx;
       wc = std::max(wc, rows * t2 + std::min(rows, t2));  // L->R QR
@@ -617,11 +794,12 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
     }
   }
   {
-    const int64_t X0 = std::max(P.I[0], P.J[0]), t1 = P.RA[1] * P.sq[1];
+    const int64_t X0 = std::max(P.I[0], P.J[0]), t1 = zip ? zq[1] : P.RA[1] * P.sq[1];
     wc = std::max(wc, X0 * t1 * K + K + 2 * K * K + 2 * K + jacobi_mixed_work(K));  // site-1 QR, K x K SVD
-    wc = std::max(wc, P.I[0] * P.J[0] * P.RA[1] + X0 * K * t1);  // BF16 x3 operands (floats)
+    wc = std::max(wc, (P.I[0] * P.J[0] * P.RA[1] + X0 * K * P.sq[1] + 1) / 2);  // FP32 operands of site 1
   }
-  if (wc > kIntMax || P.L.maxcore > kIntMax) return TNR_ERANGE;
+  if (wc > kIntMax || P.L.maxcore > kIntMax || zt_cap > kIntMax || zw_cap > kIntMax || zf_cap > kIntMax)
+    return TNR_ERANGE;
   const int64_t gram_cap = std::max<int64_t>(1, (P.d - 1) * 1024);
   if (bp) {
     memset(bp, 0, sizeof(*bp));
@@ -631,7 +809,8 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
     bp->K = (int)K;
     bp->k = pr.k;
     bp->q = pr.q;
-    bp->mixed = pr.opts.precision == TNR_MIXED ? 1 : 0;
+    bp->mixed = mixed ? 1 : 0;
+    bp->zip = zip ? 1 : 0;
     bp->status = 0;
     bp->seed = pr.seed;
     bp->tol = pr.opts.tol;
@@ -675,6 +854,26 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
   double *gram = ar.take<double>(gram_cap);
   double *Rm = ar.take<double>(K * K), *W = ar.take<double>(K * K), *Zr = ar.take<double>(K * K);
   double *Sv = ar.take<double>(K);
+  double *zc0 = nullptr, *zc1 = nullptr, *zw = nullptr, *zt = nullptr;
+  float *zf = nullptr;
+  if (zip) {
+    zc0 = ar.take<double>(zc_cap);
+    zc1 = ar.take<double>(zc_cap);
+    zw = ar.take<double>(zw_cap);
+    zt = ar.take<double>(zt_cap);
+    if (mixed) zf = ar.take<float>(zf_cap);
+  }
+  if (bp) {
+    bp->zc[0] = zc0;
+    bp->zc[1] = zc1;
+    bp->zw = zw;
+    bp->zt = zt;
+    bp->zf = zf;
+    bp->zc_cap = zc_cap;
+    bp->zw_cap = zw_cap;
+    bp->zt_cap = zt_cap;
+    bp->zf_cap = mixed ? zf_cap : 0;
+  }
   if (bp) {
     bp->merged = merged;
     bp->merge_tmp = merge_tmp;
@@ -695,7 +894,17 @@ int plan_problem(const tnr_problem &pr, Arena &ar, BatchProblem *bp, double *cos
   }
   if (cost) {
     double c = 0.0;
-    for (int k = 0; k < P.d; ++k) c += (double)P.pcap[k];
+    if (zip) {  // per product: the two contraction stages and the SVD step of every site
+      for (int k = 1; k < P.d; ++k) {
+        const double X = (double)std::max(P.I[k], P.J[k]), rows = (double)P.RA[k] * P.sq[k], w = X * zq[k + 1];
+        const double n = std::min(rows, w);
+        c += 2.0 * X * (double)P.sq[k] * P.RA[k + 1] * zq[k + 1] * P.sq[k + 1] + 2.0 * rows * w * X * P.RA[k + 1] +
+             2.0 * std::max(rows, w) * n * n;
+      }
+      c += 2.0 * (double)std::max(P.I[0], P.J[0]) * K * P.RA[1] * zq[1] * (P.sq[1] + P.I[0]);
+    } else {
+      for (int k = 0; k < P.d; ++k) c += (double)P.pcap[k];
+    }
     *cost = c * (2.0 * pr.q + 2.0);
   }
   if (bucket) *bucket = pow2_ceil(P.L.maxbond) * 4096 + pow2_ceil(std::max(P.I[0], P.J[0])) * 64 + pow2_ceil(K);

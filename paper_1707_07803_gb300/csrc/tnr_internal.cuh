@@ -119,6 +119,9 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 // FP64 products: min(64 eps, tol / 100). BF16 x3 products carry about 2^-16 relative error per
 // term, so their noise directions are dropped at 0.05 tol (tol is then at least kMixedTol).
 constexpr double kMixedTol = 1.2e-4;
+// The persistent batch's products use FP32 operands (about 2^-24 relative per term, ~1e-7 noise in
+// a product): its power iteration is rounded at max(tol, kMixedTolF32), an order above that noise.
+constexpr double kMixedTolF32 = 1e-6;
 __host__ __device__ inline double compress_cut(double tol, bool mixed_product) {
   if (mixed_product) return 0.05 * tol;
   const double a = 64.0 * 2.220446049250313e-16, b = 0.01 * tol;

@@ -574,6 +574,8 @@ int64_t tall_bound(const int64_t *dims, int d, int64_t K, int b) {
 int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
   TNR_TRY(validate_input(A, true));
   if (K < 1) return TNR_EINVAL;
+  if (o && o->rounding != TNR_ROUND_TWO_SWEEP && o->rounding != TNR_ROUND_ZIPUP) return TNR_EINVAL;
+  const bool zip = o && o->rounding == TNR_ROUND_ZIPUP;
   double pi = 1, pj = 1;
   int m = 0;
   for (int k = 0; k < A->d; ++k) {
@@ -614,7 +616,8 @@ int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
     const int64_t Kx = k == 0 ? K : 1;
     const int64_t b0 = P.RA[k] * P.sq[k], b1 = P.RA[k + 1] * P.sq[k + 1];
     const double cap = (double)b0 * (double)X * (double)Kx * (double)b1;
-    if (cap > 2e9) return TNR_ENOMEM;  // product core over 16 GB: outside the supported sizes
+    // product core over 16 GB: outside the supported sizes (a zip-up rounding never forms it)
+    if (cap > 2e9 && !zip) return TNR_ENOMEM;
     P.pcap[k] = (int64_t)cap;
     P.L.maxcore = std::max(P.L.maxcore, P.pcap[k]);
     P.L.maxbond = std::max(P.L.maxbond, std::max(b0, b1));
@@ -628,7 +631,7 @@ int make_plan(const tnr_mpo *A, int64_t K, const tnr_opts *o, Plan &P) {
     P.L.maxsq = std::max(P.L.maxsq, std::min(t, w));
   }
   P.L.maxcore = std::max(P.L.maxcore, std::max(P.I[0], P.J[0]) * K * P.L.maxbond);
-  if (P.L.maxsq > 1024) return TNR_ENOMEM;  // Jacobi kernel limit
+  if (P.L.maxsq > 1024 && !zip) return TNR_ENOMEM;  // Jacobi kernel limit (zip-up: checked per plan)
   P.omega_len = P.J[0] * K;
   for (int k = 1; k < P.d; ++k) P.omega_len += P.J[k];
   P.merged_elems = 0;
@@ -726,6 +729,7 @@ int solve_impl(cudaStream_t s, const tnr_mpo *A, int32_t k, int32_t p, int32_t q
                tnr_mpo *U, double *S, tnr_mpo *V, void *ws, size_t ws_bytes) {
   if (k < 1 || p < 0 || q < 0 || !U || !V || !S || !o) return TNR_EINVAL;
   if (o->precision != TNR_FP64 && o->precision != TNR_MIXED) return TNR_EINVAL;
+  if (o->rounding != TNR_ROUND_TWO_SWEEP) return TNR_EINVAL;  // zip-up: persistent batch only
   const int64_t K = (int64_t)k + p;
   Plan P;
   TNR_TRY(make_plan(A, K, o, P));
@@ -895,6 +899,7 @@ extern "C" int tnr_orthogonalize_workspace(const tnr_mpo *Y, size_t *bytes) {
 extern "C" int tnr_orthogonalize(tnr_mpo *Y, double *R_KxK, const tnr_opts *opts, void *ws, size_t ws_bytes,
                                  void *stream) {
   Limits L;
+  if (opts && opts->rounding != TNR_ROUND_TWO_SWEEP) return TNR_EINVAL;
   TNR_TRY(orth_limits(Y, L));
   for (int k = 1; k < Y->d; ++k)
     if (Y->J[k] != 1) return TNR_EINVAL;
@@ -919,10 +924,14 @@ extern "C" int tnr_solve_query(const tnr_mpo *A, int32_t k, int32_t p, const tnr
   const int64_t K = (int64_t)k + p;
   Plan P;
   TNR_TRY(make_plan(A, K, opts, P));
-  Arena ar;
-  SolveBufs sb;
-  carve_solve(ar, P, K, sb, A);
-  if (ws_bytes) *ws_bytes = ar.off;
+  if (opts->rounding == TNR_ROUND_TWO_SWEEP) {
+    Arena ar;
+    SolveBufs sb;
+    carve_solve(ar, P, K, sb, A);
+    if (ws_bytes) *ws_bytes = ar.off;
+  } else if (ws_bytes) {
+    *ws_bytes = 0;  // zip-up runs in the persistent batch, whose workspace tnr_batch_workspace gives
+  }
   for (tnr_mpo *M : {U_shape, V_shape}) {
     if (!M) continue;
     const bool isU = M == U_shape;

@@ -19,6 +19,8 @@ MAX_SITES = 64
 
 TNR_FP64 = 0
 TNR_MIXED = 1
+TNR_ROUND_TWO_SWEEP = 0
+TNR_ROUND_ZIPUP = 1
 
 _STATUS = {
     0: "ok", -1: "EINVAL", -2: "EDUP", -3: "ENOTSORTED", -4: "ENONFINITE", -5: "ENOMEM", -6: "ECUDA",
@@ -47,7 +49,7 @@ class tnr_mpo(ctypes.Structure):
 class tnr_opts(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("rounding", ctypes.c_int32),
         ("tol", ctypes.c_double),
         ("max_rank", ctypes.c_int64),
     ]
@@ -326,9 +328,10 @@ def tnr_mpo_contract(A, trans, X, precision=TNR_FP64, stream=None):
     return Y
 
 
-def _opts(tol, max_rank, precision):
+def _opts(tol, max_rank, precision, rounding=TNR_ROUND_TWO_SWEEP):
     o = tnr_opts()
     o.precision = int(precision)
+    o.rounding = int(rounding)
     o.tol = float(tol)
     o.max_rank = int(max_rank)
     return o
@@ -407,7 +410,8 @@ def _batch_outputs(problems, precision):
     for pr in problems:
         sp = SolvePlan.__new__(SolvePlan)  # outputs only; the batch owns the workspace
         sp.k, sp.p = int(pr["k"]), int(pr["p"])
-        sp.opts = _opts(pr.get("tol", 0.0), pr.get("max_rank", 0), pr.get("precision", precision))
+        sp.opts = _opts(pr.get("tol", 0.0), pr.get("max_rank", 0), pr.get("precision", precision),
+                        pr.get("rounding", TNR_ROUND_TWO_SWEEP))
         sp.A = pr["A"]
         sp.sa = sp.A.to_struct()
         sp.us, sp.vs = tnr_mpo(), tnr_mpo()
@@ -442,7 +446,8 @@ class BatchPlan:
     one workspace slice per worker, sized by the largest problem of the batch."""
 
     def __init__(self, problems, workers=0, precision=TNR_MIXED):
-        """problems: list of dicts with keys A (Mpo), k, p, q, seed and optional tol, max_rank."""
+        """problems: list of dicts with keys A (Mpo), k, p, q, seed and optional tol, max_rank,
+        precision and rounding (TNR_ROUND_ZIPUP is accepted by the persistent batch only)."""
         n = len(problems)
         self.n = n
         self.workers = int(workers) if workers else min(max(n, 1), 16)

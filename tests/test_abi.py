@@ -144,3 +144,36 @@ def test_noalloc_binding_checks_buffers_before_the_call():
                                     torch.zeros(16, dtype=torch.uint8), max_blocks=8)
     with pytest.raises(ValueError, match="max_blocks"):
         T.tnr_sparse_to_mpo_noalloc(8, 8, rows, rows, vals, [2, 4], [2, 4], None, None, max_blocks=-1)
+
+
+def test_zipup_planning_reaches_the_stated_batched_shapes(lib):
+    """With the zip-up rounding the persistent batch plans problems of the stated batched sizes
+    (ranks to 32, K to 64, d to 20), whose full products (2048-wide bonds) the two-sweep plan
+    refuses; the single solve refuses the zip-up option (host-side checks only)."""
+    import ctypes
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    keep = []
+    shapes = [(20, 4, 32, 32), (20, 2, 32, 32), (8, 4, 4, 8), (14, 2, 17, 16)]
+    probs = (T.tnr_problem * len(shapes))()
+    for i, (d, x, r, k) in enumerate(shapes):
+        A, U, V = _host_problem(T, d, x, r, k, k)
+        keep += [A, U, V]
+        P = probs[i]
+        P.A, P.U, P.V = ctypes.pointer(A), ctypes.pointer(U), ctypes.pointer(V)
+        P.k, P.p, P.q, P.seed = k, k, 1, i
+        P.S = 1 << 20
+        P.opts = T._opts(1e-12, 2 * k, T.TNR_MIXED, T.TNR_ROUND_ZIPUP)
+    b = ctypes.c_size_t(0)
+    assert lib.tnr_batch_workspace(len(shapes), probs, ctypes.byref(b)) == 0
+    assert 0 < b.value < (1 << 30)  # well under a GB for these four problems
+    two = T._opts(1e-12, 64, T.TNR_MIXED)
+    probs[0].opts = two
+    assert lib.tnr_batch_workspace(1, probs, ctypes.byref(b)) == -5  # two-sweep: products too wide
+    probs[0].opts = T._opts(1e-12, 64, T.TNR_MIXED, 7)
+    assert lib.tnr_batch_workspace(1, probs, ctypes.byref(b)) == -1  # unknown rounding
+    zo = T._opts(1e-12, 64, T.TNR_FP64, T.TNR_ROUND_ZIPUP)
+    S = ctypes.c_void_p(1 << 20)
+    assert lib.tnr_solve(probs[2].A, 8, 8, 1, 0, ctypes.byref(zo), probs[2].U, S, probs[2].V, ctypes.c_void_p(1 << 20),
+                         1 << 20, None) == -1

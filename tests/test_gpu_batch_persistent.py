@@ -21,9 +21,10 @@ from tests.gpu_util import dev_mpo, host_cores, sv_rel_err
 pytestmark = pytest.mark.gpu
 
 FP64_SV_TOL = 1e-10
-# Mixed precision on flat Gaussian spectra: first-order bound of the BF16 x3 products' noise and
-# the power-iteration rounding at tol_p = 1.2e-4 (the same gate as the worker-pool batch tests).
-MIXED_SV_TOL_FLAT = 1e-4
+# Mixed precision: the persistent batch's products use FP32 operands (about 2^-24 relative per
+# term) and its power iteration is rounded at max(tol, 1e-6); the relative singular-value error
+# against the FP64 oracle is held to the mixed-mode gate, 1e-6.
+MIXED_SV_TOL = 1e-6
 
 
 def _problems(seed, n, precision, d_range=(4, 7), rank_range=(2, 5), ks=(2, 4), q=1, tol=1e-13):
@@ -62,7 +63,7 @@ def test_persistent_batch_matches_oracle(precision):
     assert pb.statuses() == [0] * len(probs)
     cfg = pb.config()
     assert 1 <= cfg["ctas_per_sm"] <= 4 and 1 <= cfg["grid"] <= len(probs) and cfg["smem_bytes"] >= 16384
-    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL_FLAT
+    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL
     for i, pr in enumerate(probs):
         Uh, S, Vh = _host(pb, i)
         _check_against_oracle(pr, Uh, S, Vh, tol, check_ranks=precision == T.TNR_FP64)

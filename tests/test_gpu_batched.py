@@ -14,12 +14,10 @@ from tests.gpu_util import dev_mpo, sv_rel_err
 pytestmark = pytest.mark.gpu
 
 FP64_SV_TOL = 1e-10
-# Mixed precision on Gaussian-core inputs: the BF16 x3 products (relative error ~2^-16) and the
-# power-iteration rounding at tol_p = 1.2e-4 move Q's subspace by up to ~1e-4, and with a flat
-# spectrum and small oversampling the Ritz values sigma(Q^T A) move to first order with it. The
-# 1e-6 mixed gate holds where the sketch captures the dominant subspace (decaying spectra, the
-# prescribed-sigma workload: 1e-11 measured); on these batches the gate is the first-order bound.
-MIXED_SV_TOL_FLAT = 1e-4
+# Mixed precision (the single solve's kernels: BF16 x3 products, about 2^-16 relative per term,
+# FP32 accumulation; power iteration rounded at max(tol, 1.2e-4)): held to the mixed-mode gate of
+# 1e-6 relative singular-value error against the FP64 oracle.
+MIXED_SV_TOL = 1e-6
 
 
 def _problems(seed, n, precision):
@@ -36,7 +34,7 @@ def test_batch_matches_single_solves_and_oracle(precision, workers):
     plan.run()
     torch.cuda.synchronize()
     assert plan.statuses() == [0] * len(probs)
-    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL_FLAT
+    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL
     for i, pr in enumerate(probs):
         _, S_b, _ = plan.outputs(i)
         S_b = S_b.cpu().numpy()

@@ -1,0 +1,105 @@
+"""Persistent batched TNrSVD with the zip-up rounding (TNR_ROUND_ZIPUP) against the zip-up oracle.
+
+Every product of the power iteration and B = Q^T A is rounded while it is formed, right to left
+(oracle.rounding.zipup_product), then orthogonalised as in Alg. 5.2 / Alg. 5.3. Checked: singular
+values (FP64 1e-10, mixed 1e-6, relative Frobenius error) and ranks against the oracle's zip-up
+TNrSVD, orthonormal U and V with U^T A V = diag(S), on small batches where the rank cap binds and
+on problems drawn from the stated batched distribution (d 8-20, I = J in {2, 4}, ranks 4-32,
+k in {8, 16, 32}, p = k, q = 1, max_rank = K).
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mpo as om
+from oracle import rounding as orr
+from oracle import tnrsvd as ot
+from paper_1707_07803_gb300 import tnrsvd as T
+from tests.gpu_util import dev_mpo, host_cores, sv_rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_SV_TOL = 1e-10
+MIXED_SV_TOL = 1e-6
+
+
+def _problems(seed, n, precision, d_range, rank_range, ks, tol=1e-12):
+    probs = W.batched_gaussian(seed, n, d_range=d_range, phys=(2, 4), rank_range=rank_range, ks=ks, q=1, tol=tol)
+    return [dict(pr, A=dev_mpo(pr["A"]), A_host=pr["A"], precision=precision, rounding=T.TNR_ROUND_ZIPUP)
+            for pr in probs]
+
+
+def _check(pr, pb, i, sv_tol, check_ranks):
+    U, S, V = pb.outputs(i)
+    Uh, Vh, S = host_cores(U), host_cores(V), S.cpu().numpy().copy()
+    Uo, So, Vo = ot.tnrsvd(pr["A_host"], pr["k"], pr["p"], pr["q"], pr["seed"], tol=pr["tol"],
+                           max_rank=pr["max_rank"], rounding_mode="zipup")
+    err = sv_rel_err(S, So)
+    assert err <= sv_tol, (i, err, S, So)
+    if check_ranks:
+        assert orr.ranks(Uh) == orr.ranks(Uo) and orr.ranks(Vh) == orr.ranks(Vo), i
+    k = pr["k"]
+    np.testing.assert_allclose(om.inner(Uh, Uh), np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(om.inner(Vh, Vh), np.eye(k), atol=1e-12)
+    m = om.merge_count(*om.dims(pr["A_host"])[:2], k + pr["p"])
+    Am = om.merge_leading(pr["A_host"], m) if m > 1 else pr["A_host"]
+    np.testing.assert_allclose(om.sandwich(Uh, Am, Vh), np.diag(S), atol=1e-9 * S[0])
+    return err
+
+
+@pytest.mark.parametrize("precision", [T.TNR_FP64, T.TNR_MIXED])
+def test_zipup_batch_small_rank_cap_binds(precision):
+    """Ranks 3-8 with K = 4 or 8: the products' bonds (up to 64 wide) are cut to K by the zip-up."""
+    probs = _problems(81, 10, precision, d_range=(4, 7), rank_range=(3, 8), ks=(2, 4))
+    pb = T.PersistentBatch(probs, precision=precision, autotune=False, graph=True)
+    pb.launch()
+    assert pb.collect() == 0
+    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL
+    for i, pr in enumerate(probs):
+        _check(pr, pb, i, tol, check_ranks=precision == T.TNR_FP64)
+    pb.close()
+
+
+def _stated(n_pick, precision, seed, with_costliest):
+    """Problems of the stated batched distribution: the n_pick cheapest of 16 draws (the oracle runs
+    them on the CPU), and with_costliest: also the costliest of the same draws (k = 32, K = 64,
+    2048-wide product bonds; its FP32 products keep it to seconds on one SM)."""
+    probs = W.batched_gaussian(seed, 16, d_range=(8, 20), phys=(2, 4), rank_range=(4, 32), ks=(8, 16, 32), q=1,
+                               tol=1e-12)
+    cost = [sum(c.size for c in pr["A"]) * (pr["k"] ** 2) for pr in probs]
+    order = np.argsort(cost)
+    pick = [probs[i] for i in order[:n_pick]] + ([probs[order[-1]]] if with_costliest else [])
+    return [dict(pr, A=dev_mpo(pr["A"]), A_host=pr["A"], precision=precision, rounding=T.TNR_ROUND_ZIPUP)
+            for pr in pick]
+
+
+@pytest.mark.parametrize("precision", [T.TNR_FP64, T.TNR_MIXED])
+def test_zipup_batch_stated_shapes_against_oracle(precision):
+    probs = _stated(5, precision, seed=3 + precision, with_costliest=precision == T.TNR_MIXED)
+    pb = T.PersistentBatch(probs, precision=precision, autotune=False, graph=False)
+    pb.launch()
+    assert pb.collect() == 0
+    assert pb.statuses() == [0] * len(probs)
+    tol = FP64_SV_TOL if precision == T.TNR_FP64 else MIXED_SV_TOL
+    for i, pr in enumerate(probs):
+        _check(pr, pb, i, tol, check_ranks=precision == T.TNR_FP64)
+    pb.close()
+
+
+def test_zipup_graph_replay_bit_identical_and_shared_vs_global_work_areas():
+    probs = _problems(91, 6, T.TNR_MIXED, d_range=(5, 8), rank_range=(4, 12), ks=(4, 8))
+    outs = []
+    for per_sm in (1, 2):
+        pb = T.PersistentBatch(probs, precision=T.TNR_MIXED, autotune=False, graph=True, ctas_per_sm=per_sm)
+        pb.launch()
+        assert pb.collect() == 0
+        first = [pb.outputs(i)[1].cpu().numpy().copy() for i in range(len(probs))]
+        pb.launch()
+        pb.launch()
+        assert pb.collect() == 0
+        again = [pb.outputs(i)[1].cpu().numpy().copy() for i in range(len(probs))]
+        assert all(np.array_equal(a, b) for a, b in zip(first, again))
+        outs.append(first)
+        pb.close()
+    assert all(np.array_equal(a, b) for a, b in zip(*outs))

@@ -129,6 +129,25 @@ int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t *ro
                     double *X, uint8_t *digits, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Dense cores of the Alg. 4.1 MPO from its block form (Section 4.1, Eq. (4.1): the sum of the
+ * rank-1 MPOs E^(d)_{i_d j_d} (x) ... (x) E^(2)_{i_2 j_2} (x) X_t, rank R at every bond by
+ * Lemma 4.2), for rounding the converted MPO (Section 4.2's example: a Kronecker product of
+ * three 2 x 2 matrices converts to rank 16 and rounds to rank 1; Section 6.1 rounds a converted
+ * MPO from rank 347 to 7). Core 1 (1 x I_1 x J_1 x R) holds the blocks (core(0, i1, j1, t) =
+ * X_t(i1, j1)); core k = 2..d-1 (R x I_k x J_k x R) is the bond-diagonal selection
+ * core(t, i, j, t) = [i = i_{t,k}][j = j_{t,k}]; core d (R x I_d x J_d x 1) likewise with the bond
+ * closed; with d = 1 the single core is the sum of the blocks. Inputs R, X, digits as written by
+ * tnr_sparse_fill (device). Output: A->core[k] (device) with room A->cap[k] elements each, set by
+ * the caller; the library sets A->d, dtype, I, J, R. Copy and integer work only (bit-exact).
+ * Asynchronous on `stream`; a digit outside its site's range is reported through the device
+ * status word (TNR_ERANGE at the next synchronising call). Errors: TNR_EINVAL (dims, pointers,
+ * R < 1), TNR_ENOMEM (a core capacity too small), TNR_ERANGE (I_1 J_1 > 4096 or R >= 2^31).
+ * Interior cores take R^2 I_k J_k doubles: this serves converted MPOs of modest rank.
+ * ------------------------------------------------------------------------------------- */
+int tnr_sparse_cores(int64_t R, const double *X, const uint8_t *digits, int32_t d, const int64_t *I,
+                     const int64_t *J, tnr_mpo *A, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Sparse -> MPO conversion that allocates nothing. The paper has no counterpart: this entry is
  * a service to callers of this library. It computes exactly what tnr_sparse_count followed by
  * tnr_sparse_fill computes, for callers that cannot call cudaMalloc or take memory from an

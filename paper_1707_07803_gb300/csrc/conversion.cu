@@ -23,6 +23,7 @@
 //                 scatter the entry's value into block t, digits from each first occurrence.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "tnr_internal.cuh"
@@ -423,6 +424,46 @@ extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Dense cores of the Alg. 4.1 MPO (Section 4.1: the sum of the rank-1 MPOs E_{i_d j_d} (x) ... (x)
+// E_{i_2 j_2} (x) X_t has rank R at every bond, Lemma 4.2). Site 1 holds the blocks themselves
+// (core (0, i1, j1, t) = X_t(i1, j1): the same memory as X); site k (2..d-1) is a bond-diagonal
+// selection, core (t, i, j, t) = [i = i_{t,k}][j = j_{t,k}]; site d is (t, i, j, 0) = [...]. The
+// cores are zeroed first, then one thread per (block, site) writes its single 1.0. For d = 1 the
+// one core is the sum of the blocks. Copy and integer work only: bit-exact.
+// ---------------------------------------------------------------------------------------------
+struct CoreSites {
+  double *core[TNR_MAX_SITES];
+  int32_t I[TNR_MAX_SITES], J[TNR_MAX_SITES];
+};
+
+__global__ void __launch_bounds__(256) k_block_units(const uint8_t *__restrict__ digits, int64_t R, int32_t d,
+                                                     const __grid_constant__ CoreSites S, int *status) {
+  const int64_t total = R * (d - 1);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx % R;
+    const int k = 1 + (int)(idx / R);
+    const int i = digits[t * 2 * (d - 1) + 2 * (k - 1)], j = digits[t * 2 * (d - 1) + 2 * (k - 1) + 1];
+    const int I = S.I[k], J = S.J[k];
+    if (i >= I || j >= J) {
+      set_status(status, TNR_ERANGE);
+      continue;
+    }
+    const int64_t r2 = k == d - 1 ? 0 : t;  // the last site closes the bond
+    S.core[k][t + R * (i + (int64_t)I * (j + (int64_t)J * r2))] = 1.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_block_sum(const double *__restrict__ X, int64_t R, int64_t bs,
+                                                   double *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bs; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t t = 0; t < R; ++t) acc += X[t * bs + e];  // blocks in order
+    out[e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Conversion without any device allocation (no counterpart in the paper).
 //
 // The scratch that tnr_sparse_count/fill take from the caller's workspace (one int32 prefix
@@ -509,4 +550,46 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   }
   TNR_CK(cudaGetLastError());
   return TNR_OK;
+}
+
+extern "C" int tnr_sparse_cores(int64_t R, const double *X, const uint8_t *digits, int32_t d, const int64_t *I,
+                                const int64_t *J, tnr_mpo *A, void *stream) {
+  if (!A || d < 1 || d > TNR_MAX_SITES || !I || !J || R < 1 || !X || (d > 1 && !digits)) return TNR_EINVAL;
+  for (int k = 0; k < d; ++k) {
+    if (I[k] < 1 || J[k] < 1 || (k > 0 && (I[k] > 256 || J[k] > 256))) return TNR_EINVAL;
+    if (!A->core[k]) return TNR_EINVAL;
+  }
+  const int64_t bs = I[0] * J[0];
+  if (bs > 4096 || R > (int64_t(1) << 31)) return TNR_ERANGE;
+  A->d = d;
+  A->dtype = TNR_F64;
+  A->R[0] = 1;
+  A->R[d] = 1;
+  for (int k = 1; k < d; ++k) A->R[k] = R;
+  for (int k = 0; k < d; ++k) {
+    A->I[k] = I[k];
+    A->J[k] = J[k];
+    const double need = (double)A->R[k] * (double)I[k] * (double)J[k] * (double)A->R[k + 1];
+    if (need > (double)A->cap[k]) return TNR_ENOMEM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  LaunchScope ls(K_CONV_FILL, s);
+  if (d == 1) {
+    k_block_sum<<<(unsigned)std::min<int64_t>(cdiv(bs, 256), 4096), 256, 0, s>>>(X, R, bs, A->core[0]);
+    return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
+  }
+  TNR_CK(cudaMemcpyAsync(A->core[0], X, sizeof(double) * R * bs, cudaMemcpyDeviceToDevice, s));
+  CoreSites S;
+  memset(&S, 0, sizeof(S));
+  for (int k = 1; k < d; ++k) {
+    const int64_t n = A->R[k] * I[k] * J[k] * A->R[k + 1];
+    TNR_CK(cudaMemsetAsync(A->core[k], 0, sizeof(double) * n, s));
+    S.core[k] = A->core[k];
+    S.I[k] = (int32_t)I[k];
+    S.J[k] = (int32_t)J[k];
+  }
+  const int64_t total = R * (d - 1);
+  k_block_units<<<(unsigned)std::min<int64_t>(cdiv(total, 256), 152 * 16), 256, 0, s>>>(digits, R, d, S,
+                                                                                      status_ptr());
+  return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }

@@ -89,6 +89,7 @@ _SIGS = {
                         [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _I64, _P, _P, _P, ctypes.c_size_t, _P]),
     "tnr_sparse_to_mpo_noalloc": (ctypes.c_int, [_I64, _I64, _I64, _P, _P, _P, _I32, _I64P, _I64P, _P, _P, _I64,
                                                   _I64P, _P]),
+    "tnr_sparse_cores": (ctypes.c_int, [_I64, _P, _P, _I32, _I64P, _I64P, _MPOP, _P]),
     "tnr_mpo_contract": (ctypes.c_int, [_MPOP, _I32, _MPOP, _MPOP, _I32, _P]),
     "tnr_orthogonalize_workspace": (ctypes.c_int, [_MPOP, _SZP]),
     "tnr_orthogonalize": (ctypes.c_int, [_MPOP, _P, _OPTP, _P, ctypes.c_size_t, _P]),
@@ -307,6 +308,40 @@ def tnr_sparse_to_mpo_noalloc(nrows, ncols, row, col, val, I, J, X, digits, max_
                                          _i64arr(I), _i64arr(J), _ptr(X), _ptr(digits), max_blocks,
                                          ctypes.byref(R), _stream(stream)), "tnr_sparse_to_mpo_noalloc")
     return R.value
+
+
+def tnr_sparse_cores(R, X, digits, I, J, stream=None):
+    """Dense cores (Mpo) of the Alg. 4.1 MPO from its block form (R, X, digits on the device)."""
+    lib = load()
+    d = len(I)
+    R = int(R)
+    ranks = [1] + [R] * (d - 1) + [1]
+    dev = X.device
+    cores = [torch.empty(max(ranks[k] * int(I[k]) * int(J[k]) * ranks[k + 1], 1), dtype=torch.float64, device=dev)
+             for k in range(d)]
+    A = Mpo(list(I), list(J), ranks, cores)
+    sa = A.to_struct()
+    _need_buffer(X, torch.float64, R * int(I[0]) * int(J[0]), "X")
+    if d > 1:
+        _need_buffer(digits, torch.uint8, R * 2 * (d - 1), "digits")
+    _check(lib.tnr_sparse_cores(R, _ptr(X), _ptr(digits), d, _i64arr(I), _i64arr(J), ctypes.byref(sa), _stream(stream)),
+           "tnr_sparse_cores")
+    A.R = [sa.R[k] for k in range(d + 1)]
+    return A
+
+
+def round_operator(A, tol=0.0, max_rank=0, stream=None):
+    """SVD-based rounding of an operator MPO (Section 3; Section 4.2's rounding of the converted MPO):
+    the cores viewed as a one-column tall MPO (rows (i_k, j_k) per site, K = 1) go through
+    tnr_orthogonalize (the sweeps of Section 5.4 with the truncation rule of tnr_opts), and the 1 x 1
+    factor R = ||A|| is put back on site 1. Returns the rounded Mpo (new buffers; A is unchanged)."""
+    d = A.d
+    cores = [c.clone() for c in A.cores]
+    Y = Mpo([A.I[k] * A.J[k] for k in range(d)], [1] * d, list(A.R), cores)
+    Q, Rf = tnr_orthogonalize(Y, tol=tol, max_rank=max_rank, stream=stream)
+    n0 = Q.R[0] * Q.I[0] * Q.R[1]
+    Q.cores[0][:n0].mul_(Rf.reshape(-1)[0])
+    return Mpo(list(A.I), list(A.J), list(Q.R), Q.cores)
 
 
 def tnr_mpo_contract(A, trans, X, precision=TNR_FP64, stream=None):

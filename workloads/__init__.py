@@ -196,3 +196,65 @@ def prescribed_bond_mpo(seed, n, spectra, g=1.0, site1_split=None, canonical="ri
         assert I1 * K == int(n[0])
         cores[0] = cores[0][0, :, 0, :].reshape(I1, K, r[1], order="F")[None].copy()
     return cores, s
+
+
+# Section 6.3's second experiment: N sites of 2 x 2, 50 prescribed singular values 0.5^k, random
+# orthogonal U and V, rank-50 approximation (K = 100, q = 1), the paper's rounding tolerance for
+# each N, and the first 7 sites merged (I_1 = 128 >= K).
+PAPER_SIGMA_TOLS = {10: 1e-5, 15: 1e-6, 20: 1e-8, 25: 1e-8, 30: 1e-9, 35: 1e-10, 40: 1e-11, 45: 1e-12, 50: 1e-13}
+
+
+def paper_prescribed(N, seed_u=0, seed_v=1, seed_omega=2, rank=5):
+    """2^N x 2^N MPO A = U diag(0.5^k) V^T (k < 50) in the merged layout (site 1: 128 = 2^7 rows,
+    sites 2..N-6: 2 x 2), U and V orthogonal MPOs of rank `rank` (A's ranks rank^2 = 25, the paper's
+    maximal rank); k = 50, p = 50, q = 1, tol from PAPER_SIGMA_TOLS."""
+    if N not in PAPER_SIGMA_TOLS:
+        raise ValueError("N must be one of 10, 15, ..., 50")
+    sigma = 0.5 ** np.arange(50)
+    A, U, V = prescribed_mpo(seed_u, seed_v, 128, [2] * (N - 7), 50, rank, sigma)
+    return dict(A=A, k=50, p=50, q=1, seed=seed_omega, tol=PAPER_SIGMA_TOLS[N], max_rank=0, sigma=sigma)
+
+
+def hilbert_submatrix(N):
+    """Dense H(:, 1:2^(N-1)) of the 2^N x 2^N Hilbert matrix, H(i, j) = 1 / (i + j - 1) (1-based)."""
+    i = np.arange(1, 2 ** N + 1, dtype=np.float64)[:, None]
+    j = np.arange(1, 2 ** (N - 1) + 1, dtype=np.float64)[None, :]
+    return 1.0 / (i + j - 1.0)
+
+
+def tt_svd_operator(D, I, J, tol):
+    """MPO of a dense matrix by successive truncated SVDs (the TT-SVD of the tensor-train
+    literature; an input builder for tests and benchmarks, not a step of the method). Row and column
+    multi-indices are column-major (first site fastest), as everywhere in this package; at each of
+    the d - 1 splits the smallest rank whose discarded squared singular values are at most
+    (tol ||D||_F)^2 / (d - 1) is kept. Returns the cores (R_k, I_k, J_k, R_{k+1})."""
+    d = len(I)
+    T = np.asarray(D, dtype=np.float64).reshape(list(I) + list(J), order="F")
+    # interleave to (i1, j1, i2, j2, ...): site k's physical pair adjacent
+    perm = [x for k in range(d) for x in (k, d + k)]
+    T = T.transpose(perm)
+    delta2 = (tol * np.linalg.norm(D)) ** 2 / max(d - 1, 1)
+    cores, r = [], 1
+    M = T.reshape(r * I[0] * J[0], -1, order="F")
+    for k in range(d - 1):
+        U, s, Vt = np.linalg.svd(M, full_matrices=False)
+        tail = np.concatenate([np.cumsum((s ** 2)[::-1])[::-1], [0.0]])
+        keep = next(c for c in range(1, len(s) + 1) if tail[c] <= delta2)
+        cores.append(U[:, :keep].reshape(r, I[k], J[k], keep, order="F"))
+        M = (s[:keep, None] * Vt[:keep]).reshape(keep * I[k + 1] * J[k + 1], -1, order="F")
+        r = keep
+    cores.append(M.reshape(r, I[d - 1], J[d - 1], 1, order="F"))
+    return cores
+
+
+def paper_hilbert(N, tol=1e-11, seed_omega=2):
+    """Section 6.3's first experiment, H(:, 1:2^(N-1)) with N row sites and N - 1 column sites of 2
+    (the last site has J = 1), as an MPO from tt_svd_operator (the paper used TT-cross with relative
+    error 1e-11); rank-16 approximation, K = 32, q = 2, rounding tolerance 1e-9 (5 sites merged).
+    For N <= 12 (a dense 4096 x 2048 matrix at most)."""
+    if N > 12:
+        raise ValueError("the dense TT-SVD construction is for N <= 12")
+    I = [2] * N
+    J = [2] * (N - 1) + [1]
+    D = hilbert_submatrix(N)
+    return dict(A=tt_svd_operator(D, I, J, tol), k=16, p=16, q=2, seed=seed_omega, tol=1e-9, max_rank=0, dense=D)

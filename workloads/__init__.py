@@ -207,12 +207,14 @@ PAPER_SIGMA_TOLS = {10: 1e-5, 15: 1e-6, 20: 1e-8, 25: 1e-8, 30: 1e-9, 35: 1e-10,
 def paper_prescribed(N, seed_u=0, seed_v=1, seed_omega=2, rank=5):
     """2^N x 2^N MPO A = U diag(0.5^k) V^T (k < 50) in the merged layout (site 1: 128 = 2^7 rows,
     sites 2..N-6: 2 x 2), U and V orthogonal MPOs of rank `rank` (A's ranks rank^2 = 25, the paper's
-    maximal rank); k = 50, p = 50, q = 1, tol from PAPER_SIGMA_TOLS."""
+    maximal rank); k = 50, p = 50, q = 1, tol from PAPER_SIGMA_TOLS. max_rank = 40 bounds the
+    buffers and never binds: range(A) lies in range(U) (and range(A^T) in range(V)), so every Q of
+    the iteration has bond ranks of at most `rank`."""
     if N not in PAPER_SIGMA_TOLS:
         raise ValueError("N must be one of 10, 15, ..., 50")
     sigma = 0.5 ** np.arange(50)
     A, U, V = prescribed_mpo(seed_u, seed_v, 128, [2] * (N - 7), 50, rank, sigma)
-    return dict(A=A, k=50, p=50, q=1, seed=seed_omega, tol=PAPER_SIGMA_TOLS[N], max_rank=0, sigma=sigma)
+    return dict(A=A, k=50, p=50, q=1, seed=seed_omega, tol=PAPER_SIGMA_TOLS[N], max_rank=40, sigma=sigma)
 
 
 def hilbert_submatrix(N):

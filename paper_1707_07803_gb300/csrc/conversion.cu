@@ -116,21 +116,37 @@ __device__ __forceinline__ int64_t segment_end(const int64_t *__restrict__ row, 
   return lo;
 }
 
+// Per entry: validation, first-occurrence flag of its block, tile-local exclusive scan of the flags.
+// An entry of row r > p I1 is the first of block (p, q) when no earlier row of block-row p holds a
+// column in [q J1, (q+1) J1). The tile's rows and columns are staged in shared memory, so that
+// test is a few binary searches in shared memory whenever the block-row's segment starts inside the
+// tile (a segment crossing the tile's start falls back to searches in global memory). seg (may be
+// null): seg[pp] = first entry of block-row pp, for pp < seg_len (seg[seg_len - 1] = nnz).
 __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
                                                       ConvDims D, int32_t *__restrict__ F_local,
-                                                      int32_t *__restrict__ tile_total, int *status) {
+                                                      int32_t *__restrict__ tile_total, int32_t *__restrict__ seg,
+                                                      int64_t seg_len, int *status) {
   __shared__ int32_t warp_sums[kTile / 32];
-  const int64_t e = (int64_t)blockIdx.x * kTile + threadIdx.x;
+  __shared__ int64_t s_row[kTile], s_col[kTile];
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  const int64_t e = base + threadIdx.x;
+  const int nloc = (int)(D.nnz - base < kTile ? D.nnz - base : kTile);
+  if (e < D.nnz) {
+    s_row[threadIdx.x] = __ldg(row + e);
+    s_col[threadIdx.x] = __ldg(col + e);
+  }
+  __syncthreads();
   int flag = 0;
   if (e < D.nnz) {
-    const int64_t r = __ldg(row + e), c = __ldg(col + e);
+    const int64_t r = s_row[threadIdx.x], c = s_col[threadIdx.x];
+    const int64_t rp = e == 0 ? -1 : (threadIdx.x > 0 ? s_row[threadIdx.x - 1] : __ldg(row + e - 1));
+    const int64_t cp = e == 0 ? -1 : (threadIdx.x > 0 ? s_col[threadIdx.x - 1] : __ldg(col + e - 1));
     bool ok = true;
     if (r < 0 || r >= D.nrows || c < 0 || c >= D.ncols) {
       set_status(status, TNR_ERANGE);
       ok = false;
     }
     if (e > 0) {
-      const int64_t rp = __ldg(row + e - 1), cp = __ldg(col + e - 1);
       if (rp > r || (rp == r && cp > c)) {
         set_status(status, TNR_ENOTSORTED);
         ok = false;
@@ -141,18 +157,50 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
     }
     if (ok) {
       const int64_t p = qdiv(r, D.I1), q = qdiv(c, D.J1);
-      bool first = true;
-      if (e > 0 && __ldg(row + e - 1) == r && qdiv(__ldg(col + e - 1), D.J1) == q) first = false;
-      if (first && r > p * D.I1) {
-        const int64_t s0 = segment_start(row, e, p * D.I1);
-        for (int64_t rr = p * D.I1; rr < r && first; ++rr) {
-          const int64_t x = lower_bound_rc(row, col, s0, e, rr, q * D.J1);
-          if (x < e && __ldg(row + x) == rr && __ldg(col + x) < (q + 1) * D.J1) first = false;
+      const int64_t r0 = p * D.I1, clo = q * D.J1, chi = (q + 1) * D.J1;
+      bool first = !(e > 0 && rp == r && qdiv(cp, D.J1) == q);
+      if (first && r > r0) {
+        // does block-row p start inside this tile?
+        const bool inside = s_row[0] >= r0 ? (base == 0 || __ldg(row + base - 1) < r0) : true;
+        if (inside) {
+          int lo = 0, hi = (int)threadIdx.x;  // first local index with row >= r0
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_row[mid] < r0)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          for (int64_t rr = r0; rr < r && first; ++rr) {
+            int a = lo, b = (int)threadIdx.x;  // first index in [lo, tid) with (row, col) >= (rr, clo)
+            while (a < b) {
+              const int mid = (a + b) >> 1;
+              if (s_row[mid] < rr || (s_row[mid] == rr && s_col[mid] < clo))
+                a = mid + 1;
+              else
+                b = mid;
+            }
+            if (a < (int)threadIdx.x && s_row[a] == rr && s_col[a] < chi) first = false;
+            lo = a;
+          }
+        } else {
+          const int64_t s0 = segment_start(row, e, r0);
+          for (int64_t rr = r0; rr < r && first; ++rr) {
+            const int64_t x = lower_bound_rc(row, col, s0, e, rr, clo);
+            if (x < e && __ldg(row + x) == rr && __ldg(col + x) < chi) first = false;
+          }
         }
       }
       flag = first ? 1 : 0;
+      if (seg) {  // starts of the block-rows between the previous entry's and this one's
+        const int64_t pprev = e == 0 ? -1 : qdiv(rp, D.I1);
+        for (int64_t pp = pprev + 1; pp <= p && pp < seg_len; ++pp) seg[pp] = (int32_t)e;
+        if (e == D.nnz - 1)
+          for (int64_t pp = p + 1; pp < seg_len; ++pp) seg[pp] = (int32_t)D.nnz;
+      }
     }
   }
+  (void)nloc;
   // CTA-wide exclusive scan of flag.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int incl = flag;
@@ -235,6 +283,13 @@ __device__ __forceinline__ void write_digits(const ConvDims &D, int64_t p, int64
   }
 }
 
+// Segments handled whole by k_fill_rows: at most two entries per lane, blocks within the warp's buffer.
+constexpr int kRowsMaxL = 64;
+constexpr int kRowsBuf = 512;  // doubles of shared buffer per warp (4 KB)
+__device__ __forceinline__ bool fill_rows_small(int64_t L, int64_t nb, int64_t bs) {
+  return L <= kRowsMaxL && nb * bs <= kRowsBuf;
+}
+
 // Warp-window fill. Warp w handles the 32 consecutive nonzeros [32w, 32w + 32). Lanes whose
 // entries share a block-row p form a run (entries are sorted, so runs are contiguous lanes and
 // found with a ballot). The block index of an entry is t = F(s0) + rank, rank = number of first
@@ -260,10 +315,13 @@ __global__ void __launch_bounds__(256) k_fill_w(const int64_t *__restrict__ row,
                                                 const double *__restrict__ val, ConvDims D,
                                                 const int32_t *__restrict__ F_local,
                                                 const int32_t *__restrict__ tile_off, double *__restrict__ X,
-                                                uint8_t *__restrict__ digits, int64_t R, int *status) {
+                                                uint8_t *__restrict__ digits, int64_t R,
+                                                const int32_t *__restrict__ seg, const int *__restrict__ big,
+                                                int *status) {
   const int lane = threadIdx.x & 31;
   const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane;  // window start
   if (e0 >= D.nnz) return;
+  if (big && *big == 0) return;  // k_fill_rows wrote every block-row
   const int64_t e = e0 + lane;
   const bool valid = e < D.nnz;
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
@@ -312,8 +370,79 @@ __global__ void __launch_bounds__(256) k_fill_w(const int64_t *__restrict__ row,
       set_status(status, TNR_ERANGE);
       return;
     }
+    if (seg && fill_rows_small(s1 - s0, F_at(F_local, tile_off, s1, D.nnz) - F_at(F_local, tile_off, s0, D.nnz),
+                               D.I1 * D.J1))
+      return;  // written by k_fill_rows
     X[t * D.I1 * D.J1 + (r - r0) + D.I1 * (c - q * D.J1)] = v;
     if (first) write_digits(D, p, q, t, digits);
+  }
+}
+
+// Block-row fill, one warp per block-row p with segment [seg[p], seg[p+1]). A short segment (at
+// most kRowsMaxL entries, its blocks at most kRowsBuf values) is assembled in the warp's shared
+// buffer (zeros, then each entry's value at its block's rank among the block-row's distinct
+// block-columns) and written out whole, block after block, with its digits; no block of X is
+// touched twice and every write covers whole sectors. A longer segment only has its blocks zeroed
+// here (coalesced) and raises *big; k_fill_w then scatters its values and digits.
+__global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+                                                   const double *__restrict__ val, ConvDims D,
+                                                   const int32_t *__restrict__ F_local,
+                                                   const int32_t *__restrict__ tile_off,
+                                                   const int32_t *__restrict__ seg, int64_t nbr,
+                                                   double *__restrict__ X, uint8_t *__restrict__ digits, int64_t R,
+                                                   int *big, int *status) {
+  __shared__ double s_buf[8][kRowsBuf];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  double *buf = s_buf[wl];
+  const int64_t bs = D.I1 * D.J1;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nbr;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t s0 = seg[p], s1 = seg[p + 1], L = s1 - s0;
+    if (L <= 0) continue;
+    const int64_t t0 = F_at(F_local, tile_off, s0, D.nnz);
+    const int64_t nb = F_at(F_local, tile_off, s1, D.nnz) - t0;
+    if (t0 < 0 || nb < 1 || t0 + nb > R) {
+      if (lane == 0) set_status(status, TNR_ERANGE);
+      continue;
+    }
+    if (!fill_rows_small(L, nb, bs)) {  // long segment: zero its blocks, k_fill_w scatters
+      for (int64_t i = lane; i < nb * bs; i += 32) X[t0 * bs + i] = 0.0;
+      if (lane == 0) atomicOr(big, 1);
+      continue;
+    }
+    const int64_t r0 = p * D.I1;
+    int64_t rr[2], qq[2];
+    double vv[2];
+    int ff[2];
+    bool have[2];
+    for (int h = 0; h < 2; ++h) {
+      const int64_t e = s0 + lane + 32 * h;
+      have[h] = e < s1;
+      rr[h] = have[h] ? __ldg(row + e) : 0;
+      const int64_t c = have[h] ? __ldg(col + e) : 0;
+      qq[h] = have[h] ? qdiv(c, D.J1) : 0;
+      vv[h] = have[h] ? __ldg(val + e) : 0.0;
+      ff[h] = have[h] ? (F_at(F_local, tile_off, e + 1, D.nnz) != F_at(F_local, tile_off, e, D.nnz)) : 0;
+      rr[h] = rr[h] - r0 + D.I1 * (c - qq[h] * D.J1);  // offset inside the block
+    }
+    // rank of each entry's block: distinct block-columns of the segment below its own
+    int64_t rank[2] = {0, 0};
+    for (int j = 0; j < (int)L; ++j) {
+      const int hj = j >> 5, lj = j & 31;
+      const int64_t qj = __shfl_sync(0xffffffffu, hj ? qq[1] : qq[0], lj);
+      const int fj = __shfl_sync(0xffffffffu, hj ? ff[1] : ff[0], lj);
+      for (int h = 0; h < 2; ++h)
+        if (fj && qj < qq[h]) ++rank[h];
+    }
+    for (int64_t i = lane; i < nb * bs; i += 32) buf[i] = 0.0;
+    __syncwarp();
+    for (int h = 0; h < 2; ++h)
+      if (have[h]) buf[rank[h] * bs + rr[h]] = vv[h];
+    __syncwarp();
+    for (int64_t i = lane; i < nb * bs; i += 32) X[t0 * bs + i] = buf[i];
+    for (int h = 0; h < 2; ++h)
+      if (have[h] && ff[h]) write_digits(D, p, qq[h], t0 + rank[h], digits);
+    __syncwarp();
   }
 }
 
@@ -346,6 +475,34 @@ size_t ws_bytes_for(int64_t nnz) {
   return ((size_t(nnz) * 4 + 255) & ~size_t(255)) + ((size_t(ntiles + 1) * 4 + 255) & ~size_t(255));
 }
 
+// Block-row segment starts (one int32 per block-row, plus the end) are kept when the number of
+// block-rows is modest next to nnz; then the fill writes whole blocks (k_fill_rows).
+int64_t seg_len_for(int64_t nrows, int64_t I1, int64_t nnz) {
+  const int64_t nbr = nrows / I1;
+  return nbr <= 4 * nnz + (int64_t(1) << 20) ? nbr + 1 : 0;
+}
+
+// Workspace of the two-phase conversion: F_local | tile offsets | segment starts | the long-segment flag.
+struct ConvWs {
+  int32_t *F_local, *tile_off, *seg;
+  int *big;
+  int64_t seg_len;
+};
+size_t conv_ws_bytes(int64_t nrows, int64_t I1, int64_t nnz) {
+  const int64_t sl = seg_len_for(nrows, I1, nnz);
+  return ws_bytes_for(nnz) + ((size_t(sl) * 4 + 255) & ~size_t(255)) + 256;
+}
+ConvWs conv_ws(void *ws, int64_t nrows, int64_t I1, int64_t nnz) {
+  ConvWs w;
+  char *b = static_cast<char *>(ws);
+  w.F_local = reinterpret_cast<int32_t *>(b);
+  w.tile_off = reinterpret_cast<int32_t *>(b + ((size_t(nnz) * 4 + 255) & ~size_t(255)));
+  w.seg_len = seg_len_for(nrows, I1, nnz);
+  w.seg = w.seg_len ? reinterpret_cast<int32_t *>(b + ws_bytes_for(nnz)) : nullptr;
+  w.big = reinterpret_cast<int *>(b + ws_bytes_for(nnz) + ((size_t(w.seg_len) * 4 + 255) & ~size_t(255)));
+  return w;
+}
+
 }  // namespace
 }  // namespace tnr
 
@@ -356,7 +513,7 @@ extern "C" int tnr_sparse_workspace(int64_t nrows, int64_t ncols, int64_t nnz, i
   ConvDims D;
   TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
   if (!bytes) return TNR_EINVAL;
-  *bytes = ws_bytes_for(nnz);
+  *bytes = conv_ws_bytes(nrows, I[0], nnz);
   return TNR_OK;
 }
 
@@ -372,14 +529,14 @@ extern "C" int tnr_sparse_count(int64_t nrows, int64_t ncols, int64_t nnz, const
     return TNR_OK;
   }
   if (!row || !col || !ws) return TNR_EINVAL;
-  if (ws_bytes < ws_bytes_for(nnz)) return TNR_ENOMEM;
+  if (ws_bytes < conv_ws_bytes(nrows, I[0], nnz)) return TNR_ENOMEM;
   const int64_t ntiles = cdiv(nnz, kTile);
-  int32_t *F_local = reinterpret_cast<int32_t *>(ws);
-  int32_t *tile_off = reinterpret_cast<int32_t *>((char *)ws + ((size_t(nnz) * 4 + 255) & ~size_t(255)));
+  const ConvWs W = conv_ws(ws, nrows, I[0], nnz);
+  int32_t *F_local = W.F_local, *tile_off = W.tile_off;
   TNR_TRY(reset_status(s));
   {
     LaunchScope ls(K_CONV_FLAGS, s);
-    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, status_ptr());
+    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, W.seg, W.seg_len, status_ptr());
   }
   TNR_CK(cudaGetLastError());
   {
@@ -402,13 +559,28 @@ extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const 
   TNR_TRY(make_dims(nrows, ncols, nnz, d, I, J, &D));
   if (nnz == 0 || R == 0) return TNR_OK;
   if (!row || !col || !val || !X || !ws || (d > 1 && !digits) || R < 0) return TNR_EINVAL;
-  if (ws_bytes < ws_bytes_for(nnz)) return TNR_ENOMEM;
+  if (ws_bytes < conv_ws_bytes(nrows, I[0], nnz)) return TNR_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
-  const int32_t *F_local = reinterpret_cast<const int32_t *>(ws);
-  const int32_t *tile_off =
-      reinterpret_cast<const int32_t *>((const char *)ws + ((size_t(nnz) * 4 + 255) & ~size_t(255)));
+  const ConvWs W = conv_ws(ws, nrows, I[0], nnz);
+  const int32_t *F_local = W.F_local, *tile_off = W.tile_off;
   // algorithmic bytes of the conversion: 24 B per nonzero read, values and digits written
   stats_work(K_CONV_FILL, 24.0 * (double)nnz + (double)R * (8.0 * (double)(I[0] * J[0]) + 2.0 * (d - 1)));
+  if (W.seg) {  // whole blocks per block-row; the scatter kernel only for long segments (if any)
+    const int64_t nbr = W.seg_len - 1;
+    TNR_CK(cudaMemsetAsync(W.big, 0, sizeof(int), s));
+    {
+      LaunchScope ls(K_CONV_FILL, s);
+      k_fill_rows<<<(unsigned)std::min<int64_t>(cdiv(nbr, 8), 152 * 64), 256, 0, s>>>(
+          row, col, val, D, F_local, tile_off, W.seg, nbr, X, digits, R, W.big, status_ptr());
+    }
+    {
+      LaunchScope ls(K_CONV_FILL, s);
+      k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R, W.seg,
+                                                         W.big, status_ptr());
+    }
+    TNR_CK(cudaGetLastError());
+    return TNR_OK;
+  }
   {
     LaunchScope ls(K_CONV_FILL, s);
     const int64_t nx = R * I[0] * J[0];
@@ -416,8 +588,8 @@ extern "C" int tnr_sparse_fill(int64_t nrows, int64_t ncols, int64_t nnz, const 
   }
   {
     LaunchScope ls(K_CONV_FILL, s);
-    k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R,
-                                                       status_ptr());
+    k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, R, nullptr,
+                                                       nullptr, status_ptr());
   }
   TNR_CK(cudaGetLastError());
   return TNR_OK;
@@ -524,7 +696,7 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   TNR_TRY(reset_status(s));
   {
     LaunchScope ls(K_CONV_FLAGS, s);
-    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, status_ptr());
+    k_first_scan<<<(unsigned)ntiles, kTile, 0, s>>>(row, col, D, F_local, tile_off, nullptr, 0, status_ptr());
   }
   TNR_CK(cudaGetLastError());
   {
@@ -546,7 +718,7 @@ extern "C" int tnr_sparse_to_mpo_noalloc(int64_t nrows, int64_t ncols, int64_t n
   {
     LaunchScope ls(K_CONV_FILL, s);
     k_fill_w<<<(unsigned)cdiv(nnz, 256), 256, 0, s>>>(row, col, val, D, F_local, tile_off, X, digits, total,
-                                                       status_ptr());
+                                                       nullptr, nullptr, status_ptr());
   }
   TNR_CK(cudaGetLastError());
   return TNR_OK;

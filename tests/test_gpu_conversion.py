@@ -105,3 +105,18 @@ def test_banded_2pow20_bit_exact():
     got = _gpu_convert(rows, cols, vals, n, n, I, J)
     assert want[0] > 5_000_000
     _assert_same(got, want)
+
+
+def test_short_and_long_block_rows_in_one_matrix():
+    """Block-rows assembled whole in shared memory (short segments) next to block-rows with more
+    than 64 entries or more block values than the warp's buffer (left to the scatter fill), in one
+    conversion; bit-exact against the oracle."""
+    rng = np.random.default_rng(12)
+    I, J = [4, 8, 8], [4, 8, 8]
+    n = 256
+    D = np.where(rng.random((n, n)) < 0.01, rng.standard_normal((n, n)), 0.0)
+    for r in (5, 6, 77, 200):  # dense rows: their block-rows have > 64 entries
+        D[r] = rng.standard_normal(n)
+    D[130:134, :] = np.where(rng.random((4, n)) < 0.3, 1.5, 0.0)  # many blocks (nb * 16 > 512)
+    rows, cols, vals = _coo(D)
+    _assert_same(_gpu_convert(rows, cols, vals, n, n, I, J), oc.convert(rows, cols, vals, n, n, I, J))

@@ -39,10 +39,10 @@ def test_prescribed_sigma_sweep_points(N):
 @pytest.mark.parametrize("N", [10, 12])
 def test_hilbert_submatrix(N):
     c = W.paper_hilbert(N)
-    _, S, _ = T.tnr_solve(dev_mpo(c["A"]), c["k"], c["p"], c["q"], c["seed"], tol=c["tol"], max_rank=0,
+    _, S, _ = T.tnr_solve(dev_mpo(c["A"]), c["k"], c["p"], c["q"], c["seed"], tol=c["tol"], max_rank=c["max_rank"],
                           precision=T.TNR_FP64)
     S = S.cpu().numpy()
-    _, So, _ = ot.tnrsvd(c["A"], c["k"], c["p"], c["q"], c["seed"], tol=c["tol"], max_rank=0)
+    _, So, _ = ot.tnrsvd(c["A"], c["k"], c["p"], c["q"], c["seed"], tol=c["tol"], max_rank=c["max_rank"])
     assert sv_rel_err(S, So) <= 1e-10
     s_true = np.linalg.svd(c["dense"], compute_uv=False)[: c["k"]]
     assert sv_rel_err(S, s_true) <= 1e-8

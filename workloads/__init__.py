@@ -253,10 +253,11 @@ def paper_hilbert(N, tol=1e-11, seed_omega=2):
     """Section 6.3's first experiment, H(:, 1:2^(N-1)) with N row sites and N - 1 column sites of 2
     (the last site has J = 1), as an MPO from tt_svd_operator (the paper used TT-cross with relative
     error 1e-11); rank-16 approximation, K = 32, q = 2, rounding tolerance 1e-9 (5 sites merged).
-    For N <= 12 (a dense 4096 x 2048 matrix at most)."""
+    For N <= 12 (a dense 4096 x 2048 matrix at most). max_rank = 64 bounds the buffers and does not
+    bind (the rounded bonds stay below 40 at tolerance 1e-9)."""
     if N > 12:
         raise ValueError("the dense TT-SVD construction is for N <= 12")
     I = [2] * N
     J = [2] * (N - 1) + [1]
     D = hilbert_submatrix(N)
-    return dict(A=tt_svd_operator(D, I, J, tol), k=16, p=16, q=2, seed=seed_omega, tol=1e-9, max_rank=0, dense=D)
+    return dict(A=tt_svd_operator(D, I, J, tol), k=16, p=16, q=2, seed=seed_omega, tol=1e-9, max_rank=64, dense=D)

@@ -122,25 +122,32 @@ __device__ __forceinline__ int64_t segment_end(const int64_t *__restrict__ row, 
 // test is a few binary searches in shared memory whenever the block-row's segment starts inside the
 // tile (a segment crossing the tile's start falls back to searches in global memory). seg (may be
 // null): seg[pp] = first entry of block-row pp, for pp < seg_len (seg[seg_len - 1] = nnz).
+constexpr int kHalo = 128;  // entries before the tile staged with it (block-rows crossing the tile start)
+
 __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
                                                       ConvDims D, int32_t *__restrict__ F_local,
                                                       int32_t *__restrict__ tile_total, int32_t *__restrict__ seg,
                                                       int64_t seg_len, int *status) {
   __shared__ int32_t warp_sums[kTile / 32];
-  __shared__ int64_t s_row[kTile], s_col[kTile];
+  __shared__ int64_t s_row[kHalo + kTile], s_col[kHalo + kTile];
   const int64_t base = (int64_t)blockIdx.x * kTile;
   const int64_t e = base + threadIdx.x;
-  const int nloc = (int)(D.nnz - base < kTile ? D.nnz - base : kTile);
-  if (e < D.nnz) {
-    s_row[threadIdx.x] = __ldg(row + e);
-    s_col[threadIdx.x] = __ldg(col + e);
+  const int64_t hbase = base > kHalo ? base - kHalo : 0;  // first staged entry
+  const int hoff = (int)(base - hbase);                    // local index of entry `base`
+  for (int i = threadIdx.x; i < hoff + kTile; i += kTile) {
+    const int64_t x = hbase + i;
+    if (x < D.nnz) {
+      s_row[i] = __ldg(row + x);
+      s_col[i] = __ldg(col + x);
+    }
   }
   __syncthreads();
+  const int me = hoff + (int)threadIdx.x;  // local index of entry e
   int flag = 0;
   if (e < D.nnz) {
-    const int64_t r = s_row[threadIdx.x], c = s_col[threadIdx.x];
-    const int64_t rp = e == 0 ? -1 : (threadIdx.x > 0 ? s_row[threadIdx.x - 1] : __ldg(row + e - 1));
-    const int64_t cp = e == 0 ? -1 : (threadIdx.x > 0 ? s_col[threadIdx.x - 1] : __ldg(col + e - 1));
+    const int64_t r = s_row[me], c = s_col[me];
+    const int64_t rp = e == 0 ? -1 : s_row[me - 1];
+    const int64_t cp = e == 0 ? -1 : s_col[me - 1];
     bool ok = true;
     if (r < 0 || r >= D.nrows || c < 0 || c >= D.ncols) {
       set_status(status, TNR_ERANGE);
@@ -160,10 +167,27 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
       const int64_t r0 = p * D.I1, clo = q * D.J1, chi = (q + 1) * D.J1;
       bool first = !(e > 0 && rp == r && qdiv(cp, D.J1) == q);
       if (first && r > r0) {
-        // does block-row p start inside this tile?
-        const bool inside = s_row[0] >= r0 ? (base == 0 || __ldg(row + base - 1) < r0) : true;
+        // does block-row p start inside the staged range?
+        const bool inside = hbase == 0 || s_row[0] < r0;
+        // short block-row prefix: walk back over the earlier rows' entries (the same row's
+        // entries with the same block-column are adjacent, handled above)
+        int i = me - 1, steps = 0;
+        bool walked = false;
         if (inside) {
-          int lo = 0, hi = (int)threadIdx.x;  // first local index with row >= r0
+          while (i >= 0 && s_row[i] == r) --i;
+          for (; i >= 0 && steps < 96; --i, ++steps) {
+            if (s_row[i] < r0) break;
+            if (s_col[i] >= clo && s_col[i] < chi) {
+              first = false;
+              break;
+            }
+          }
+          walked = !first || i < 0 || s_row[i] < r0;
+        }
+        if (walked) {
+          // decided by the walk
+        } else if (inside) {
+          int lo = 0, hi = me;  // first local index with row >= r0
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (s_row[mid] < r0)
@@ -172,7 +196,7 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
               hi = mid;
           }
           for (int64_t rr = r0; rr < r && first; ++rr) {
-            int a = lo, b = (int)threadIdx.x;  // first index in [lo, tid) with (row, col) >= (rr, clo)
+            int a = lo, b = me;  // first index in [lo, me) with (row, col) >= (rr, clo)
             while (a < b) {
               const int mid = (a + b) >> 1;
               if (s_row[mid] < rr || (s_row[mid] == rr && s_col[mid] < clo))
@@ -180,7 +204,7 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
               else
                 b = mid;
             }
-            if (a < (int)threadIdx.x && s_row[a] == rr && s_col[a] < chi) first = false;
+            if (a < me && s_row[a] == rr && s_col[a] < chi) first = false;
             lo = a;
           }
         } else {
@@ -200,7 +224,6 @@ __global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict_
       }
     }
   }
-  (void)nloc;
   // CTA-wide exclusive scan of flag.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int incl = flag;
@@ -286,6 +309,7 @@ __device__ __forceinline__ void write_digits(const ConvDims &D, int64_t p, int64
 // Segments handled whole by k_fill_rows: at most two entries per lane, blocks within the warp's buffer.
 constexpr int kRowsMaxL = 64;
 constexpr int kRowsBuf = 512;  // doubles of shared buffer per warp (4 KB)
+constexpr int kRowsDig = 1024;  // bytes of digit staging per warp
 __device__ __forceinline__ bool fill_rows_small(int64_t L, int64_t nb, int64_t bs) {
   return L <= kRowsMaxL && nb * bs <= kRowsBuf;
 }
@@ -392,9 +416,11 @@ __global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ r
                                                    double *__restrict__ X, uint8_t *__restrict__ digits, int64_t R,
                                                    int *big, int *status) {
   __shared__ double s_buf[8][kRowsBuf];
+  __shared__ uint8_t s_dig[8][kRowsDig];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   double *buf = s_buf[wl];
   const int64_t bs = D.I1 * D.J1;
+  const int64_t nd = 2 * (int64_t)(D.d - 1);  // digit bytes per block
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nbr;
        p += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t s0 = seg[p], s1 = seg[p + 1], L = s1 - s0;
@@ -440,8 +466,15 @@ __global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ r
       if (have[h]) buf[rank[h] * bs + rr[h]] = vv[h];
     __syncwarp();
     for (int64_t i = lane; i < nb * bs; i += 32) X[t0 * bs + i] = buf[i];
-    for (int h = 0; h < 2; ++h)
-      if (have[h] && ff[h]) write_digits(D, p, qq[h], t0 + rank[h], digits);
+    if (nd > 0 && nb * nd <= kRowsDig) {  // the block-row's digit rows are contiguous: stage, then
+      for (int h = 0; h < 2; ++h)          // one run of consecutive byte stores
+        if (have[h] && ff[h]) write_digits(D, p, qq[h], rank[h], s_dig[wl]);
+      __syncwarp();
+      for (int64_t i = lane; i < nb * nd; i += 32) digits[t0 * nd + i] = s_dig[wl][i];
+    } else {
+      for (int h = 0; h < 2; ++h)
+        if (have[h] && ff[h]) write_digits(D, p, qq[h], t0 + rank[h], digits);
+    }
     __syncwarp();
   }
 }

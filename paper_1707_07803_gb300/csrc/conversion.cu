@@ -37,8 +37,10 @@ struct ConvDims {
   int64_t nrows, ncols, nnz;
   int64_t I1, J1;
   int32_t d;
+  int32_t narrow;  // block-row indices fit 31 bits and block-column indices 30 (radix strides too)
   int32_t I[TNR_MAX_SITES];
   int32_t J[TNR_MAX_SITES];
+  int32_t Is[TNR_MAX_SITES], Js[TNR_MAX_SITES];  // radix strides: prod of I_2..I_{k-1} (valid when narrow)
 };
 
 // Non-negative division that takes the 32-bit path whenever both operands fit (64-bit division
@@ -124,7 +126,7 @@ __device__ __forceinline__ int64_t segment_end(const int64_t *__restrict__ row, 
 // null): seg[pp] = first entry of block-row pp, for pp < seg_len (seg[seg_len - 1] = nnz).
 constexpr int kHalo = 128;  // entries before the tile staged with it (block-rows crossing the tile start)
 
-__global__ void __launch_bounds__(kTile) k_first_scan(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
+__global__ void __launch_bounds__(kTile, 2) k_first_scan(const int64_t *__restrict__ row, const int64_t *__restrict__ col,
                                                       ConvDims D, int32_t *__restrict__ F_local,
                                                       int32_t *__restrict__ tile_total, int32_t *__restrict__ seg,
                                                       int64_t seg_len, int *status) {
@@ -417,6 +419,7 @@ __global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ r
                                                    int *big, int *status) {
   __shared__ double s_buf[8][kRowsBuf];
   __shared__ uint8_t s_dig[8][kRowsDig];
+  __shared__ uint8_t s_pdig[8][TNR_MAX_SITES];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   double *buf = s_buf[wl];
   const int64_t bs = D.I1 * D.J1;
@@ -453,12 +456,26 @@ __global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ r
     }
     // rank of each entry's block: distinct block-columns of the segment below its own
     int64_t rank[2] = {0, 0};
-    for (int j = 0; j < (int)L; ++j) {
-      const int hj = j >> 5, lj = j & 31;
-      const int64_t qj = __shfl_sync(0xffffffffu, hj ? qq[1] : qq[0], lj);
-      const int fj = __shfl_sync(0xffffffffu, hj ? ff[1] : ff[0], lj);
-      for (int h = 0; h < 2; ++h)
-        if (fj && qj < qq[h]) ++rank[h];
+    if (D.narrow) {  // block columns and first flags packed in one 32-bit word (q < 2^31)
+      const int32_t w0 = ((int32_t)qq[0] << 1) | ff[0], w1 = ((int32_t)qq[1] << 1) | ff[1];
+      const int32_t m0 = (int32_t)qq[0] << 1, m1 = (int32_t)qq[1] << 1;
+      int r0c = 0, r1c = 0;
+      for (int j = 0; j < (int)L; ++j) {
+        const int32_t wj = __shfl_sync(0xffffffffu, (j >> 5) ? w1 : w0, j & 31);
+        // first occurrence (low bit) with a smaller block column
+        r0c += ((wj & 1) && wj < m0) ? 1 : 0;
+        r1c += ((wj & 1) && wj < m1) ? 1 : 0;
+      }
+      rank[0] = r0c;
+      rank[1] = r1c;
+    } else {
+      for (int j = 0; j < (int)L; ++j) {
+        const int hj = j >> 5, lj = j & 31;
+        const int64_t qj = __shfl_sync(0xffffffffu, hj ? qq[1] : qq[0], lj);
+        const int fj = __shfl_sync(0xffffffffu, hj ? ff[1] : ff[0], lj);
+        for (int h = 0; h < 2; ++h)
+          if (fj && qj < qq[h]) ++rank[h];
+      }
     }
     for (int64_t i = lane; i < nb * bs; i += 32) buf[i] = 0.0;
     __syncwarp();
@@ -467,10 +484,28 @@ __global__ void __launch_bounds__(256) k_fill_rows(const int64_t *__restrict__ r
     __syncwarp();
     for (int64_t i = lane; i < nb * bs; i += 32) X[t0 * bs + i] = buf[i];
     if (nd > 0 && nb * nd <= kRowsDig) {  // the block-row's digit rows are contiguous: stage, then
-      for (int h = 0; h < 2; ++h)          // one run of consecutive byte stores
-        if (have[h] && ff[h]) write_digits(D, p, qq[h], rank[h], s_dig[wl]);
+      uint8_t *dg = s_dig[wl];             // one run of consecutive byte stores
+      if (D.narrow) {
+        // digit k of p (shared by every block of the block-row) and of each block's q from the
+        // radix strides: independent 32-bit divisions instead of a dependent chain
+        const uint32_t p32 = (uint32_t)p;
+        for (int k = 1 + lane; k < D.d; k += 32) s_pdig[wl][k] = (uint8_t)((p32 / (uint32_t)D.Is[k]) % (uint32_t)D.I[k]);
+        __syncwarp();
+        for (int h = 0; h < 2; ++h) {
+          if (!(have[h] && ff[h])) continue;
+          const uint32_t q32 = (uint32_t)qq[h];
+          uint8_t *row_d = dg + rank[h] * nd;
+          for (int k = 1; k < D.d; ++k) {
+            row_d[2 * (k - 1)] = s_pdig[wl][k];
+            row_d[2 * (k - 1) + 1] = (uint8_t)((q32 / (uint32_t)D.Js[k]) % (uint32_t)D.J[k]);
+          }
+        }
+      } else {
+        for (int h = 0; h < 2; ++h)
+          if (have[h] && ff[h]) write_digits(D, p, qq[h], rank[h], dg);
+      }
       __syncwarp();
-      for (int64_t i = lane; i < nb * nd; i += 32) digits[t0 * nd + i] = s_dig[wl][i];
+      for (int64_t i = lane; i < nb * nd; i += 32) digits[t0 * nd + i] = dg[i];
     } else {
       for (int h = 0; h < 2; ++h)
         if (have[h] && ff[h]) write_digits(D, p, qq[h], t0 + rank[h], digits);
@@ -494,6 +529,18 @@ int make_dims(int64_t nrows, int64_t ncols, int64_t nnz, int32_t d, const int64_
   }
   if (pi != nrows || pj != ncols) return TNR_EINVAL;
   if (I[0] * J[0] > 4096) return TNR_EINVAL;
+  {
+    const int64_t lim = (int64_t(1) << 31) - 1;
+    // block rows below 2^31, block columns below 2^30 (the fill packs 2 q + flag in 32 bits)
+    D->narrow = (nrows / I[0] <= lim && ncols / J[0] <= (lim >> 1)) ? 1 : 0;
+    int64_t si = 1, sj = 1;
+    for (int k = 1; k < d; ++k) {
+      D->Is[k] = (int32_t)(si <= lim ? si : 0);
+      D->Js[k] = (int32_t)(sj <= lim ? sj : 0);
+      si *= I[k];
+      sj *= J[k];
+    }
+  }
   D->nrows = nrows;
   D->ncols = ncols;
   D->nnz = nnz;

@@ -120,3 +120,21 @@ def test_short_and_long_block_rows_in_one_matrix():
     D[130:134, :] = np.where(rng.random((4, n)) < 0.3, 1.5, 0.0)  # many blocks (nb * 16 > 512)
     rows, cols, vals = _coo(D)
     _assert_same(_gpu_convert(rows, cols, vals, n, n, I, J), oc.convert(rows, cols, vals, n, n, I, J))
+
+
+def test_wide_matrix_with_64_bit_block_columns():
+    """64 x 2^33 (sites 4 x 4, 4 x 256, 4 x 256, 1 x 256, 1 x 128): block columns beyond 2^30 take
+    the 64-bit rank and digit paths of the block-row fill; bit-exact against the oracle."""
+    rng = np.random.default_rng(21)
+    I, J = [4, 4, 4, 1, 1], [4, 256, 256, 256, 128]
+    nr, nc = 64, 1 << 33
+    rows, cols = [], []
+    for r in range(nr):
+        cs = np.unique(rng.integers(0, nc, size=10))
+        rows += [r] * cs.size
+        cols += list(cs)
+    rows = np.array(rows, dtype=np.int64)
+    cols = np.array(cols, dtype=np.int64)
+    vals = rng.standard_normal(rows.size)
+    vals[vals == 0.0] = 1.0
+    _assert_same(_gpu_convert(rows, cols, vals, nr, nc, I, J), oc.convert(rows, cols, vals, nr, nc, I, J))

@@ -130,7 +130,7 @@ def test_wide_matrix_with_64_bit_block_columns():
     nr, nc = 64, 1 << 33
     rows, cols = [], []
     for r in range(nr):
-        cs = np.unique(rng.integers(0, nc, size=10))
+        cs = np.unique(rng.integers(0, nc, size=7))  # 28 entries per block-row: the whole-block path
         rows += [r] * cs.size
         cols += list(cs)
     rows = np.array(rows, dtype=np.int64)

@@ -124,14 +124,42 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, int ld, T 
           act = al > floor2 && be > floor2;
         }
         T ga = 0;
-        if (act)
-          for (int i = li; i < n; i += g) ga = fma(G[i + ld * p], G[i + ld * q], ga);
+        if (act) {  // four rows in flight per lane (operands may sit in global memory)
+          const T *gp = G + ld * p, *gq = G + ld * q;
+          T a1 = 0, a2 = 0, a3 = 0;
+          int i = li;
+          for (; i + 3 * g < n; i += 4 * g) {
+            const T x0 = gp[i], x1 = gp[i + g], x2 = gp[i + 2 * g], x3 = gp[i + 3 * g];
+            const T y0 = gq[i], y1 = gq[i + g], y2 = gq[i + 2 * g], y3 = gq[i + 3 * g];
+            ga = fma(x0, y0, ga);
+            a1 = fma(x1, y1, a1);
+            a2 = fma(x2, y2, a2);
+            a3 = fma(x3, y3, a3);
+          }
+          for (; i < n; i += g) ga = fma(gp[i], gq[i], ga);
+          ga = (ga + a1) + (a2 + a3);
+        }
         for (int o = g >> 1; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o, g);
         T cs = 1, sn = 0;
         if (act) act = ga != (T)0 && ga * ga > tol2 * al * be && jacobi_rot(al, be, ga, cs, sn);
         if (act) {
           T *gp = G + ld * p, *gq = G + ld * q, *vp = V + ld * p, *vq = V + ld * q;
-          for (int i = li; i < n; i += g) {
+          // all loads of a row pair before its stores, two rows at a time: the four columns are
+          // distinct, but the compiler cannot prove it, so each store would otherwise wait
+          int i = li;
+          for (; i + g < n; i += 2 * g) {
+            const T x0 = gp[i], y0 = gq[i], x1 = gp[i + g], y1 = gq[i + g];
+            const T u0 = vp[i], w0 = vq[i], u1 = vp[i + g], w1 = vq[i + g];
+            gp[i] = fma(-sn, y0, cs * x0);
+            gq[i] = fma(sn, x0, cs * y0);
+            gp[i + g] = fma(-sn, y1, cs * x1);
+            gq[i + g] = fma(sn, x1, cs * y1);
+            vp[i] = fma(-sn, w0, cs * u0);
+            vq[i] = fma(sn, u0, cs * w0);
+            vp[i + g] = fma(-sn, w1, cs * u1);
+            vq[i + g] = fma(sn, u1, cs * w1);
+          }
+          for (; i < n; i += g) {
             const T x = gp[i], y = gq[i];
             gp[i] = fma(-sn, y, cs * x);
             gq[i] = fma(sn, x, cs * y);

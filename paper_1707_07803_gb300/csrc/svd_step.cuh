@@ -75,11 +75,22 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
     if (tv != 0.0) {
       for (int j = i + 1 + warp; j < n; j += kStepWarps) {
         double *col = X + mm * j;
-        double s = lane == 0 ? col[i] : 0.0;
-        for (int r = i + 1 + lane; r < mm; r += 32) s = fma(v[r], col[r], s);
-        s = dwarp_sum(s) * tv;
+        double s = lane == 0 ? col[i] : 0.0, s1 = 0.0;
+        int r = i + 1 + lane;
+        for (; r + 32 < mm; r += 64) {  // two rows in flight per lane
+          s = fma(v[r], col[r], s);
+          s1 = fma(v[r + 32], col[r + 32], s1);
+        }
+        if (r < mm) s = fma(v[r], col[r], s);
+        s = dwarp_sum(s + s1) * tv;
         if (lane == 0) col[i] -= s;
-        for (int r = i + 1 + lane; r < mm; r += 32) col[r] = fma(-s, v[r], col[r]);
+        r = i + 1 + lane;
+        for (; r + 32 < mm; r += 64) {  // loads of both rows before the stores
+          const double c0 = col[r], c1 = col[r + 32], v0 = v[r], v1 = v[r + 32];
+          col[r] = fma(-s, v0, c0);
+          col[r + 32] = fma(-s, v1, c1);
+        }
+        if (r < mm) col[r] = fma(-s, v[r], col[r]);
       }
     }
     __syncthreads();

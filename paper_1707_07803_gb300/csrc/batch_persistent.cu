@@ -293,13 +293,23 @@ __device__ __noinline__ void cta_zipup(BatchProblem &P, const Ctx &c, const doub
         const int x0 = s_ + S * (y + Ny * cc), xs = S * Ny * Kx;
         const int c0 = r2 + R2 * S2 * b, cs = R2;
         if (mixed) {
-          float acc = 0.f;
-          for (int s2 = 0; s2 < S2; ++s2) acc = fmaf(Xf[x0 + xs * s2], Cf[c0 + cs * s2], acc);
-          Wf[idx] = acc;
+          float acc = 0.f, acc1 = 0.f;
+          int s2 = 0;
+          for (; s2 + 1 < S2; s2 += 2) {  // two terms in flight
+            acc = fmaf(Xf[x0 + xs * s2], Cf[c0 + cs * s2], acc);
+            acc1 = fmaf(Xf[x0 + xs * (s2 + 1)], Cf[c0 + cs * (s2 + 1)], acc1);
+          }
+          if (s2 < S2) acc = fmaf(Xf[x0 + xs * s2], Cf[c0 + cs * s2], acc);
+          Wf[idx] = acc + acc1;
         } else {
-          double acc = 0.0;
-          for (int s2 = 0; s2 < S2; ++s2) acc = fma(X[x0 + xs * s2], C[c0 + cs * s2], acc);
-          P.zw[idx] = acc;
+          double acc = 0.0, acc1 = 0.0;
+          int s2 = 0;
+          for (; s2 + 1 < S2; s2 += 2) {
+            acc = fma(X[x0 + xs * s2], C[c0 + cs * s2], acc);
+            acc1 = fma(X[x0 + xs * (s2 + 1)], C[c0 + cs * (s2 + 1)], acc1);
+          }
+          if (s2 < S2) acc = fma(X[x0 + xs * s2], C[c0 + cs * s2], acc);
+          P.zw[idx] = acc + acc1;
         }
       }
       __syncthreads();
@@ -310,13 +320,23 @@ __device__ __noinline__ void cta_zipup(BatchProblem &P, const Ctx &c, const doub
         const int a0 = (trans ? r + R * (I * x) : r + R * x) + a_y * y, as = R * I * J;
         const int w0 = s_ + S * (cc + Kx * R2 * b), ws = S * Kx;
         if (mixed) {
-          float acc = 0.f;
-          for (int r2 = 0; r2 < R2; ++r2) acc = fmaf(Af[a0 + as * r2], Wf[w0 + ws * r2], acc);
-          T[idx] += (double)acc;
+          float acc = 0.f, acc1 = 0.f;
+          int r2 = 0;
+          for (; r2 + 1 < R2; r2 += 2) {  // two terms in flight
+            acc = fmaf(Af[a0 + as * r2], Wf[w0 + ws * r2], acc);
+            acc1 = fmaf(Af[a0 + as * (r2 + 1)], Wf[w0 + ws * (r2 + 1)], acc1);
+          }
+          if (r2 < R2) acc = fmaf(Af[a0 + as * r2], Wf[w0 + ws * r2], acc);
+          T[idx] += (double)(acc + acc1);
         } else {
-          double acc = 0.0;
-          for (int r2 = 0; r2 < R2; ++r2) acc = fma(A[a0 + as * r2], P.zw[w0 + ws * r2], acc);
-          T[idx] += acc;
+          double acc = 0.0, acc1 = 0.0;
+          int r2 = 0;
+          for (; r2 + 1 < R2; r2 += 2) {
+            acc = fma(A[a0 + as * r2], P.zw[w0 + ws * r2], acc);
+            acc1 = fma(A[a0 + as * (r2 + 1)], P.zw[w0 + ws * (r2 + 1)], acc1);
+          }
+          if (r2 < R2) acc = fma(A[a0 + as * r2], P.zw[w0 + ws * r2], acc);
+          T[idx] += acc + acc1;
         }
       }
       __syncthreads();

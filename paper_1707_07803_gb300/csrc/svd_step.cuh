@@ -54,9 +54,14 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
   for (int i = 0; i < n; ++i) {
     if (warp == 0) {
       double *col = X + mm * i;
-      double sig = 0.0;
-      for (int r = i + 1 + lane; r < mm; r += 32) sig = fma(col[r], col[r], sig);
-      sig = dwarp_sum(sig);
+      double sig = 0.0, sig1 = 0.0;
+      int r0 = i + 1 + lane;
+      for (; r0 + 32 < mm; r0 += 64) {  // two rows in flight per lane
+        sig = fma(col[r0], col[r0], sig);
+        sig1 = fma(col[r0 + 32], col[r0 + 32], sig1);
+      }
+      if (r0 < mm) sig = fma(col[r0], col[r0], sig);
+      sig = dwarp_sum(sig + sig1);
       const double alpha = col[i];
       double tv = 0.0, beta = alpha, scal = 0.0;
       if (sig > 0.0) {
@@ -244,11 +249,22 @@ static __device__ __noinline__ int svd_step_cta(const double *M, int t, int w, d
     const double *v = X + mm * i;
     for (int c = warp; c < r; c += kStepWarps) {
       double *col = W + mm * c;
-      double s = lane == 0 ? col[i] : 0.0;
-      for (int q = i + 1 + lane; q < mm; q += 32) s = fma(v[q], col[q], s);
-      s = dwarp_sum(s) * tv;
+      double s = lane == 0 ? col[i] : 0.0, s1 = 0.0;
+      int q = i + 1 + lane;
+      for (; q + 32 < mm; q += 64) {  // two rows in flight per lane
+        s = fma(v[q], col[q], s);
+        s1 = fma(v[q + 32], col[q + 32], s1);
+      }
+      if (q < mm) s = fma(v[q], col[q], s);
+      s = dwarp_sum(s + s1) * tv;
       if (lane == 0) col[i] -= s;
-      for (int q = i + 1 + lane; q < mm; q += 32) col[q] = fma(-s, v[q], col[q]);
+      q = i + 1 + lane;
+      for (; q + 32 < mm; q += 64) {  // loads of both rows before the stores
+        const double c0 = col[q], c1 = col[q + 32], v0 = v[q], v1 = v[q + 32];
+        col[q] = fma(-s, v0, c0);
+        col[q + 32] = fma(-s, v1, c1);
+      }
+      if (q < mm) col[q] = fma(-s, v[q], col[q]);
     }
     __syncthreads();
   }

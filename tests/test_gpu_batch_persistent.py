@@ -174,3 +174,25 @@ def test_bad_problem_refused_and_capacity_checked_per_problem():
         _check_against_oracle(pr, host_cores(sp.outputs()[0]), sp.S.cpu().numpy(), host_cores(sp.outputs()[2]),
                               FP64_SV_TOL, check_ranks=True)
     assert lib.tnr_batch_destroy(h) == 0
+
+
+def test_mixed_batch_on_decaying_spectra_where_the_rounding_truncates():
+    """Prescribed-sigma problems (sigma_j = 0.5^j, 16 values, K = 8 < 16): the power iteration's
+    rounding at max(tol, 1e-6) truncates real directions; the mixed batch (FP32 products) still
+    matches the FP64 oracle within the mixed-mode gate 1e-6, and the FP64 batch within 1e-10."""
+    probs = []
+    for i in range(6):
+        sigma = 0.5 ** np.arange(16) * (1 + 0.1 * i)
+        A, _, _ = W.prescribed_mpo(10 + i, 20 + i, 16, [2, 2, 2, 2, 2], 16, 3, sigma)
+        probs.append(dict(A=A, k=4, p=4, q=1, seed=i, tol=1e-12, max_rank=8))
+    for precision, gate in ((T.TNR_FP64, FP64_SV_TOL), (T.TNR_MIXED, MIXED_SV_TOL)):
+        dp = [dict(pr, A=dev_mpo(pr["A"]), A_host=pr["A"], precision=precision) for pr in probs]
+        pb = T.PersistentBatch(dp, precision=precision, autotune=False, graph=False)
+        pb.launch()
+        assert pb.collect() == 0
+        for i, pr in enumerate(dp):
+            _, S, _ = pb.outputs(i)
+            _, So, _ = ot.tnrsvd(pr["A_host"], pr["k"], pr["p"], pr["q"], pr["seed"], tol=pr["tol"],
+                                 max_rank=pr["max_rank"])
+            assert sv_rel_err(S.cpu().numpy(), So) <= gate
+        pb.close()

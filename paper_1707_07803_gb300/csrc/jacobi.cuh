@@ -186,6 +186,157 @@ static __device__ __noinline__ int jacobi_sweeps_t(T *G, T *V, int n, int ld, T 
 
 // Doubles of work area jacobi_sweeps_mixed needs for an n x n matrix.
 __host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 3 * n * (n + 1); }
+// Extra doubles the matrix-product refinement (jacobi_refine) needs after that area.
+__host__ __device__ inline int64_t jacobi_refine_work(int64_t n) { return 7 * n * (n + 1); }
+
+// C (n x n, ld ldc) = op(X) op(Y) for n x n operands with leading dimensions ldx, ldy
+// (tx / ty: transpose), by the whole CTA, one output per thread per pass, two accumulators.
+static __device__ void cta_nn_product(double *C, int ldc, const double *X, int ldx, bool tx, const double *Y,
+                                      int ldy, bool ty, int n) {
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    double s0 = 0.0, s1 = 0.0;
+    int l = 0;
+    for (; l + 1 < n; l += 2) {
+      s0 = fma(tx ? X[l + ldx * i] : X[i + ldx * l], ty ? Y[j + ldy * l] : Y[l + ldy * j], s0);
+      s1 = fma(tx ? X[l + 1 + ldx * i] : X[i + ldx * (l + 1)], ty ? Y[j + ldy * (l + 1)] : Y[l + 1 + ldy * j], s1);
+    }
+    if (l < n) s0 = fma(tx ? X[l + ldx * i] : X[i + ldx * l], ty ? Y[j + ldy * l] : Y[l + ldy * j], s0);
+    C[i + ldc * j] = s0 + s1;
+  }
+}
+
+// Matrix-product refinement of an SVD (Ogita and Aishima, "Iterative refinement for singular value
+// decomposition based on matrix multiplication", 2020), restated. A (n x n, ld n) is the matrix,
+// Vin (ld ldv) approximate right singular vectors (the FP32 sweeps' result, widened). With
+// U = A V diag(1/sigma), a step forms R = I - U^T U, S = I - V^T V and T = U^T A V, and the
+// first-order corrections F, Gc with U <- U (I + F), V <- V (I + Gc) such that both stay
+// orthonormal and U^T A V becomes diagonal: sigma_i = t_ii / (1 - (r_ii + s_ii) / 2),
+// f_ii = r_ii / 2, g_ii = s_ii / 2, and for i < j, with a = -t_ij - sigma_j r_ij and
+// b = -t_ji - sigma_j s_ij, f_ij = (-sigma_j a - sigma_i b) / (sigma_j^2 - sigma_i^2),
+// g_ij = (-sigma_i a - sigma_j b) / (sigma_j^2 - sigma_i^2), f_ji = r_ij - f_ij, g_ji = s_ij - g_ij.
+// The error contracts quadratically while the singular values are separated: two steps take the
+// FP32 result to FP64 accuracy, with products only (no sequential rotation rounds). On success A
+// becomes U diag(sigma) (columns sigma_j u_j, the one-sided Jacobi convention), Vout (ld n) the refined V,
+// and the function returns true. It returns false, leaving A and Vin untouched, when two singular
+// values lie within 1e-3 relative of each other, one is below n eps sigma_max, or the residual has
+// not dropped below 1e-9 after the first step; the caller then runs the FP64 sweeps.
+// wk: jacobi_refine_work(n) doubles.
+static __device__ __noinline__ bool jacobi_refine(double *A, const double *Vin, int ldv, double *Vout, int n,
+                                                  double *wk) {
+  const int ld = n + 1;
+  double *U = wk, *V = U + n * ld, *H = V + n * ld, *R = H + n * ld, *Sm = R + n * ld, *Tm = Sm + n * ld;
+  double *Fm = Tm + n * ld;  // F, then Gc written over R / S as they are consumed
+  __shared__ double s_sig[1024];
+  __shared__ int s_ok;
+  __shared__ double s_err;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    V[i + ld * j] = Vin[i + ldv * j];
+  }
+  __syncthreads();
+  cta_nn_product(H, ld, A, n, false, V, ld, false, n);  // H = A V
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s0 = 0.0;
+    for (int i = 0; i < n; ++i) s0 = fma(H[i + ld * j], H[i + ld * j], s0);
+    s_sig[j] = sqrt(s0);
+  }
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    U[i + ld * j] = s_sig[j] > 0.0 ? H[i + ld * j] / s_sig[j] : 0.0;
+  }
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    cta_nn_product(R, ld, U, ld, true, U, ld, false, n);   // U^T U
+    cta_nn_product(Sm, ld, V, ld, true, V, ld, false, n);  // V^T V
+    if (step > 0) cta_nn_product(H, ld, A, n, false, V, ld, false, n);
+    __syncthreads();
+    cta_nn_product(Tm, ld, U, ld, true, H, ld, false, n);  // T = U^T A V
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {  // R = I - U^T U, S = I - V^T V
+      const int i = idx % n, j = idx / n;
+      R[i + ld * j] = (i == j ? 1.0 : 0.0) - R[i + ld * j];
+      Sm[i + ld * j] = (i == j ? 1.0 : 0.0) - Sm[i + ld * j];
+    }
+    __syncthreads();
+    // sigma from the diagonal (one thread per value), then the checks spread over the CTA (FP64
+    // work on one thread would hold its pipe ~64 cycles per instruction)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      s_sig[i] = Tm[i + ld * i] / (1.0 - 0.5 * (R[i + ld * i] + Sm[i + ld * i]));
+    if (threadIdx.x == 0) s_err = 0.0;
+    __syncthreads();
+    double smax = 0.0;
+    for (int i = 0; i < n; ++i) smax = fmax(smax, fabs(s_sig[i]));
+    {
+      bool bad = false;
+      double err = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        bad |= !(s_sig[i] > (double)n * DBL_EPSILON * smax);
+        for (int j = 0; j < i; ++j) bad |= fabs(s_sig[i] - s_sig[j]) <= 1e-3 * fmax(s_sig[i], s_sig[j]);
+      }
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx % n, j = idx / n;
+        err = fmax(err, fmax(fabs(R[i + ld * j]), fabs(Sm[i + ld * j])));
+        if (i != j) err = fmax(err, fabs(Tm[i + ld * j]) / smax);
+      }
+      for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+      if (bad) s_ok = 0;
+      if ((threadIdx.x & 31) == 0 && err > 0.0)  // non-negative doubles order like their bits
+        atomicMax(reinterpret_cast<unsigned long long *>(&s_err), (unsigned long long)__double_as_longlong(err));
+    }
+    __syncthreads();
+    if (step == 1 && !(s_err <= 1e-9)) s_ok = 0;
+    __syncthreads();
+    if (!s_ok) return false;
+    // corrections: F into Fm, Gc into H (H = A V is recomputed next step)
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx % n, j = idx / n;
+      double f, g;
+      if (i == j) {
+        f = 0.5 * R[i + ld * i];
+        g = 0.5 * Sm[i + ld * i];
+      } else {
+        const int a_ = i < j ? i : j, b_ = i < j ? j : i;  // solve for the pair (a_, b_), a_ < b_
+        const double sa = s_sig[a_], sb = s_sig[b_];
+        const double aa = -Tm[a_ + ld * b_] - sb * R[a_ + ld * b_];
+        const double bb = -Tm[b_ + ld * a_] - sb * Sm[a_ + ld * b_];
+        const double det = sb * sb - sa * sa;
+        const double fab = (-sb * aa - sa * bb) / det, gab = (-sa * aa - sb * bb) / det;
+        if (i < j) {
+          f = fab;
+          g = gab;
+        } else {
+          f = R[a_ + ld * b_] - fab;
+          g = Sm[a_ + ld * b_] - gab;
+        }
+      }
+      Fm[i + ld * j] = f;
+      H[i + ld * j] = g;
+    }
+    __syncthreads();
+    // U <- U + U F, V <- V + V Gc (products into R / S, then added)
+    cta_nn_product(R, ld, U, ld, false, Fm, ld, false, n);
+    cta_nn_product(Sm, ld, V, ld, false, H, ld, false, n);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx % n, j = idx / n;
+      U[i + ld * j] += R[i + ld * j];
+      V[i + ld * j] += Sm[i + ld * j];
+    }
+    __syncthreads();
+  }
+  // sigma from the last step's diagonal formula; A <- U diag(sigma), Vout <- V
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    A[i + n * j] = U[i + ld * j] * s_sig[j];
+    Vout[i + n * j] = V[i + ld * j];
+  }
+  __syncthreads();
+  return true;
+}
 
 // Mixed-precision one-sided Jacobi (the preconditioned scheme of Gao, Ma and Shao, "A mixed
 // precision Jacobi SVD algorithm", 2022): the sweeps run to convergence in FP32 on a copy of G
@@ -197,7 +348,8 @@ __host__ __device__ inline int64_t jacobi_mixed_work(int64_t n) { return 3 * n *
 // the FP32 pipe, 64 times wider than FP64 on GB300. Results: G V = U S with V orthogonal to FP64
 // rounding, as plain FP64 sweeps give. V on entry is ignored (the identity is assumed).
 // work: jacobi_mixed_work(n) doubles. Returns the number of FP64 sweeps.
-static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work) {
+static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work,
+                                                       double *refine_work = nullptr) {
   const int nthr = blockDim.x;
   const int nn = n * n;
   // padded working copies (leading dimension n + 1): columns i and i + 1 start in different
@@ -235,6 +387,8 @@ static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int
     Vp[i + ld * j] = (double)Vf[i + ld * j];
   }
   __syncthreads();
+  // separated singular values: finish with the product refinement instead of the FP64 sweeps
+  if (refine_work && n <= 1024 && jacobi_refine(G, Vp, ld, V, n, refine_work)) return 0;
   // Newton-Schulz steps: T1 = V^T V (in Gp), V <- 1.5 V - 0.5 V T1 (into Tp; the FP32 copies
   // are dead now), then the roles of Vp and Tp swap. Lane i reads row l of column i of V (stride
   // n + 1: conflict-free) or row i of column l; the other operand is a broadcast.

@@ -768,7 +768,8 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
     v[idx] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
-  jacobi_sweeps_mixed(g, v, n, s_norm, jw);  // jacobi.cuh
+  // FP32 sweeps, then the product refinement (or, for close singular values, the FP64 sweeps)
+  jacobi_sweeps_mixed(g, v, n, s_norm, jw, jw + jacobi_mixed_work(n));  // jacobi.cuh
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nthr / 32;
   // final column norms and their reciprocals, one thread per column (the square roots and
@@ -1036,7 +1037,7 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
 }
 
 // Doubles of the K x K Jacobi's working set: G, V and the mixed-precision work area.
-static int64_t jacobi_elems(int64_t n) { return 2 * n * n + jacobi_mixed_work(n); }
+static int64_t jacobi_elems(int64_t n) { return 2 * n * n + jacobi_mixed_work(n) + jacobi_refine_work(n); }
 
 size_t jacobi_scratch(int64_t n) {
   if (jacobi_elems(n) * (int64_t)sizeof(double) <= 160 * 1024) return 0;

@@ -10,6 +10,7 @@
 #include <cfloat>
 #include <cmath>
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "dev_common.cuh"
@@ -769,7 +770,26 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
   }
   __syncthreads();
   // FP32 sweeps, then the product refinement (or, for close singular values, the FP64 sweeps)
-  jacobi_sweeps_mixed(g, v, n, s_norm, jw, jw + jacobi_mixed_work(n));  // jacobi.cuh
+  const unsigned nc = cluster_nctarank();  // 1: launched without a cluster
+  if (nc == 1) {
+    jacobi_sweeps_mixed(g, v, n, s_norm, jw, jw + jacobi_mixed_work(n));  // jacobi.cuh
+  } else {
+    // a cluster (working set in shared memory): CTA 0 runs the FP32 sweeps and stores V0 into
+    // every CTA's work area, then all CTAs share the refinement's products; CTA 0 alone runs the
+    // FP64 sweeps if the refinement declines, and writes the results
+    const unsigned me = cluster_ctarank();
+    const int np = n * (n + 1);
+    double *v0 = jw + np;  // where jacobi_fp32_phase leaves V0 (ld n + 1)
+    if (me == 0) {
+      jacobi_fp32_phase(g, n, s_norm, jw);
+      for (int idx = threadIdx.x; idx < np; idx += nthr)
+        for (unsigned rk = 1; rk < nc; ++rk) dsmem_st_f64(dsmem_addr(v0 + idx, rk), v0[idx]);
+    }
+    cluster_sync_all();
+    const bool ok = jacobi_refine(g, v0, n + 1, v, n, jw + jacobi_mixed_work(n), true);
+    if (me != 0) return;  // no shared-memory access between CTAs follows the last cluster barrier
+    if (!ok) jacobi_fp64_finish(g, v, n, s_norm, jw);
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nthr / 32;
   // final column norms and their reciprocals, one thread per column (the square roots and
@@ -1036,6 +1056,11 @@ int qr_small_f64(cudaStream_t s, const double *src, int64_t lds, int64_t m, int6
   return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }
 
+// CTAs of the K x K Jacobi's cluster, and whether cluster launches work in this process
+// (-1 unknown, 0 refused, 1 working).
+constexpr int kJacCluster = 8;
+static std::atomic<int> g_jac_cluster{-1};
+
 // Doubles of the K x K Jacobi's working set: G, V and the mixed-precision work area.
 static int64_t jacobi_elems(int64_t n) { return 2 * n * n + jacobi_mixed_work(n) + jacobi_refine_work(n); }
 
@@ -1057,8 +1082,36 @@ int jacobi_svd_f64(cudaStream_t s, double *G, int64_t n, int64_t ldg, double *S,
   }
   TNR_TRY(ensure_dynamic_smem((const void *)k_jacobi, smem));
   const int ppw = jacobi_pairs_per_warp((int)n, kJacThreads / 32);
-  const int warps = (int)std::min<int64_t>(kJacThreads / 32, std::max<int64_t>(1, ((n + 1) / 2 + ppw - 1) / ppw));
+  // at least eight warps: the sweeps use those their pairs need, the refinement's FP64 products all
+  // (one warp per SM sub-partition leaves the FMA latency exposed); up to 32 columns, one warp per
+  // column pair of the FP32 sweeps
+  int64_t want = std::max<int64_t>(8, ((n + 1) / 2 + ppw - 1) / ppw);
+  if (n <= 32) want = std::max<int64_t>(want, (n + 1) / 2);
+  const int warps = (int)std::min<int64_t>(kJacThreads / 32, want);
   LaunchScope ls(K_SVD, s);
+  // working set in shared memory: a cluster of kJacCluster CTAs shares the refinement's products
+  // (one GPU; distributed shared memory), unless cluster launches were refused before
+  if (Gw == nullptr && n <= 32 && g_jac_cluster.load() != 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)kJacCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)kJacCluster);
+    cfg.blockDim = dim3((unsigned)(32 * warps));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi, G, (int)n, (int)ldg, S, V, (int)ldv, Gw, Vw, status_ptr());
+    if (e == cudaSuccess) {
+      g_jac_cluster.store(1);
+      return TNR_OK;
+    }
+    (void)cudaGetLastError();  // refused: one CTA from now on
+    g_jac_cluster.store(0);
+  }
   k_jacobi<<<1, 32 * warps, smem, s>>>(G, (int)n, (int)ldg, S, V, (int)ldv, Gw, Vw, status_ptr());
   return check_cuda_at(cudaGetLastError(), __FILE__, __LINE__);
 }

@@ -117,6 +117,27 @@ def test_solve_exact_recovery_prescribed_sigma():
     np.testing.assert_allclose(S, sigma[:4], rtol=1e-12)
 
 
+def test_solve_repeated_singular_values_take_the_fp64_sweeps():
+    """Prescribed singular values in groups of equal values (1 x3, 0.5 x3, 0.25 x2, then distinct):
+    the K x K SVD of B has equal singular values, so its product refinement declines and the FP64
+    Jacobi sweeps finish it (on the cluster's first CTA). k = 8 ends at a gap, so the top-k
+    subspaces are unique: the singular values match the oracle and the exact ones, and U, V span
+    the oracle's subspaces (their cross Gram matrices are orthogonal)."""
+    K, k = 16, 8
+    sigma = np.array([1, 1, 1, 0.5, 0.5, 0.5, 0.25, 0.25] + [0.1 * 0.7**j for j in range(K - 8)])
+    A, _, _ = W.prescribed_mpo(3, 4, 16, [2, 2, 2], K, 3, sigma)
+    Uo, So, Vo = ot.tnrsvd(A, k, k, 1, 5, tol=1e-13)
+    U, S, V = T.tnr_solve(dev_mpo(A), k, k, 1, 5, tol=1e-13)
+    torch.cuda.synchronize()
+    S = S.cpu().numpy()
+    assert sv_rel_err(S, So) <= FP64_SV_TOL
+    np.testing.assert_allclose(S, sigma[:k], rtol=1e-12)
+    Uh, Vh = host_cores(U), host_cores(V)
+    for X, Xo in ((Uh, Uo), (Vh, Vo)):
+        np.testing.assert_allclose(om.inner(X, X), np.eye(k), atol=1e-12)
+        np.testing.assert_allclose(np.linalg.svd(om.inner(X, Xo), compute_uv=False), 1.0, atol=1e-10)
+
+
 def test_solve_max_rank_cap():
     A = W.gaussian_mpo(9, [4, 4, 4, 4, 4], [4, 4, 4, 4, 4], [1, 4, 4, 4, 4, 1], scale=0.25)
     _check_solve(A, 4, 4, 1, seed=3, tol=1e-14, max_rank=6)

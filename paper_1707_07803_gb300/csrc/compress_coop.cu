@@ -73,6 +73,23 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     }
     int r_qr = 0;
     QrSmallArgs q;
+    // absorbing CTAs (a cluster factors M_k): their block of rows of core k-1 staged in shared
+    // memory while the cluster runs the QR (core k-1 is not written before its own bond)
+    const unsigned first = C > 1 ? C : 0;  // CTAs that absorb: [first, gridDim.x)
+    const int rows = a.R[k - 1] * a.phys[k - 1];
+    const int nA = (int)gridDim.x - (int)first;
+    const int rpb = (rows + nA - 1) / nA;
+    const int arow0 = ((int)blockIdx.x - (int)first) * rpb;
+    const int anrow = blockIdx.x >= first ? max(0, min(rpb, rows - arow0)) : 0;
+    const bool pre = C > 1 && nA > 0 &&
+                     ((int64_t)rpb * t + (int64_t)t * min(w, t)) * (int64_t)sizeof(double) <= a.round_cap;
+    if (pre && blockIdx.x >= first) {
+      const double *c0 = a.core[k - 1];
+      for (int x = threadIdx.x; x < anrow * t; x += blockDim.x) {
+        const int rr = x % anrow, j = x / anrow;
+        sm[x] = __ldcg(c0 + arow0 + rr + (int64_t)rows * j);
+      }
+    }
     if (blockIdx.x < C) {  // M_k^T (w x t) = Q~ R~ P^T: core k <- Q~^T (r x w), L <- R~^T (t x r)
       q.src = cur;
       q.lds = t;
@@ -100,13 +117,39 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
     const int r = (C > 1 && blockIdx.x < C) ? r_qr : (int)__ldcg(a.R_out + k);
     const double *Cc = a.core[k - 1];
     double *out = a.buf[k & 1];
-    const unsigned first = C > 1 ? C : 0;  // CTAs that absorb: [first, gridDim.x)
     if (blockIdx.x < first) {
       qr_cluster_form_q(q, sm, r);  // core k <- Q~^T, beside the absorb
+    } else if (pre) {
+      // the staged rows times L (t x r, staged after them): eight lanes per output, each summing
+      // the terms j = lane mod 8 in two chains, then a three-level shuffle sum (fixed order)
+      const double *cs = sm;
+      double *Ls = sm + (int64_t)anrow * t;
+      for (int x = threadIdx.x; x < t * r; x += blockDim.x) Ls[x] = __ldcg(a.L + x);
+      __syncthreads();
+      const int part = threadIdx.x & 7, nout = anrow * r, ngroups = (int)(blockDim.x >> 3);
+      // g0: the warp's first group, so the loop condition (and the shuffles) are warp-uniform
+      for (int g = (int)(threadIdx.x >> 3), g0 = (int)(threadIdx.x >> 5) * 4; g0 < nout; g += ngroups, g0 += ngroups) {
+        const bool live = g < nout;
+        const int rr = live ? g % anrow : 0, c = live ? g / anrow : 0;
+        double s0 = 0.0, s1 = 0.0;
+        if (live) {
+          const double *ci = cs + rr, *l = Ls + (int64_t)t * c;
+          int j = part;
+          for (; j + 8 < t; j += 16) {
+            s0 = fma(ci[(int64_t)anrow * j], l[j], s0);
+            s1 = fma(ci[(int64_t)anrow * (j + 8)], l[j + 8], s1);
+          }
+          if (j < t) s0 = fma(ci[(int64_t)anrow * j], l[j], s0);
+        }
+        double acc = s0 + s1;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (live && part == 0) out[arow0 + rr + (int64_t)rows * c] = acc;
+      }
     } else {
       // absorb: core k-1 (rows x t) L (t x r) -> buf (rows x r); L staged in shared memory (the
       // QR's buffer is free now), the core streamed from global memory
-      const int rows = a.R[k - 1] * a.phys[k - 1];
       double *Ls = sm;
       const bool staged = (int64_t)t * r * (int64_t)sizeof(double) <= a.round_cap;
       if (staged)
@@ -226,8 +269,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_compress(CompressArgs a) {
 // Cluster size of the factoring cluster; whether the cooperative launch with clusters is
 // available is decided at the first launch of the process (kept: -1 unknown, 0 refused, else C).
 constexpr int kCompressCluster = 8;
+// CTAs of the launch at most (whole clusters that fit): the absorb of each bond is bound by the
+// FP64 instructions per SM, so it runs on every CTA outside the factoring cluster.
+constexpr int kCompressGrid = 128;
 static_assert(kCompressCluster * kQrWarps <= 32 && kCompressCluster <= kClusterMaxCtas,
               "one warp reads every candidate of the cluster; portable cluster size");
+static_assert(kSmallThreads >= 32 * (kQrWarps + 1), "the cluster QR needs a parameter warp besides its factorisation warps");
 static std::atomic<int> g_cluster_mode{-1};
 
 int compress_cluster_size() { return g_cluster_mode.load() > 0 ? g_cluster_mode.load() : 1; }
@@ -284,7 +331,7 @@ int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, dou
       at[0].val.clusterDim.z = 1;
       at[1].id = cudaLaunchAttributeCooperative;
       at[1].val.cooperative = 1;
-      cfg.gridDim = dim3(64);
+      cfg.gridDim = dim3(kCompressGrid);
       cfg.blockDim = dim3(kSmallThreads);
       cfg.dynamicSmemBytes = (size_t)smem;
       cfg.stream = s;
@@ -297,7 +344,7 @@ int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, dou
         g_cluster_mode.store(0);
         continue;
       }
-      cfg.gridDim = dim3((unsigned)(C * std::min(64 / C, clusters)));
+      cfg.gridDim = dim3((unsigned)(C * std::min(kCompressGrid / C, clusters)));
       cfg.numAttrs = 2;
       TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
       cudaError_t e;
@@ -317,7 +364,7 @@ int compress_launch(cudaStream_t s, const tnr_mpo &Y, double cut, double *L, dou
     int per_sm = 0;
     TNR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compress, kSmallThreads, (size_t)smem));
     if (per_sm < 1) return TNR_OK;
-    const int blocks = std::min(64, sms * per_sm);
+    const int blocks = std::min(kCompressGrid, sms * per_sm);
     TNR_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
     {
       LaunchScope ls(K_QR_PIV, s);

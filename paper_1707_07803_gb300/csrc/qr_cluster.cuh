@@ -39,7 +39,7 @@ constexpr int kClusterMaxCtas = 8;  // portable cluster size limit
 // Dynamic shared-memory bytes of qr_cluster_cta per CTA for an m x n matrix over C CTAs.
 __host__ __device__ inline int64_t qr_cluster_bytes(int64_t m, int64_t n, int64_t C) {
   const int64_t nl = (n + C - 1) / C, nref = m < n ? m : n;
-  return (int64_t)sizeof(double) * (m * nl + 2 * nl + m * nref + 2 * nref + kQrWarps * 64 + 2 * C * kQrWarps * 64) +
+  return (int64_t)sizeof(double) * (m * nl + 3 * nl + m * nref + 2 * nref + kQrWarps * 64 + 2 * C * kQrWarps * 64) +
          (int64_t)sizeof(int) * nl;
 }
 
@@ -67,6 +67,7 @@ struct QrClusterLayout {
   double *A;     // m x nl row-major: A(t, jl) at t * nl + jl
   double *nrm;   // nl: squared norms below the active row
   double *thr;   // nl: 2^-26 x the squared norm at the last recompute
+  double *dsum;  // nl: partial dot products of the current step (rows below the pivot row)
   double *V;     // m x nref: reflector i in column i (rows >= i)
   double *tau;   // nref
   double *bet;   // nref: R(i, p_i)
@@ -79,7 +80,8 @@ struct QrClusterLayout {
     A = sm;
     nrm = A + m * nl;
     thr = nrm + nl;
-    V = thr + nl;
+    dsum = thr + nl;
+    V = dsum + nl;
     tau = V + m * nref;
     bet = tau + nref;
     vb = bet + nref;
@@ -130,6 +132,11 @@ static __device__ __forceinline__ void warp_argmax(long long &k, int &j) {
   }
 }
 
+// Named barrier 1 among the factorisation warps and the parameter warp (kQrWarps + 1 warps).
+__device__ __forceinline__ void qr_cluster_join() {
+  asm volatile("bar.sync 1, %0;" ::"r"((kQrWarps + 1) * 32) : "memory");
+}
+
 static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *sm) {
   const int m = (int)a.m, n = (int)a.n;
   const unsigned C = cluster_nctarank(), me = cluster_ctarank();
@@ -138,6 +145,7 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
   double *A = lay.A, *nrm = lay.nrm, *thr = lay.thr, *V = lay.V, *tau = lay.tau, *bet = lay.bet, *vb = lay.vb;
   int *step_of = lay.step_of;
   __shared__ QrClusterSlots sl;
+  __shared__ double s_hh[2];  // the current reflector's tau and scale
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lg = qr_cluster_lg(m, nl), g = 1 << lg, cpw = 32 >> lg, sub = lane & (g - 1);
   const int rounds = (nl + cpw - 1) / cpw;
@@ -193,34 +201,53 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
       r = i;
       break;
     }
-    if (warp >= kQrWarps) continue;
+    // Warp kQrWarps forms the reflector's parameters from p's received column (rows i .. m-1;
+    // posted by the warp that updates column pl, slot own x kQrWarps + (pl / cpw) mod kQrWarps)
+    // while the factorisation warps form the partial dot products d_j = sum_{t > i} x_t a_tj,
+    // which do not depend on them; a named barrier joins the two. With v_i = 1, v_t = x_t scal:
+    // w_j = tau (a_ij + scal d_j), a_ij <- a_ij - w_j, a_tj <- a_tj - (w_j scal) x_t.
     const int p = ci;
     const unsigned own = (unsigned)(p / nl);
     const int pl = p - (int)own * nl;
-    // reflector from p's received column (rows i .. m-1); it was posted by the warp that updates
-    // column pl, slot own x kQrWarps + (pl / cpw) mod kQrWarps
     const double *col = lay.rcol + (b * ncand + (int)own * kQrWarps + (pl / cpw) % kQrWarps) * 64;
     const int t0 = i + lane, t1 = i + lane + 32;
+    if (warp > kQrWarps) continue;
     const double x0 = t0 < m ? col[t0] : 0.0;
     const double x1 = t1 < m ? col[t1] : 0.0;
-    const double alpha = __shfl_sync(0xffffffffu, x0, 0);
-    const double sig = dwarp_sum(fma(x1, x1, lane > 0 ? x0 * x0 : 0.0));
-    double tv = 0.0, beta = alpha, scal = 0.0;
-    if (sig > 0.0) householder_params(alpha, sig, beta, tv, scal);
-    double *v = vb + warp * 64;
-    const double v0 = lane == 0 ? 1.0 : x0 * scal, v1 = x1 * scal;
-    if (t0 < m) v[t0] = v0;
-    if (t1 < m) v[t1] = v1;
-    if (warp == 0) {
-      if (t0 < m) V[i * m + t0] = v0;
-      if (t1 < m) V[i * m + t1] = v1;
+    if (warp == kQrWarps) {
+      const double alpha = __shfl_sync(0xffffffffu, x0, 0);
+      const double sig = dwarp_sum(fma(x1, x1, lane > 0 ? x0 * x0 : 0.0));
+      double tv = 0.0, beta = alpha, scal = 0.0;
+      if (sig > 0.0) householder_params(alpha, sig, beta, tv, scal);
       if (lane == 0) {
+        s_hh[0] = tv;
+        s_hh[1] = scal;
         tau[i] = tv;
         bet[i] = beta;
         if (own == me) step_of[pl] = i;
       }
+      qr_cluster_join();
+      // the normalised reflector for the Q formation and the R output (off the critical path)
+      if (t0 < m) V[i * m + t0] = lane == 0 ? 1.0 : x0 * scal;
+      if (t1 < m) V[i * m + t1] = x1 * scal;
+      continue;
     }
+    double *v = vb + warp * 64;  // the raw column (rows > i are read)
+    if (t0 < m) v[t0] = x0;
+    if (t1 < m) v[t1] = x1;
     __syncwarp();
+    for (int rho = warp; rho < rounds; rho += kQrWarps) {
+      const int jl = rho * cpw + (lane >> lg), j = c0 + jl;
+      if (jl >= nl || j == p || step_of[jl] >= 0) continue;  // uniform over the lane group
+      const double *cj = A + jl;
+      double dot = 0.0;
+      for (int t = i + 1 + sub; t < m; t += g) dot = fma(v[t], cj[t * nl], dot);
+      for (int o = 1; o < g; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
+      if (sub == 0) lay.dsum[jl] = dot;
+    }
+    qr_cluster_join();
+    const double tv = s_hh[0], scal = s_hh[1];
+    __syncwarp();  // each column's partial dot, stored by its group's first lane, is read by the group
     // apply to this warp's remaining columns; post the best remaining column for step i + 1
     long long bk = -1;
     int bi = INT_MAX;
@@ -231,18 +258,16 @@ static __device__ __noinline__ int qr_cluster_cta(const QrSmallArgs &a, double *
       const double aij = cj[i * nl];
       double rij = aij;
       if (tv != 0.0) {
-        double dot = 0.0;
-        for (int t = i + sub; t < m; t += g) dot = fma(v[t], cj[t * nl], dot);
-        for (int o = 1; o < g; o <<= 1) dot += __shfl_xor_sync(gmask, dot, o);
-        const double w = dot * tv;
-        for (int t = i + sub; t < m; t += g) cj[t * nl] = fma(-w, v[t], cj[t * nl]);
-        rij = fma(-w, 1.0, aij);  // the value the lane owning row i stored (v_i = 1)
+        const double w = tv * fma(scal, lay.dsum[jl], aij);
+        const double ws = w * scal;
+        for (int t = i + 1 + sub; t < m; t += g) cj[t * nl] = fma(-ws, v[t], cj[t * nl]);
+        rij = aij - w;
+        if (sub == 0) cj[i * nl] = rij;
       }
       double nn = fma(-rij, rij, nrm[jl]);
       if (nn <= thr[jl]) {  // cancelled (or negative): recompute from rows i+1 .. m-1
         double q = 0.0;
-        for (int t = i + sub; t < m; t += g)
-          if (t > i) q = fma(cj[t * nl], cj[t * nl], q);
+        for (int t = i + 1 + sub; t < m; t += g) q = fma(cj[t * nl], cj[t * nl], q);
         for (int o = 1; o < g; o <<= 1) q += __shfl_xor_sync(gmask, q, o);
         nn = q;
         if (sub == 0) thr[jl] = 0x1p-26 * q;

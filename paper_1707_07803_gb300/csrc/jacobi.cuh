@@ -356,6 +356,42 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 // Extra doubles the matrix-product refinement (jacobi_refine) needs after the sweeps' area.
 __host__ __device__ inline int64_t jacobi_refine_work(int64_t n) { return 7 * n * (n + 1); }
 
+// Whether the product refinement can succeed, judged from the FP32 sweeps' squared column norms nf
+// (the singular values to FP32 accuracy, up to a common scale): all of them above an FP32 noise
+// floor (4 sqrt(n) FLT_EPSILON sigma_max) and no two within 1e-3 relative of each other. Declining
+// here skips the refinement's O(n^3) products where its own FP64 checks would reject the matrix
+// (exactly rank-deficient or clustered spectra); an accepted matrix is still checked there. All
+// threads of the CTA call it; the result is uniform.
+static __device__ __noinline__ bool jacobi_refine_plausible(const float *nf, int n) {
+  __shared__ float s_mx;
+  __shared__ int s_ok;
+  if (threadIdx.x < 32) {
+    float mx = 0.0f;
+    for (int i = threadIdx.x; i < n; i += 32) mx = fmaxf(mx, nf[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) {
+      s_mx = sqrtf(mx);
+      s_ok = mx > 0.0f && isfinite(mx) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  const float floor_ = 4.0f * sqrtf((float)n) * FLT_EPSILON * s_mx;
+  bool bad = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float si = sqrtf(fmaxf(nf[i], 0.0f));
+    bad |= !(si > floor_);
+    for (int j = 0; j < i; ++j) {
+      const float sj = sqrtf(fmaxf(nf[j], 0.0f));
+      bad |= fabsf(si - sj) <= 1e-3f * fmaxf(si, sj);
+    }
+  }
+  if (bad) s_ok = 0;  // benign race: every writer stores 0
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
+}
+
 // Matrix-product refinement of an SVD (Ogita and Aishima, "Iterative refinement for singular value
 // decomposition based on matrix multiplication", 2020), restated. A (n x n, ld n) is the matrix,
 // Vin (ld ldv) approximate right singular vectors (the FP32 sweeps' result, widened). With
@@ -665,7 +701,9 @@ static __device__ __noinline__ int jacobi_fp64_finish(double *G, double *V, int 
 static __device__ __noinline__ int jacobi_sweeps_mixed(double *G, double *V, int n, double *nrm, double *work,
                                                        double *refine_work = nullptr) {
   jacobi_fp32_phase(G, n, nrm, work);
-  if (refine_work && n <= 1024 && jacobi_refine(G, work + n * (n + 1), n + 1, V, n, refine_work)) return 0;
+  if (refine_work && n <= 1024 && jacobi_refine_plausible(reinterpret_cast<const float *>(nrm), n) &&
+      jacobi_refine(G, work + n * (n + 1), n + 1, V, n, refine_work))
+    return 0;
   return jacobi_fp64_finish(G, V, n, nrm, work);
 }
 

@@ -780,13 +780,17 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(double *G, int n, int ld
     const unsigned me = cluster_ctarank();
     const int np = n * (n + 1);
     double *v0 = jw + np;  // where jacobi_fp32_phase leaves V0 (ld n + 1)
+    __shared__ int s_try;  // the refinement is worth trying (decided on CTA 0, stored into every CTA)
     if (me == 0) {
       jacobi_fp32_phase(g, n, s_norm, jw);
-      for (int idx = threadIdx.x; idx < np; idx += nthr)
-        for (unsigned rk = 1; rk < nc; ++rk) dsmem_st_f64(dsmem_addr(v0 + idx, rk), v0[idx]);
+      const bool plausible = jacobi_refine_plausible(reinterpret_cast<const float *>(s_norm), n);
+      if (plausible)
+        for (int idx = threadIdx.x; idx < np; idx += nthr)
+          for (unsigned rk = 1; rk < nc; ++rk) dsmem_st_f64(dsmem_addr(v0 + idx, rk), v0[idx]);
+      if (threadIdx.x < (int)nc) dsmem_st_s32(dsmem_addr(&s_try, (unsigned)threadIdx.x), plausible ? 1 : 0);
     }
     cluster_sync_all();
-    const bool ok = jacobi_refine(g, v0, n + 1, v, n, jw + jacobi_mixed_work(n), true);
+    const bool ok = s_try && jacobi_refine(g, v0, n + 1, v, n, jw + jacobi_mixed_work(n), true);
     if (me != 0) return;  // no shared-memory access between CTAs follows the last cluster barrier
     if (!ok) jacobi_fp64_finish(g, v, n, s_norm, jw);
   }

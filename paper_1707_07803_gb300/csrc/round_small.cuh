@@ -76,30 +76,43 @@ static __device__ int bonds_certified(const RoundSmallArgs &a, const double *sm,
   for (int k = 1; k + 1 < d; ++k) {
     const int r = Rs[k], ph = a.phys[k], r2 = Rs[k + 1], w = ph * r2;
     const double *C = sm + a.off[k], *G = gram + goff[k];
-    if (r <= 8) {
-      // small bond: G_{k+1}(b, b') = sum_{a, x} C(a, x, b) (sum_{a'} G_k(a, a') C(a', x, b')) in one
-      // pass per entry (lanes over (a, x)), instead of the product and a second pass
+    if (r <= 8 && r * ph * r2 <= a.tmp_cap) {
+      // small bond, two short phases over the whole CTA: T = G_k C_k (r x (ph r'), one output per
+      // thread, an r-term chain), then G_{k+1}(b, b') = sum_{(a, x)} C((a, x), b) T((a, x), b') for
+      // b <= b' by groups of eight lanes (three-level shuffle sum): the chain per site is ~r + 6
+      // dependent FP64 operations instead of a per-entry product and a five-level warp sum
       double *Gn = gram + goff[k + 1];
-      const int E = r2 * (r2 + 1) / 2, m = r * ph;
-      for (int ee = warp; ee < E; ee += kStepWarps) {
+      const int m = r * ph, nT = m * r2, E = r2 * (r2 + 1) / 2;
+      for (int idx = threadIdx.x; idx < nT; idx += kStepThreads) {
+        const int aa = idx % r, col = idx / r;
+        const double *cc = C + r * col;
+        double t = 0.0;
+        for (int a2 = 0; a2 < r; ++a2) t = fma(G[aa + r * a2], cc[a2], t);
+        tmp[idx] = t;
+      }
+      __syncthreads();
+      const int part = threadIdx.x & 7, ngroups = kStepThreads / 8;
+      // g0: the warp's first group, so the loop condition (and the shuffles) are warp-uniform
+      for (int ee = threadIdx.x >> 3, g0 = warp * 4; g0 < E; ee += ngroups, g0 += ngroups) {
         int j = 0, base = 0;
-        while (base + j + 1 <= ee) {
-          base += j + 1;
-          ++j;
-        }
+        const bool live = ee < E;
+        if (live)
+          while (base + j + 1 <= ee) {
+            base += j + 1;
+            ++j;
+          }
         const int i = ee - base;  // (i, j) = (b, b'), i <= j
         double sacc = 0.0;
-        for (int ax = lane; ax < m; ax += 32) {
-          const int aa = ax % r, x = ax / r;
-          const double *cj = C + r * (x + ph * j);
-          double t = 0.0;
-          for (int a2 = 0; a2 < r; ++a2) t = fma(G[aa + r * a2], cj[a2], t);
-          sacc = fma(C[aa + r * (x + ph * i)], t, sacc);
+        if (live) {
+          const double *ci = C + m * i, *tj = tmp + m * j;
+          for (int ax = part; ax < m; ax += 8) sacc = fma(ci[ax], tj[ax], sacc);
         }
-        const double v = dwarp_sum(sacc);
-        if (lane == 0) {
-          Gn[i + r2 * j] = v;
-          Gn[j + r2 * i] = v;
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+        if (live && part == 0) {
+          Gn[i + r2 * j] = sacc;
+          Gn[j + r2 * i] = sacc;
         }
       }
       __syncthreads();
@@ -135,12 +148,35 @@ static __device__ __noinline__ void round_small_body(const RoundSmallArgs &a, do
   // the certificate with G_1 from the grid's partials never reads core 0: it is loaded only when
   // the sweeps have to run
   const bool lazy0 = a.certify && a.g1_part && a.R[1] <= 16;
-  for (int k = lazy0 ? 1 : 0; k < d; ++k) {
-    const int n = a.R[k] * a.phys[k] * a.R[k + 1];
-    const double *src = a.core[k];
-    double *dst = sm + a.off[k];
-    // through L2: inside the cooperative compression other CTAs wrote these cores
-    for (int i = threadIdx.x; i < n; i += kStepThreads) dst[i] = __ldcg(src + i);
+  // every core's loads in flight together: one pass over the concatenated index range, four
+  // elements per thread loaded before any is stored (through L2: inside the cooperative
+  // compression other CTAs wrote these cores)
+  {
+    const int k0 = lazy0 ? 1 : 0;
+    int total = 0;
+    for (int k = k0; k < d; ++k) total += a.R[k] * a.phys[k] * a.R[k + 1];
+    for (int g0 = threadIdx.x; g0 < total; g0 += 4 * kStepThreads) {
+      double v[4];
+      int dst[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int g = g0 + u * kStepThreads;
+        dst[u] = -1;
+        if (g < total) {
+          int k = k0, n = a.R[k] * a.phys[k] * a.R[k + 1];
+          while (g >= n) {
+            g -= n;
+            ++k;
+            n = a.R[k] * a.phys[k] * a.R[k + 1];
+          }
+          dst[u] = a.off[k] + g;
+          v[u] = __ldcg(a.core[k] + g);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (dst[u] >= 0) sm[dst[u]] = v[u];
+    }
   }
   __syncthreads();
   double *tmp = sm + a.tmp_off, *rbuf = sm + a.rbuf_off, *work = sm + a.work_off;

@@ -117,6 +117,30 @@ def test_solve_exact_recovery_prescribed_sigma():
     np.testing.assert_allclose(S, sigma[:4], rtol=1e-12)
 
 
+@pytest.mark.parametrize("K", [1, 2, 3, 7, 9, 31, 32, 33, 40])
+def test_solve_kxk_svd_sizes(K):
+    """The K x K SVD of the MPO-SVD at sizes around its paths: K <= 32 runs on an 8-CTA cluster
+    (K < 8: CTAs without product columns; K = 31, 32: the FP32 sweeps' widest one-warp-per-pair
+    case), K > 32 on one CTA with the same refinement. A of exact rank K with singular values 0.8^j
+    (separated: the refinement accepts), k = K // 2, p = K - k: the singular values equal the
+    oracle's and the exact ones."""
+    sigma = 0.8 ** np.arange(K)
+    A, _, _ = W.prescribed_mpo(K, K + 1, 16, [2, 2, 2], K, 3, sigma)
+    k = max(1, K // 2)
+    S, So, _ = _check_solve(A, k, K - k, 1, seed=K, tol=1e-13, max_rank=0)
+    np.testing.assert_allclose(S, sigma[:k], rtol=1e-12)
+
+
+def test_solve_rank_deficient_kxk_factor():
+    """A of rank 10 solved with K = 16: the K x K factor has six zero singular values, so the
+    refinement is skipped (FP32 noise floor) and the FP64 sweeps finish; the leading eight singular
+    values are exact."""
+    sigma = 0.8 ** np.arange(10)
+    A, _, _ = W.prescribed_mpo(50, 51, 16, [2, 2, 2], 10, 3, sigma)
+    S, So, _ = _check_solve(A, 8, 8, 1, seed=3, tol=1e-13, max_rank=0)
+    np.testing.assert_allclose(S, sigma[:8], rtol=1e-12)
+
+
 def test_solve_repeated_singular_values_take_the_fp64_sweeps():
     """Prescribed singular values in groups of equal values (1 x3, 0.5 x3, 0.25 x2, then distinct):
     the K x K SVD of B has equal singular values, so its product refinement declines and the FP64

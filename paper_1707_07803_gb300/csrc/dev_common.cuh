@@ -14,6 +14,18 @@ __device__ __forceinline__ double dwarp_sum(double v) {
   return v;
 }
 
+// Position (i, j), i <= j (strict: i < j), of entry idx of the packed upper triangle of an n x n
+// matrix, column by column. The FP32 square root is corrected by integer steps.
+__device__ __forceinline__ void packed_upper(int idx, bool strict, int &i, int &j) {
+  const int s = strict ? 1 : 0;  // strict: column j holds j entries, else j + 1
+  int c = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f) + s;
+  auto start = [s](int col) { return s ? col * (col - 1) / 2 : col * (col + 1) / 2; };
+  while (c > 0 && start(c) > idx) --c;
+  while (start(c + 1) <= idx) ++c;
+  j = c;
+  i = idx - start(c);
+}
+
 // Jacobi rotation (c, s) annihilating gamma = g_p^T g_q for alpha = ||g_p||^2, beta = ||g_q||^2:
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) / (2 gamma). The angle
 // only steers convergence, so t is formed in FP32 after an exact power-of-two scaling; c =

@@ -308,18 +308,6 @@ static __device__ void cta_nn_product(double *C, int ldc, const double *X, int l
   }
 }
 
-// Position (i, j), i <= j (strict: i < j), of entry idx of the packed upper triangle of an n x n
-// matrix, column by column. The FP32 square root is corrected by integer steps.
-__device__ __forceinline__ void packed_upper(int idx, bool strict, int &i, int &j) {
-  const int s = strict ? 1 : 0;  // strict: column j holds j entries, else j + 1
-  int c = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f) + s;
-  auto start = [s](int col) { return s ? col * (col - 1) / 2 : col * (col + 1) / 2; };
-  while (c > 0 && start(c) > idx) --c;
-  while (start(c + 1) <= idx) ++c;
-  j = c;
-  i = idx - start(c);
-}
-
 // R = I - X^T X (n x n, ld ldr) for X (ld ldx): the upper triangle computed (entries
 // me, me + nc, ... of its packed order on CTA me of nc), the lower mirrored, stored as
 // cta_nn_product stores.

@@ -183,26 +183,54 @@ __device__ void rows_solve(double *ys, int nr, int K, const double *Ru, const do
 
 // X <- Phi(E - X^T X) for E = a - I (a: G2 in shared memory), the fixed-point step of the series
 // of the Cholesky factor of I + E; xs, ps: K x K work (leading dimension kS1Ld), xs = X on entry
-// (ignored when first) and on exit. (X^T X)(i, l) = sum_{q <= i} X(q, i) X(q, l) for i <= l: a
-// warp takes whole rows i (lanes over l, so its loop length i + 1 is uniform), rows paired as
-// i and K - 1 - i so that every warp's dependent chain has the same length.
-__device__ void chol_series_step(const double *a, double *xs, double *ps, int K, bool first) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (!first)
-    for (int h = warp; h < (K + 1) / 2; h += nw)
-      for (int side = 0; side < 2; ++side) {
-        const int i = side == 0 ? h : K - 1 - h;
-        if (side == 1 && i == h) break;
-        double p = 0.0;
-        if (lane < K && lane >= i)
-          for (int q = 0; q <= i; ++q) p = fma(xs[q + kS1Ld * i], xs[q + kS1Ld * lane], p);
-        if (lane < K) ps[i + kS1Ld * lane] = p;
+// (ignored when first) and on exit. (X^T X)(i, l) = sum_{q <= i} X(q, i) X(q, l) for i <= l (X is
+// upper triangular): the packed upper triangle is spread over the whole CTA, one entry per thread
+// and pass, summed in four interleaved chains; only the upper triangle of ps is read. With f32 the
+// sums run on the FP32 pipe from xs32, an FP32 copy of X kept beside it: X^T X is a correction of
+// size ~K emax^2 (emax = max |E|), so its FP32 rounding error is at most ~K^2 2^-24 emax^2, below
+// 1e-17 when K emax <= 1e-5 (the caller's condition for f32); on GB300 the FP64 pipe issues one
+// warp instruction per ~64 cycles, so the FP64 sums cost ~5 us per step and the FP32 ones ~0.3.
+__device__ void chol_series_step(const double *a, double *xs, float *xs32, double *ps, int K, bool first, bool f32) {
+  if (!first) {
+    const int E = K * (K + 1) / 2;
+    for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
+      int i, l;
+      packed_upper(idx, false, i, l);  // i <= l
+      double sum;
+      int q = 0;
+      if (f32) {
+        const float *xi = xs32 + kS1Ld * i, *xl = xs32 + kS1Ld * l;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        for (; q + 3 <= i; q += 4) {
+          s0 = fmaf(xi[q], xl[q], s0);
+          s1 = fmaf(xi[q + 1], xl[q + 1], s1);
+          s2 = fmaf(xi[q + 2], xl[q + 2], s2);
+          s3 = fmaf(xi[q + 3], xl[q + 3], s3);
+        }
+        for (; q <= i; ++q) s0 = fmaf(xi[q], xl[q], s0);
+        sum = (double)((s0 + s1) + (s2 + s3));
+      } else {
+        const double *xi = xs + kS1Ld * i, *xl = xs + kS1Ld * l;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (; q + 3 <= i; q += 4) {
+          s0 = fma(xi[q], xl[q], s0);
+          s1 = fma(xi[q + 1], xl[q + 1], s1);
+          s2 = fma(xi[q + 2], xl[q + 2], s2);
+          s3 = fma(xi[q + 3], xl[q + 3], s3);
+        }
+        for (; q <= i; ++q) s0 = fma(xi[q], xl[q], s0);
+        sum = (s0 + s1) + (s2 + s3);
       }
+      ps[i + kS1Ld * l] = sum;
+    }
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int i = e % K, l = e / K;
-    const double m = a[i + kS1Ld * l] - (i == l ? 1.0 : 0.0) - (first ? 0.0 : ps[i + kS1Ld * l]);
-    xs[i + kS1Ld * l] = i < l ? m : (i == l ? 0.5 * m : 0.0);
+    const double m = a[i + kS1Ld * l] - (i == l ? 1.0 : 0.0) - (first || i > l ? 0.0 : ps[i + kS1Ld * l]);
+    const double x = i < l ? m : (i == l ? 0.5 * m : 0.0);
+    xs[i + kS1Ld * l] = x;
+    if (f32) xs32[i + kS1Ld * l] = (float)x;
   }
   __syncthreads();
 }
@@ -214,6 +242,7 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
   __shared__ double r1s[kS1MaxK * kS1Ld];  // R1
   __shared__ double xs[kS1MaxK * kS1Ld];   // R2 (series: X, then I + X)
   __shared__ double ps[kS1MaxK * kS1Ld];   // series work
+  __shared__ float xs32[kS1MaxK * kS1Ld];  // series: an FP32 copy of X
   __shared__ double dinv[kS1MaxK], rd1[kS1MaxK], rd2[kS1MaxK], rdq[kS1MaxK];
   __shared__ unsigned long long s_emax;
   if (a.gate && __ldcg(a.gate) == 0) return;  // uniform: written by an earlier launch
@@ -288,9 +317,10 @@ __global__ void __launch_bounds__(kS1Threads) k_site1_cholqr2(Site1Args a) {
     return;  // uniform; the core is unchanged
   }
   if (K * emax <= 1e-4) {  // R2 = I + X from three steps of the series
-    chol_series_step(am, xs, ps, K, true);
-    chol_series_step(am, xs, ps, K, false);
-    chol_series_step(am, xs, ps, K, false);
+    const bool f32 = K * emax <= 1e-5;  // uniform: every CTA read the same Gram
+    chol_series_step(am, xs, xs32, ps, K, true, f32);
+    chol_series_step(am, xs, xs32, ps, K, false, f32);
+    chol_series_step(am, xs, xs32, ps, K, false, f32);
     if (tid < K) {
       const double r = 1.0 + xs[tid + kS1Ld * tid];
       xs[tid + kS1Ld * tid] = r;

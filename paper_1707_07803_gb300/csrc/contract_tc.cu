@@ -28,7 +28,9 @@ namespace {
 
 constexpr int kTcM = 128;      // MMA M (cta_group::1)
 constexpr int kTcBK = 64;      // K elements staged per stage (4 MMAs of K = 16)
-constexpr int kTcThreads = 128;
+// 8 warps: two per TMEM lane quadrant (tcgen05.ld reaches lanes 32 (warp mod 4) ..), splitting the
+// epilogue's columns, and twice the threads of the operand conversions of one warp per quadrant
+constexpr int kTcThreads = 256;
 
 // index i -> (i % n1) * s1 + (i / n1) * s2
 struct IdxMap {
@@ -229,11 +231,12 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(TcArgs a) {
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!s_abort) {
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-    const int64_t rowoff = s_crow[warp * 32 + lane];
-    for (int c0 = 0; c0 < a.BN; c0 += 8) {
+    // epilogue: warps w and w + 4 own TMEM lanes 32w..32w+31 = tile rows, alternate 8-column groups
+    const int quad = warp & 3, nh = kTcThreads / 128;
+    const int64_t rowoff = s_crow[quad * 32 + lane];
+    for (int c0 = (warp >> 2) * 8; c0 < a.BN; c0 += 8 * nh) {
       uint32_t v[8];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
@@ -406,10 +409,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm_tma(const __grid_constan
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!s_abort) {
-    const int64_t rowoff = s_crow[warp * 32 + lane];
-    for (int c0 = 0; c0 < a.BN; c0 += 8) {
+    const int quad = warp & 3, nh = kTcThreads / 128;  // as in k_tc_gemm
+    const int64_t rowoff = s_crow[quad * 32 + lane];
+    for (int c0 = (warp >> 2) * 8; c0 < a.BN; c0 += 8 * nh) {
       uint32_t v[8];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])

@@ -176,11 +176,12 @@ class Mpo:
     """Dims, ranks and flat CUDA core buffers of an MPO (layout of include/tnrsvd.h): float64, or
     float32 for the inputs that accept it (tnr_solve, the differentiable solve)."""
 
-    def __init__(self, I, J, R, cores):
+    def __init__(self, I, J, R, cores, flat=None):
         self.I = [int(x) for x in I]
         self.J = [int(x) for x in J]
         self.R = [int(x) for x in R]
         self.cores = list(cores)
+        self.flat = flat  # one buffer holding every core back to back (the cores are views), or None
 
     @property
     def d(self):
@@ -205,18 +206,35 @@ class Mpo:
         return m
 
     @staticmethod
-    def from_numpy(cores, device="cuda", dtype=None):
+    def from_numpy(cores, device="cuda", dtype=None, flat=False):
         """Logical numpy cores (R, I, J, R') -> flat device buffers in memory order (float64, or
-        dtype=numpy.float32 for float32 input cores)."""
+        dtype=numpy.float32 for float32 input cores). With flat=True the cores are views into one
+        buffer (Mpo.flat), so that one copy moves all of them (host_flat gives its host image)."""
         import numpy as np
 
         dt = np.float64 if dtype is None else dtype
-        flat = [torch.from_numpy(np.ascontiguousarray(np.asarray(c, dtype=dt).reshape(-1, order="F")))
-                .to(device) for c in cores]
+        host = [np.ascontiguousarray(np.asarray(c, dtype=dt).reshape(-1, order="F")) for c in cores]
         I = [c.shape[1] for c in cores]
         J = [c.shape[2] for c in cores]
         R = [cores[0].shape[0]] + [c.shape[3] for c in cores]
-        return Mpo(I, J, R, flat)
+        if not flat:
+            return Mpo(I, J, R, [torch.from_numpy(h).to(device) for h in host])
+        buf = torch.from_numpy(np.concatenate(host)).to(device)
+        views, off = [], 0
+        for h in host:
+            views.append(buf[off:off + h.size])
+            off += h.size
+        return Mpo(I, J, R, views, flat=buf)
+
+    @staticmethod
+    def host_flat(cores, dtype=None):
+        """The host image of Mpo.from_numpy(cores, flat=True).flat: one pinned buffer with the cores
+        in memory order, back to back (the input of SolvePlan.run_host)."""
+        import numpy as np
+
+        dt = np.float64 if dtype is None else dtype
+        host = np.concatenate([np.ascontiguousarray(np.asarray(c, dtype=dt).reshape(-1, order="F")) for c in cores])
+        return torch.from_numpy(host).pin_memory()
 
     def to_numpy(self):
         """Flat device buffers -> logical numpy cores (copies to host)."""
@@ -405,18 +423,45 @@ class SolvePlan:
         dev = A.cores[0].device
         self.ws_bytes = b.value
         self.ws = torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
-        self.U_cores = [torch.empty(max(self.us.cap[i], 1), dtype=torch.float64, device=dev) for i in range(self.us.d)]
-        self.V_cores = [torch.empty(max(self.vs.cap[i], 1), dtype=torch.float64, device=dev) for i in range(self.vs.d)]
+        # S, U's cores and V's cores back to back in one buffer (out_flat), each core at its capacity
+        ucap = [max(self.us.cap[i], 1) for i in range(self.us.d)]
+        vcap = [max(self.vs.cap[i], 1) for i in range(self.vs.d)]
+        self.out_flat = torch.empty(self.k + sum(ucap) + sum(vcap), dtype=torch.float64, device=dev)
+        self.S = self.out_flat[:self.k]
+        off = self.k
+        self.U_cores, self.V_cores = [], []
+        for c in ucap:
+            self.U_cores.append(self.out_flat[off:off + c])
+            off += c
+        for c in vcap:
+            self.V_cores.append(self.out_flat[off:off + c])
+            off += c
         for i in range(self.us.d):
             self.us.core[i] = self.U_cores[i].data_ptr()
             self.vs.core[i] = self.V_cores[i].data_ptr()
-        self.S = torch.empty(self.k, dtype=torch.float64, device=dev)
 
     def run(self, q, seed, stream=None):
         lib = load()
         _check(lib.tnr_solve(ctypes.byref(self.sa), self.k, self.p, int(q), ctypes.c_uint64(int(seed)),
                              ctypes.byref(self.opts), ctypes.byref(self.us), _ptr(self.S), ctypes.byref(self.vs),
                              _ptr(self.ws), self.ws_bytes, _stream(stream)), "tnr_solve")
+        return self
+
+    def run_host(self, host_in, host_out, q, seed, stream=None):
+        """One solve with host buffers: host_in (pinned; the operator's cores back to back, as
+        Mpo.host_flat gives them) goes to the device in one copy into the operator's flat buffer
+        (the plan's operator must come from Mpo.from_numpy(..., flat=True)), the solve runs, and
+        out_flat (S, then U's and V's cores at their capacities) comes back in one copy into
+        host_out (pinned, out_flat.numel() doubles). All on the plan's stream; returns self."""
+        if self.A.flat is None:
+            raise ValueError("run_host needs an operator built with Mpo.from_numpy(..., flat=True)")
+        if host_in.numel() != self.A.flat.numel() or host_out.numel() != self.out_flat.numel():
+            raise ValueError("host buffers do not match the operator's flat buffer or out_flat")
+        st = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(st):
+            self.A.flat.copy_(host_in, non_blocking=True)
+            self.run(q, seed, st)
+            host_out.copy_(self.out_flat, non_blocking=True)
         return self
 
     def outputs(self):

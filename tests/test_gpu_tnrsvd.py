@@ -241,3 +241,26 @@ def test_float32_input_cores_are_widened_exactly():
     pr = dict(A=T.Mpo.from_numpy(A32, dtype=np.float32), k=4, p=4, q=1, seed=3, tol=1e-13, max_rank=8)
     with pytest.raises(T.TnrError):
         T.PersistentBatch([pr], precision=T.TNR_FP64)
+
+
+def test_run_host_moves_inputs_and_outputs_in_one_copy_each():
+    """SolvePlan.run_host: the operator built with flat=True, its host image (Mpo.host_flat) copied
+    in one transfer, the outputs (S, then U's and V's cores at their capacities) copied back in one:
+    the host copy equals the device outputs of a plain run and S equals the oracle's."""
+    A = W.gaussian_mpo(0, [4] * 4, [4] * 4, [1, 3, 3, 3, 1], scale=1 / np.sqrt(12))
+    k, p, q, seed = 5, 5, 1, 4
+    plan = T.SolvePlan(T.Mpo.from_numpy(A, flat=True), k, p, tol=1e-14)
+    assert plan.A.flat is not None and all(c.data_ptr() >= plan.A.flat.data_ptr() for c in plan.A.cores)
+    host_in = T.Mpo.host_flat(A)
+    host_out = torch.empty(plan.out_flat.numel(), dtype=torch.float64).pin_memory()
+    plan.A.flat.zero_()  # the operator must come from host_in
+    plan.run_host(host_in, host_out, q, seed)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_out.numpy(), plan.out_flat.cpu().numpy())
+    _, So, _ = ot.tnrsvd(A, k, p, q, seed, tol=1e-14)
+    assert sv_rel_err(host_out[:k].numpy(), So) <= FP64_SV_TOL
+    ref = T.SolvePlan(T.Mpo.from_numpy(A), k, p, tol=1e-14).run(q, seed)
+    torch.cuda.synchronize()
+    assert np.array_equal(ref.S.cpu().numpy(), host_out[:k].numpy())
+    with pytest.raises(ValueError):
+        plan.run_host(host_in[:-1], host_out, q, seed)

@@ -41,7 +41,7 @@ KERNELS = {
 UNIT = "solves/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the named kernel, as recorded in
 # profiles/; reported only while that kernel is unchanged (empty: not yet re-captured).
-TRAFFIC_BYTES = {"qr_piv": 2.79e6}
+TRAFFIC_BYTES = {"qr_piv": 2.80e6}
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (no tensor-core boost), nominal from the platform table
 
 

@@ -8,9 +8,9 @@
 // bond. Here the whole sweep runs on the device: the first thread-block cluster factors M_k in
 // shared memory (the cluster-distributed pivoted QR of qr_cluster.cuh: each of its CTAs owns a
 // block of columns; without clusters, CTA 0 runs the thread-per-column QR of qr_tpc.cuh) while
-// the other CTAs wait at a grid barrier; then the other CTAs absorb L into core k-1 while the
-// cluster forms Q_k (only L is on the sweep's critical path), and the next bond starts after a
-// second barrier.
+// the other CTAs stage their blocks of rows of core k-1 in shared memory and wait at a grid
+// barrier; then they multiply those rows by L (the absorb) while the cluster forms Q_k (only L is
+// on the sweep's critical path), and the next bond starts after a second barrier.
 // Ranks stay in device memory and are read back once at the end. A bond whose matrix does not
 // fit the one-CTA QR (more than 64 rows, or beyond the shared-memory capacity) ends the kernel
 // with the state of the host-driven sweep just before that bond, which the host then continues.

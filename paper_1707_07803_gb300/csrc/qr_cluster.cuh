@@ -11,11 +11,13 @@
 //      every CTA's receive buffers (st.shared::cluster; slots alternate by step parity);
 //   2. barrier.cluster (release/acquire): all C x 4 candidates are in every CTA's shared memory;
 //   3. every warp picks the same pivot p from them (largest remaining norm, ties to the lowest
-//      column), so the cutoff test is decided identically in every CTA, and each factorisation
-//      warp forms the Householder reflector from p's received column itself (no CTA-wide sync);
-//   4. each warp applies it to its columns (g lanes per column, a group-local shuffle sum) and
-//      downdates the column norms (LAPACK dgeqp3 safeguard: recompute once the downdate has lost
-//      half the digits), then posts its next candidate (1.).
+//      column), so the cutoff test is decided identically in every CTA; a fifth warp forms the
+//      Householder parameters from p's received column while the factorisation warps form the
+//      partial dot products of their columns with it (they do not depend on the parameters), and
+//      a named barrier of those five warps joins the two;
+//   4. each factorisation warp applies the reflector to its columns (g lanes per column, a
+//      group-local shuffle sum) and downdates the column norms (LAPACK dgeqp3 safeguard: recompute
+//      once the downdate has lost half the digits), then posts its next candidate (1.).
 // The cluster's control flow depends only on data every CTA holds identically, so all CTAs
 // execute the same barriers.
 // Outputs of qr_cluster_cta: L = R^T in the original column order (each CTA writes its own

@@ -12,8 +12,9 @@
 // is at the rounding level of the whole matrix (||g|| <= n eps ||G||_F) are numerically zero and
 // are not rotated: rotating one against a large column only re-injects rounding error. A pair
 // is skipped once |g_p^T g_q| <= tol ||g_p|| ||g_q||, tol = 16 eps sqrt(n).
-// The sweeps are written once for FP32 and FP64; jacobi_sweeps_mixed runs them in FP32 first and
-// finishes in FP64 (see there), which is what the SVD kernels call.
+// The sweeps are written once for FP32 and FP64 (plus a one-warp-per-pair FP32 variant for
+// n <= 32); jacobi_sweeps_mixed runs them in FP32 first and finishes in FP64 (see there), which is
+// what the SVD kernels call, optionally by the matrix-product refinement instead of FP64 sweeps.
 #pragma once
 
 #include <cfloat>

@@ -741,15 +741,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_small_tpc(QrSmallArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// One-sided Jacobi SVD of an n x n matrix in one CTA (Hestenes): rotate column pairs of G,
-// accumulating V, until every pair is orthogonal to |g_p^T g_q| <= tol ||g_p|| ||g_q||.
-// Pairs follow a round-robin tournament, so each round's pairs are disjoint and are
-// processed by different warps. Column norms are recomputed at the start of each sweep and
-// updated in between with ||g_p'||^2 = ||g_p||^2 - t gamma, ||g_q'||^2 = ||g_q||^2 + t gamma,
-// so a pair costs one dot product. Columns whose norm is at the rounding level of the whole
-// matrix (||g|| <= n eps ||G||_F) are numerically zero and are not rotated: rotating such a
-// column against a large one only re-injects rounding error and never converges.
-// Results sorted by descending singular value.
+// SVD of an n x n matrix G = U S V^T: one-sided (Hestenes) Jacobi sweeps in FP32 (jacobi.cuh:
+// column pairs of a round-robin tournament rotated until every pair is orthogonal to FP32
+// accuracy; columns at the rounding level of the whole matrix are not rotated), then the
+// matrix-product refinement to FP64 accuracy when the FP32 singular values are separated, else
+// Newton-Schulz and FP64 sweeps. Launched as one CTA, or, with the working set in shared memory
+// and n <= 32, as a thread-block cluster whose CTA 0 runs the sweeps and whose CTAs share the
+// refinement's products. Results sorted by descending singular value.
 // ------------------------------------------------------------------------------------------
 constexpr int kJacThreads = 512;
 

@@ -177,3 +177,26 @@ def test_zipup_planning_reaches_the_stated_batched_shapes(lib):
     S = ctypes.c_void_p(1 << 20)
     assert lib.tnr_solve(probs[2].A, 8, 8, 1, 0, ctypes.byref(zo), probs[2].U, S, probs[2].V, ctypes.c_void_p(1 << 20),
                          1 << 20, None) == -1
+
+
+def test_flat_operator_layout_on_the_host():
+    """Mpo.from_numpy(..., flat=True): the cores are views into one buffer, back to back in site
+    order and in the memory order of the unflattened cores (checked on the CPU device), so one copy
+    of its host image moves the whole operator."""
+    import numpy as np
+
+    from paper_1707_07803_gb300 import tnrsvd as T
+
+    rng = np.random.default_rng(3)
+    cores = [rng.standard_normal((1, 4, 3, 2)), rng.standard_normal((2, 5, 1, 3)), rng.standard_normal((3, 2, 2, 1))]
+    A = T.Mpo.from_numpy(cores, device="cpu", flat=True)
+    B = T.Mpo.from_numpy(cores, device="cpu")
+    assert A.flat is not None and B.flat is None
+    assert A.flat.numel() == sum(c.size for c in cores)
+    off = 0
+    for a, b, c in zip(A.cores, B.cores, cores):
+        assert a.data_ptr() == A.flat.data_ptr() + 8 * off
+        assert np.array_equal(a.numpy(), b.numpy())
+        off += c.size
+    assert A.R == B.R == [1, 2, 3, 1] and A.I == [4, 5, 2] and A.J == [3, 1, 2]
+    assert [np.array_equal(x, y) for x, y in zip(A.to_numpy(), cores)] == [True] * 3
